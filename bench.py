@@ -1,0 +1,373 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 multigrid Monge-Ampere reconstruction.
+
+One step = one whole reconstruction of a seeded 512^3 Zel'dovich field
+(L = 512 Mpc/h, sigma_lin = 1, smoothing R = 2 Mpc/h) with particles already
+resident in HBM:
+    CIC deposit -> Gaussian smoothing / floor (input conditioning, torch FFT)
+    -> mixed-precision FAS solve to ||r|| / ||b - 1|| < 1e-8 -> displacement.
+All reconstruction steps run in librecon's hand-written sm_103a kernels.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle instead (on a bounded sample of the same recipe, extrapolated).
+Multi-GPU runs (torchrun) are independent replicas: every rank reconstructs
+its own realisation (weak scaling, no collective in the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("512³ time-to-‖r‖/‖δ‖<1e-8 (mixed vs FP64 GPU); "
+          "GS cell-updates/s; HBM %")
+UNIT = "512^3 reconstructions/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="mixed-512")
+    p.add_argument("--dtype", default="mixed", choices=["mixed", "f64"])
+    p.add_argument("--no-fp64-compare", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-sample-n", type=int, default=128)
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            if self.uuid and self.uuid not in parts[0]:
+                continue
+            rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- CPU side
+def oracle_sample(n: int, seed: int):
+    """Oracle reconstruction of one n^3 realisation of the same recipe
+    (h = 1 Mpc/h, sigma_lin = 1, R = 2 Mpc/h).  Returns (seconds, info)."""
+    from oracle import oracle as O
+    from paper_1709_06350_gb300 import synth
+    L = float(n)
+    _, dh = synth.linear_field(n, L, 1.0, seed)
+    pos = synth.zeldovich_positions(dh, n, L)
+    t0 = time.perf_counter()
+    rho = O.cic_deposit(pos, n, L)
+    t1 = time.perf_counter()
+    b = synth.smooth_and_floor(rho, L, 2.0)        # input conditioning: not timed
+    t2 = time.perf_counter()
+    theta, info = O.solve(b, L, tol=1e-8, max_cycles=40)
+    O.displace(theta, b, L)
+    t3 = time.perf_counter()
+    return (t1 - t0) + (t3 - t2), info
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    n = 64
+    scale = (512 / n) ** 3
+    for w in range(args.warmup):
+        oracle_sample(n, 3000 + w)
+    times = []
+    for k in range(args.steps):
+        t, info = oracle_sample(n, 3100 + k)
+        times.append(t * scale)
+    ms = statistics.mean(times) * 1e3
+    v = 1.0 / statistics.mean(times)
+    sample = (f"oracle (single-threaded FP64 C) reconstruction of a {n}^3 realisation of the "
+              f"512^3 recipe (h = 1 Mpc/h, sigma_lin = 1, R = 2 Mpc/h): CIC + FAS solve to 1e-8 "
+              f"+ displacement, timed and scaled by (512/{n})^3 = {scale:.0f} (same cycle count assumed)")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "mixed-512 (oracle sample, see cpu_baseline.sample)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU side
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_1709_06350_gb300 import build as pbuild
+    from paper_1709_06350_gb300 import recon, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    if rank == 0:
+        pbuild.build()
+    if world > 1:
+        dist.barrier()
+    recon.load()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    W = synth.WORKLOADS[args.workload]
+    N, L, R, tol = W.N, W.L, W.R, W.tol
+    _, dh = synth.linear_field(N, L, W.sigma_lin, W.seed + 7919 * rank, backend="torch",
+                               device=dev)
+    pos = synth.zeldovich_positions(dh, N, L).contiguous()
+    del dh
+    torch.cuda.empty_cache()
+
+    dtype = recon.RECON_MIXED if args.dtype == "mixed" else recon.RECON_F64
+    solver = recon.Solver(N, L, dtype)
+    rho = torch.zeros((N, N, N), dtype=torch.float64, device=dev)
+    phi = torch.zeros_like(rho)
+    stream = torch.cuda.current_stream()
+    solve_ms = []
+    last = {}
+
+    def step(pos_dev):
+        rho.zero_()
+        solver.deposit_cic(pos_dev, rho=rho)
+        b = synth.smooth_and_floor(rho, L, R)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, st = solver.solve(b, phi=phi, tol=tol, max_cycles=40)
+        e1.record(stream)
+        psi, dl = solver.displace(phi, b)
+        last.update(st=st, b=b, dl=dl, ev=(e0, e1))
+        return dl
+
+    for _ in range(max(args.warmup, 3)):
+        step(pos)
+    torch.cuda.synchronize()
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        pass
+    launches0 = recon.recon_kernel_launches()
+    with ClockSampler(uuid) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for _ in range(args.steps):
+            step(pos)
+            e0, e1 = last["ev"]
+            solve_ms.append((e0, e1))
+        t_end.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    launches = recon.recon_kernel_launches() - launches0
+    elapsed_ms = max_over_ranks(t_start.elapsed_time(t_end))
+    solve_times = [a.elapsed_time(b) for a, b in solve_ms]
+    st = last["st"]
+
+    # ---- end to end through the public API from pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        pos_host = pos.cpu().pin_memory()
+        dl_host = torch.empty((N, N, N), dtype=torch.float64).pin_memory()
+        pos_dev = torch.empty_like(pos)
+        ke = max(1, min(args.steps, 3))
+        step(pos)  # warm
+        barrier()
+        torch.cuda.synchronize()
+        a, bev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(ke):
+            pos_dev.copy_(pos_host, non_blocking=True)
+            dl = step(pos_dev)
+            dl_host.copy_(dl.view(N, N, N), non_blocking=True)
+        bev.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = max_over_ranks(a.elapsed_time(bev)) / ke
+        e2e = {"value": world * 1e3 / e2e_ms, "unit": UNIT,
+               "h2d_bytes_per_step": pos.numel() * 8, "d2h_bytes_per_step": N ** 3 * 8,
+               "ms_per_step": e2e_ms}
+        del pos_host, dl_host, pos_dev
+
+    # ---- FP64 GPU path on the same density (the comparison the metric names)
+    fp64 = None
+    if not args.no_fp64_compare and dtype == recon.RECON_MIXED:
+        s64 = recon.Solver(N, L, recon.RECON_F64)
+        b = last["b"]
+        p64 = torch.zeros_like(b)
+        s64.solve(b, phi=p64, tol=tol, max_cycles=40)
+        torch.cuda.synchronize()
+        a, bev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _, st64 = s64.solve(b, phi=p64, tol=tol, max_cycles=40)
+        bev.record(stream)
+        torch.cuda.synchronize()
+        diff = float(torch.linalg.norm(p64 - phi) / torch.linalg.norm(p64))
+        fp64 = {"time_to_tol_s": a.elapsed_time(bev) / 1e3, "cycles": st64["cycles"],
+                "rel_residual": st64["rel_residual"], "mixed_vs_fp64_rel_l2": diff}
+        s64.close()
+        del p64
+
+    # ---- roofline of the dominant kernel: the FP32 red-black smoother pass,
+    # timed on the level-0 FP32 arrays with CUDA events on its own stream
+    roof = kernel_roofline(recon, torch, N, L, dev, stream)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        n = args.cpu_sample_n
+        t, info = oracle_sample(n, 3200)
+        scale = (N / n) ** 3
+        cpu = {"value": 1.0 / (t * scale), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": (f"oracle (single-threaded FP64 C) CIC + FAS solve to 1e-8 + displacement "
+                          f"of a {n}^3 realisation of the same recipe (h = 1 Mpc/h): {t:.2f} s, "
+                          f"{info['cycles']} cycles, scaled by (N/{n})^3 = {scale:.0f}")}
+
+    if rank == 0:
+        ms = elapsed_ms / args.steps
+        line = {
+            "metric": METRIC, "value": world * args.steps / (elapsed_ms / 1e3), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32/f64" if dtype == recon.RECON_MIXED else "f64",
+            "data": "synthetic",
+            "config": {"workload": (f"{W.name}: {N}^3 seeded Zel'dovich field, L = {L:g} Mpc/h, "
+                                    f"sigma_lin = {W.sigma_lin}, R = {R:g} Mpc/h, CIC + smoothing "
+                                    f"+ solve to ||r||/||b-1|| < {tol:g} + displacement"),
+                       "l2": "inputs larger than L2 (particle positions "
+                             f"{pos.numel() * 8 / 1e9:.1f} GB, fields {N ** 3 * 8 / 1e9:.2f} GB)",
+                       "solver": solver.config()},
+            "time_to_tol_s": {"mixed": statistics.median(solve_times) / 1e3,
+                              "fp64": fp64["time_to_tol_s"] if fp64 else None},
+            "solve": {"fas_cycles": st["cycles"], "outer_iterations": st["outer_iterations"],
+                      "rel_residual": st["rel_residual"], "compat_c": st["compat_c"],
+                      "history": st["history"]},
+            "fp64_path": fp64,
+            "gs_cell_updates_per_s": roof.pop("cell_updates_per_s", None),
+            "roofline": roof,
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def kernel_roofline(recon, torch, N, L, dev, stream):
+    """FP32 smoother pass at N^3: average duration over repeated launches.
+
+    Algorithmic bytes of one colour pass: the FP32 smoother moves 12 B per
+    cell per full sweep at minimum (read theta, read b, write theta), i.e.
+    6 B per cell per colour pass."""
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs")
+    src = "measured (MEASURED_PEAKS.json hbm_gbs, burst)" if hbm else "fallback 6800 GB/s"
+    hbm = hbm or 6800.0
+    h = L / N
+    th = torch.zeros((N, N, N), dtype=torch.float32, device=dev)
+    g = torch.ones_like(th)
+    work = torch.empty_like(th)
+    reps = 10
+    recon.recon_step_sweep(th, g, 0.0, h, sweeps=2, work=work, stream=stream)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    recon.recon_step_sweep(th, g, 0.0, h, sweeps=reps, work=work, stream=stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    per_launch_s = a.elapsed_time(b) / 1e3 / (2 * reps)
+    alg_bytes = 6.0 * N ** 3
+    achieved = alg_bytes / per_launch_s / 1e9
+    del th, g, work
+    return {"kernel": "k_rb_pass<float> (FP32 red-black smoother, one colour pass)",
+            "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": None, "peak_source": src,
+            "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": per_launch_s * 1e3,
+            "cell_updates_per_s": N ** 3 / (2 * per_launch_s)}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

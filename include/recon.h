@@ -1,0 +1,185 @@
+/*
+ * recon.h -- C ABI of librecon: GB300 (sm_103a) multigrid solve of the
+ * mass-conservation (Monge-Ampere) equation of Shi, Cautun & Li,
+ * "New method for initial density reconstruction" (arXiv:1709.06350).
+ *
+ * The library finds the displacement potential phi (the paper's theta,
+ * Sec. II eq. theta0: Theta = x^2/2 + theta) on a periodic N^3 grid with
+ *
+ *     det(I + H_h phi) = b + c,      mean(phi) = 0,                     (*)
+ *
+ * where b = 1 + delta is the normalised final density (eq. basic_eqs),
+ * H_h the second-order Hessian stencils of eq. discrete_examples and c one
+ * scalar that makes the discrete problem solvable (the discrete determinant
+ * is not exactly mass-conserving; c is O(h^2) and is reported).
+ *
+ * Conventions for every call
+ *   - grids are N^3 doubles in C order [i][j][k] (k fastest, i = x axis),
+ *     cell centres at (i + 1/2) h, h = L / N, periodic;
+ *   - every array pointer is a DEVICE pointer owned by the caller unless the
+ *     argument says "host"; the handle owns only its workspace;
+ *   - work is enqueued on the handle's stream (recon_set_stream; default the
+ *     legacy default stream).  recon_solve synchronises the stream once per
+ *     V-cycle to read the convergence scalar; the other calls return without
+ *     synchronising;
+ *   - no call throws; each returns a recon_status and, on failure, stores a
+ *     message retrievable with recon_last_error (per handle);
+ *   - a handle is not thread-safe: use one handle per host thread / stream.
+ */
+#ifndef RECON_H
+#define RECON_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RECON_OK = 0,
+    RECON_E_INVALID = 1,        /* bad argument (size, pointer, option)            */
+    RECON_E_DOMAIN = 2,         /* b <= 0 or non-finite somewhere                  */
+    RECON_E_NOCONV = 3,         /* max_cycles reached before the tolerance         */
+    RECON_E_DIVERGED = 4,       /* residual became non-finite or grew 1e3-fold     */
+    RECON_E_CUDA = 5,           /* a CUDA runtime call or kernel launch failed     */
+    RECON_E_OOM = 6,            /* device allocation failed                        */
+    RECON_E_TIMEOUT = 7,        /* a bounded device wait ran out                   */
+    RECON_E_UNIMPLEMENTED = 8
+} recon_status;
+
+typedef enum {
+    RECON_F64 = 0,              /* every step in FP64                              */
+    RECON_MIXED = 1             /* FP32 multigrid inside FP64 defect correction;
+                                   phi and the fine-grid residual stay FP64        */
+} recon_dtype;
+
+typedef enum {
+    RECON_RULE_NEWTON1 = 0,     /* one safeguarded Newton step on the cell cubic   */
+    RECON_RULE_EXACT = 1        /* the paper's update: largest root of the cubic   */
+} recon_rule;
+
+typedef enum {
+    RECON_START_FMG = 0,        /* nested iteration from phi = 0 on the coarsest
+                                   grid; the contents of phi on entry are ignored  */
+    RECON_START_GUESS = 1       /* V-cycles start from phi as passed in (resume)   */
+} recon_start;
+
+/* Solver options.  Defaults (recon_create): nu1 = nu2 = 2,
+ * coarse_max_sweeps = 200, coarse_rtol = 1e-3, rule = NEWTON1, start = FMG,
+ * scale_floor = 0.5, mixed_switch_rtol = 1e-4, mixed_fas_max_cycles = 12,
+ * mixed_linear_vcycles = 2. */
+typedef struct {
+    int nu1, nu2;               /* pre- / post-smoothing sweeps per level          */
+    int coarse_max_sweeps;      /* coarsest grid: sweep cap                        */
+    double coarse_rtol;         /* coarsest grid: stop when the mean-free rms
+                                   residual falls by this factor                   */
+    int rule;                   /* recon_rule                                      */
+    int start;                  /* recon_start                                     */
+    double scale_floor;         /* scaled-defect safeguard: the coarse right side
+                                   is det_H(R phi) + s R r with the largest s <= 1
+                                   keeping it >= (1 - scale_floor) det_H(R phi);
+                                   the correction is divided by s (<= 0: s = 1)   */
+    double mixed_switch_rtol;   /* MIXED: FP32 FAS cycles until this relative
+                                   residual, then FP64 defect correction           */
+    int mixed_fas_max_cycles;   /* MIXED: cap on the FP32 FAS cycles               */
+    int mixed_linear_vcycles;   /* MIXED: FP32 linear V-cycles per correction      */
+} recon_config;
+
+#define RECON_HISTORY_MAX 64
+
+typedef struct {
+    int cycles;                 /* F64: finest-grid FAS V-cycles.
+                                   MIXED: FP32 FAS V-cycles                        */
+    int outer_iterations;       /* MIXED: FP64 defect-correction iterations        */
+    double rel_residual;        /* ||r - mean r||_2 / ||b - 1||_2 at exit, r the
+                                   FP64 residual b + c - det(I + H phi)            */
+    double compat_c;            /* the scalar c of (*)                             */
+    double seconds;             /* wall time of the call                           */
+    int n_history;              /* entries of history[] that are set               */
+    double history[RECON_HISTORY_MAX]; /* relative residual after each cycle /
+                                   outer iteration, in order                       */
+} recon_stats;
+
+typedef struct recon_handle recon_handle;
+
+/* Create a solver for an N^3 grid of side L (Mpc/h or any length unit;
+ * phi comes out in that unit squared).  N must be even and >= 4, and the
+ * multigrid hierarchy (halve N while the half is even and >= 4) must end at
+ * a coarsest grid of at most 16^3; L > 0.  Allocates the whole workspace
+ * (recon_workspace_bytes) with cudaMalloc on the current device.
+ * Errors: RECON_E_INVALID, RECON_E_OOM, RECON_E_CUDA. */
+recon_status recon_create(int N, double L, recon_dtype dtype, recon_handle **out);
+
+/* Free the workspace and the handle (NULL is ignored). */
+void recon_destroy(recon_handle *h);
+
+/* Bytes of device workspace a handle of this size holds (0 if invalid). */
+size_t recon_workspace_bytes(int N, recon_dtype dtype);
+
+/* Enqueue all later work of this handle on `stream` (a cudaStream_t). */
+recon_status recon_set_stream(recon_handle *h, void *stream);
+
+/* Read / replace the solver options (host structs). */
+recon_status recon_get_config(const recon_handle *h, recon_config *cfg);
+recon_status recon_set_config(recon_handle *h, const recon_config *cfg);
+
+/* Cloud-in-cell density assignment (Sec. I footnote; spec step a1).
+ * pos: device, n_part x 3 doubles (x, y, z) in [0, L) (wrapped if not).
+ * rho: device N^3, ACCUMULATED into (zero it first for a fresh density);
+ * each particle adds mass * prod_axis w, w = (1 - f, f) on cells
+ * (i0, i0 + 1), u = x * (N / L) - 1/2, i0 = floor(u) mod N, f = u - floor(u).
+ * Use mass = N^3 / n_part for a density normalised to mean 1.
+ * Errors: RECON_E_INVALID (n_part < 0, null pointers), RECON_E_CUDA. */
+recon_status recon_deposit_cic(recon_handle *h, const double *pos, long long n_part,
+                               double mass, double *rho);
+
+/* Solve (*) (Sec. II.A: Gauss-Seidel relaxation of eq. update inside the
+ * FAS V-cycles of eqs. PDE_H and corrections).
+ * b:   device N^3, 1 + delta, every entry finite and > 0 (else RECON_E_DOMAIN).
+ * phi: device N^3; on entry the initial guess when start = GUESS (ignored
+ *      for FMG); on exit the mean-free solution.
+ * tol: stop when ||r - mean r||_2 / ||b - 1||_2 < tol (r the FP64 residual).
+ * max_cycles: cap on finest-grid cycles (F64) / outer iterations (MIXED).
+ * stats: host, nullable.
+ * Returns RECON_OK, RECON_E_NOCONV (phi holds the last iterate),
+ * RECON_E_DIVERGED, RECON_E_DOMAIN, RECON_E_INVALID, RECON_E_CUDA.
+ * The handle keeps a pointer to phi's values for recon_adjoint (it copies
+ * nothing; do not change phi between recon_solve and recon_adjoint). */
+recon_status recon_solve(recon_handle *h, const double *b, double *phi, double tol,
+                         int max_cycles, recon_stats *stats);
+
+/* Reconstruction output (Sec. II.B steps B2-B3, eq. reconstructed_density,
+ * and x - q = -grad theta of Sec. III.B), restated on the grid:
+ *   psi  (device 3 x N^3, component-major) = -(central gradient of phi);
+ *   q_c = x_c + grad phi (mod L) for every Eulerian cell centre x_c;
+ *   v_c = 3 - tr((I + H phi)^-1)   (div_q chi, chi = q - x);
+ *   deltaL (device N^3, on the Lagrangian grid) =
+ *       CIC(q_c, b_c v_c) / max(CIC(q_c, b_c), 1e-12).
+ * Uses 2 N^3 doubles of handle workspace.  Errors: RECON_E_INVALID,
+ * RECON_E_CUDA. */
+recon_status recon_displace(recon_handle *h, const double *phi, const double *b,
+                            double *psi, double *deltaL);
+
+/* Adjoint of the last recon_solve on this handle (implicit-function theorem
+ * on (*)): given gbar_phi = dLoss/dphi (device N^3), writes
+ * gbar_b = dLoss/db (device N^3, zero-sum), i.e. lam with
+ *   J^T lam + mu 1 = gbar_phi,  sum(lam) = 0,  J = d det(I + H phi)/d phi.
+ * Errors: RECON_E_INVALID (no previous solve), RECON_E_NOCONV,
+ * RECON_E_CUDA, RECON_E_UNIMPLEMENTED (not available in this build). */
+recon_status recon_adjoint(recon_handle *h, const double *gbar_phi, double *gbar_b);
+
+/* Message of the last failing call on this handle ("" if none); a handle
+ * of NULL gives the last message of recon_create on this thread. */
+const char *recon_last_error(const recon_handle *h);
+
+/* Name of a status code. */
+const char *recon_status_string(recon_status s);
+
+/* Number of CUDA kernels this library has launched in this process so far
+ * (all handles and step calls; diagnostics for launch accounting). */
+unsigned long long recon_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RECON_H */

@@ -1,0 +1,71 @@
+/*
+ * recon_steps.h -- single steps of the librecon solve, exposed one kernel
+ * (or one short kernel sequence) per call so that each step can be checked
+ * against an independent implementation on the same inputs.
+ *
+ * Every pointer is a DEVICE pointer owned by the caller; `prec` selects the
+ * element type of the grid arrays (0 = double, 1 = float); every call is
+ * asynchronous on `stream` (a cudaStream_t, NULL = legacy default stream);
+ * grids are N^3 in C order [i][j][k], periodic, spacing h.  The returned
+ * status is RECON_E_INVALID for a bad size / option, RECON_E_CUDA when a
+ * launch fails, else RECON_OK.  Scalars that the full solver keeps on the
+ * device (c, scale factors) are passed here as host values.
+ */
+#ifndef RECON_STEPS_H
+#define RECON_STEPS_H
+
+#include "recon.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* `sweeps` red-black Gauss-Seidel sweeps of eq. update (Sec. II.A.2) on
+ * det(I + H theta) = g + c.  Red = (i+j+k) even, then black; within one
+ * colour every update reads the values held at the start of that colour
+ * pass.  rule: recon_rule.  work: N^3 scratch of the same type.  N even. */
+recon_status recon_step_sweep(int N, double h, int prec, int rule, void *theta,
+                              const void *g, double c, int sweeps, void *work,
+                              void *stream);
+
+/* r = g + c - det(I + H theta) (FP64). */
+recon_status recon_step_residual(int N, double h, const double *theta,
+                                 const double *g, double c, double *r, void *stream);
+
+/* det(I + H theta) per cell (FP64). */
+recon_status recon_step_det(int N, double h, const double *theta, double *det,
+                            void *stream);
+
+/* coarse = 8-son mean of fine (Sec. II.A.3), coarse is (Nf/2)^3. */
+recon_status recon_step_restrict(int Nf, int prec, const void *fine, void *coarse,
+                                 void *stream);
+
+/* fine += scale * P(cnew - cold), P the cell-centred trilinear prolongation
+ * (eq. corrections); cnew, cold are Nc^3, fine (2 Nc)^3; cold may be NULL
+ * (taken as zero). */
+recon_status recon_step_prolong_add(int Nc, int prec, const void *cnew,
+                                    const void *cold, double scale, void *fine,
+                                    void *stream);
+
+/* Coarsest-grid solve: sweeps of recon_step_sweep until the mean-free rms
+ * residual falls below rtol times its start or max_sweeps sweeps ran; one
+ * thread block, N^3 <= 4096.  sweeps_done: device int (nullable). */
+recon_status recon_step_coarse_solve(int N, double h, int prec, int rule, void *theta,
+                                     const void *g, double c, int max_sweeps,
+                                     double rtol, void *work, int *sweeps_done,
+                                     void *stream);
+
+/* CIC cell of every particle and axis: cells (n x 3 int32) = floor(u) mod N,
+ * frac (n x 3 double) = u - floor(u), u = x * (N/L) - 1/2. */
+recon_status recon_step_cic_cells(const double *pos, long long n, int N, double L,
+                                  int *cells, double *frac, void *stream);
+
+/* J v = sum_ab adj(I + H theta)_ab D_ab v, the linearisation of
+ * det(I + H theta) in theta (FP64). */
+recon_status recon_step_jacobian_apply(int N, double h, const double *theta,
+                                       const double *v, double *out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RECON_STEPS_H */

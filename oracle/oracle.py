@@ -80,6 +80,7 @@ def _load():
             "or_jacobian_apply": (None, [_P, _P, _I, _D, _P]),
             "or_jacobian_coo": (None, [_P, _I, _D, _P, _P, _P]),
             "or_det_grid": (None, [_P, _I, _D, _P]),
+            "or_det_cells": (None, [_P, _I, _D, _L, _P, _P]),
             "or_cubic_grid": (None, [_P, _P, _D, _I, _D, _P, _P, _P]),
         }
         for name, (res, args) in sig.items():
@@ -136,6 +137,15 @@ def det_grid(theta, h) -> np.ndarray:
     t = _f64(theta)
     out = np.empty_like(t)
     _load().or_det_grid(_ptr(t), _grid_n(t), float(h), _ptr(out))
+    return out
+
+
+def det_cells(theta, h, ijk) -> np.ndarray:
+    """det(I + H_h theta) at the cells listed in ijk ([m, 3] ints)."""
+    t = _f64(theta)
+    idx = np.ascontiguousarray(ijk, dtype=np.int32).reshape(-1, 3)
+    out = np.empty(idx.shape[0])
+    _load().or_det_cells(_ptr(t), _grid_n(t), float(h), idx.shape[0], _ptr(idx), _ptr(out))
     return out
 
 

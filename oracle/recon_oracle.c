@@ -862,3 +862,11 @@ void or_cic_cells(const double *pos, long npart, int N, double L, int *cells,
         for (int d = 0; d < 3; ++d)
             or_cic_cell(pos[3 * p + d], N, L, &cells[3 * p + d], &frac[3 * p + d]);
 }
+
+/* det(I + H theta) at a list of cells (ijk: ncells x 3 ints); used to check
+ * a large solution on sampled cells. */
+void or_det_cells(const double *t, int N, double h, long ncells, const int *ijk, double *out)
+{
+    for (long m = 0; m < ncells; ++m)
+        out[m] = or_det_cell(t, N, h, ijk[3 * m], ijk[3 * m + 1], ijk[3 * m + 2]);
+}

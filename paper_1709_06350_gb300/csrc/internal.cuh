@@ -1,0 +1,86 @@
+// internal.cuh -- the handle and the launchers shared by librecon's
+// translation units (not part of the public ABI).
+#pragma once
+
+#include <string>
+
+#include "common.cuh"
+
+constexpr int kMaxLevels = 16;
+constexpr int kMaxRedBlocks = 2048;   // grid cap of every reducing kernel
+
+struct recon_handle {
+    int N = 0;
+    double L = 0.0, h = 0.0;
+    recon_dtype dtype = RECON_F64;
+    recon_config cfg{};
+    cudaStream_t stream = nullptr;
+
+    int nlev = 0;
+    int Nl[kMaxLevels] = {};
+    double hl[kMaxLevels] = {};
+
+    // FP64 hierarchy: level 0 theta / g are the caller's phi / b.
+    double *t64[kMaxLevels] = {}, *g64[kMaxLevels] = {}, *told64[kMaxLevels] = {},
+           *aux64[kMaxLevels] = {};
+    double *work64 = nullptr;    // N^3: smoother ping-pong, displace numerator
+    double *work64b = nullptr;   // N^3: displace denominator, adjoint scratch
+
+    // FP32 hierarchy (MIXED): FAS theta / g / saved theta / aux, linear e / f.
+    float *t32[kMaxLevels] = {}, *g32[kMaxLevels] = {}, *told32[kMaxLevels] = {},
+          *aux32[kMaxLevels] = {};
+    float *e32[kMaxLevels] = {}, *f32[kMaxLevels] = {};
+    float *work32 = nullptr;
+
+    double *scal = nullptr;      // device scalars (recon::Slot)
+    double *partials = nullptr;  // kMaxRedBlocks x 4 doubles
+    int *iscratch = nullptr;     // small device ints
+    double *hscal = nullptr;     // pinned host mirror of scal
+
+    const double *last_phi = nullptr;
+    const double *last_b = nullptr;
+    bool have_solve = false;
+
+    std::string err;
+};
+
+namespace recon {
+
+// Kernels launched by this library in this process (diagnostics).
+void note_launch(unsigned long long n = 1);
+
+// ---- multigrid launchers (recon_mg.cu); all asynchronous on `s`.
+template <typename T>
+cudaError_t sweep(int N, double h, int rule, T *t, const T *g, const double *cptr,
+                  double cval, int sweeps, T *work, cudaStream_t s);
+cudaError_t residual_write(int N, double h, const double *t, const double *g,
+                           const double *cptr, double cval, double *r, cudaStream_t s);
+cudaError_t det_write(int N, double h, const double *t, double *out, cudaStream_t s);
+template <typename T>
+cudaError_t restrict_plain(int Nf, const T *fine, T *coarse, cudaStream_t s);
+template <typename T>
+cudaError_t prolong_add(int Nc, const T *cnew, const T *cold, const double *pscale,
+                        double scale, T *fine, cudaStream_t s);
+template <typename T>
+cudaError_t coarse_solve(int N, double h, int rule, T *t, const T *g, const double *cptr,
+                         double cval, int max_sweeps, double rtol, T *work, int *sweeps_out,
+                         cudaStream_t s);
+cudaError_t jacobian_apply(int N, double h, const double *t, const double *v, double *out,
+                           cudaStream_t s);
+
+// ---- the solvers (recon_mg.cu)
+recon_status solve_f64(recon_handle *H, const double *b, double *phi, double tol,
+                       int max_cycles, recon_stats *st);
+recon_status solve_mixed(recon_handle *H, const double *b, double *phi, double tol,
+                         int max_cycles, recon_stats *st);
+recon_status check_domain(recon_handle *H, const double *b);
+
+// ---- CIC and displacement (recon_cic.cu)
+cudaError_t cic_cells(const double *pos, long long n, int N, double L, int *cells,
+                      double *frac, cudaStream_t s);
+cudaError_t cic_deposit(const double *pos, long long n, int N, double L, double mass,
+                        double *rho, cudaStream_t s);
+cudaError_t displace(int N, double L, const double *phi, const double *b, double *psi,
+                     double *deltaL, double *num, double *den, cudaStream_t s);
+
+}  // namespace recon

@@ -1,0 +1,421 @@
+// recon_api.cu -- the C ABI of librecon (include/recon.h, include/recon_steps.h):
+// argument checks, workspace ownership, status codes and messages.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "internal.cuh"
+
+using namespace recon;
+
+namespace {
+
+thread_local std::string g_create_err;
+
+// Hierarchy of Sec. II.A.3: halve while the half is even and >= 4.
+int level_sizes(int N, int *Nl)
+{
+    int L = 0;
+    Nl[L++] = N;
+    while (N % 2 == 0 && N / 2 >= 4 && (N / 2) % 2 == 0 && L < kMaxLevels) {
+        N /= 2;
+        Nl[L++] = N;
+    }
+    return L;
+}
+
+const char *check_size(int N, int *Nl, int *nlev)
+{
+    if (N < 4 || N % 2 != 0) return "N must be even and >= 4";
+    if (N > 4096) return "N must be <= 4096";
+    *nlev = level_sizes(N, Nl);
+    const int Nc = Nl[*nlev - 1];
+    if ((long)Nc * Nc * Nc > kMaxCoarseCells)
+        return "the coarsest grid (halving N while the half is even and >= 4) must be <= 16^3";
+    return nullptr;
+}
+
+recon_config default_config()
+{
+    recon_config c;
+    c.nu1 = 2;
+    c.nu2 = 2;
+    c.coarse_max_sweeps = 200;
+    c.coarse_rtol = 1e-3;
+    c.rule = RECON_RULE_NEWTON1;
+    c.start = RECON_START_FMG;
+    c.scale_floor = 0.5;
+    c.mixed_switch_rtol = 1e-4;
+    c.mixed_fas_max_cycles = 12;
+    c.mixed_linear_vcycles = 2;
+    return c;
+}
+
+// Byte plan of the workspace; alloc = false only sums the sizes.
+struct Planner {
+    bool alloc;
+    size_t total = 0;
+    bool failed = false;
+    template <typename T>
+    void take(T **p, size_t count)
+    {
+        const size_t bytes = ((sizeof(T) * count + 255) / 256) * 256;
+        total += bytes;
+        if (!alloc || failed) return;
+        if (cudaMalloc((void **)p, bytes) != cudaSuccess) {
+            failed = true;
+            *p = nullptr;
+        }
+    }
+};
+
+void plan(recon_handle *H, Planner &P)
+{
+    const size_t n0 = (size_t)H->N * H->N * H->N;
+    P.take(&H->work64, n0);
+    P.take(&H->work64b, n0);
+    for (int l = 1; l < H->nlev; ++l) {
+        const size_t n = (size_t)H->Nl[l] * H->Nl[l] * H->Nl[l];
+        if (H->dtype == RECON_F64) {
+            P.take(&H->t64[l], n);
+            P.take(&H->g64[l], n);
+            P.take(&H->told64[l], n);
+            P.take(&H->aux64[l], n);
+        }
+    }
+    if (H->dtype == RECON_MIXED) {
+        for (int l = 0; l < H->nlev; ++l) {
+            const size_t n = (size_t)H->Nl[l] * H->Nl[l] * H->Nl[l];
+            P.take(&H->t32[l], n);
+            P.take(&H->g32[l], n);
+            P.take(&H->e32[l], n);
+            P.take(&H->f32[l], n);
+            if (l > 0) {
+                P.take(&H->told32[l], n);
+                P.take(&H->aux32[l], n);
+            }
+        }
+        P.take(&H->work32, n0);
+    }
+    P.take(&H->scal, (size_t)S_COUNT);
+    P.take(&H->partials, (size_t)4 * kMaxRedBlocks);
+    P.take(&H->iscratch, (size_t)64);
+}
+
+void free_all(recon_handle *H)
+{
+    auto f = [](void *p) {
+        if (p) cudaFree(p);
+    };
+    f(H->work64);
+    f(H->work64b);
+    f(H->work32);
+    for (int l = 0; l < kMaxLevels; ++l) {
+        if (l > 0) {
+            f(H->t64[l]);
+            f(H->g64[l]);
+        }
+        f(H->told64[l]);
+        f(H->aux64[l]);
+        f(H->t32[l]);
+        f(H->g32[l]);
+        f(H->told32[l]);
+        f(H->aux32[l]);
+        f(H->e32[l]);
+        f(H->f32[l]);
+    }
+    f(H->scal);
+    f(H->partials);
+    f(H->iscratch);
+    if (H->hscal) cudaFreeHost(H->hscal);
+}
+
+recon_status set_err(recon_handle *H, recon_status s, const std::string &msg)
+{
+    if (H) H->err = msg;
+    return s;
+}
+
+recon_status cuda_status(recon_handle *H, cudaError_t e, const char *where)
+{
+    if (e == cudaSuccess) return RECON_OK;
+    return set_err(H, RECON_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *recon_status_string(recon_status s)
+{
+    switch (s) {
+    case RECON_OK: return "RECON_OK";
+    case RECON_E_INVALID: return "RECON_E_INVALID";
+    case RECON_E_DOMAIN: return "RECON_E_DOMAIN";
+    case RECON_E_NOCONV: return "RECON_E_NOCONV";
+    case RECON_E_DIVERGED: return "RECON_E_DIVERGED";
+    case RECON_E_CUDA: return "RECON_E_CUDA";
+    case RECON_E_OOM: return "RECON_E_OOM";
+    case RECON_E_TIMEOUT: return "RECON_E_TIMEOUT";
+    case RECON_E_UNIMPLEMENTED: return "RECON_E_UNIMPLEMENTED";
+    }
+    return "RECON_E_UNKNOWN";
+}
+
+size_t recon_workspace_bytes(int N, recon_dtype dtype)
+{
+    recon_handle H;
+    if (check_size(N, H.Nl, &H.nlev)) return 0;
+    if (dtype != RECON_F64 && dtype != RECON_MIXED) return 0;
+    H.N = N;
+    H.dtype = dtype;
+    Planner P{false};
+    plan(&H, P);
+    return P.total;
+}
+
+recon_status recon_create(int N, double L, recon_dtype dtype, recon_handle **out)
+{
+    g_create_err.clear();
+    if (!out) {
+        g_create_err = "out is NULL";
+        return RECON_E_INVALID;
+    }
+    *out = nullptr;
+    recon_handle *H = new (std::nothrow) recon_handle();
+    if (!H) {
+        g_create_err = "host allocation failed";
+        return RECON_E_OOM;
+    }
+    const char *why = check_size(N, H->Nl, &H->nlev);
+    if (!why && !(L > 0.0 && std::isfinite(L))) why = "L must be finite and > 0";
+    if (!why && dtype != RECON_F64 && dtype != RECON_MIXED) why = "unknown dtype";
+    if (why) {
+        g_create_err = why;
+        delete H;
+        return RECON_E_INVALID;
+    }
+    H->N = N;
+    H->L = L;
+    H->h = L / N;
+    for (int l = 0; l < H->nlev; ++l) H->hl[l] = H->h * (double)(1 << l);
+    H->dtype = dtype;
+    H->cfg = default_config();
+    Planner P{true};
+    plan(H, P);
+    if (P.failed) {
+        g_create_err = "cudaMalloc of " + std::to_string(P.total) + " bytes of workspace failed";
+        free_all(H);
+        delete H;
+        cudaGetLastError();
+        return RECON_E_OOM;
+    }
+    if (cudaMallocHost((void **)&H->hscal, sizeof(double) * S_COUNT) != cudaSuccess) {
+        H->hscal = nullptr;
+        g_create_err = "cudaMallocHost failed";
+        free_all(H);
+        delete H;
+        cudaGetLastError();
+        return RECON_E_OOM;
+    }
+    cudaError_t e = cudaMemset(H->scal, 0, sizeof(double) * S_COUNT);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        g_create_err = std::string("initialising the workspace: ") + cudaGetErrorString(e);
+        free_all(H);
+        delete H;
+        return RECON_E_CUDA;
+    }
+    *out = H;
+    return RECON_OK;
+}
+
+void recon_destroy(recon_handle *H)
+{
+    if (!H) return;
+    if (H->stream) cudaStreamSynchronize(H->stream);
+    else cudaDeviceSynchronize();
+    free_all(H);
+    delete H;
+}
+
+recon_status recon_set_stream(recon_handle *H, void *stream)
+{
+    if (!H) return RECON_E_INVALID;
+    H->stream = (cudaStream_t)stream;
+    return RECON_OK;
+}
+
+recon_status recon_get_config(const recon_handle *H, recon_config *cfg)
+{
+    if (!H || !cfg) return RECON_E_INVALID;
+    *cfg = H->cfg;
+    return RECON_OK;
+}
+
+recon_status recon_set_config(recon_handle *H, const recon_config *c)
+{
+    if (!H || !c) return RECON_E_INVALID;
+    if (c->nu1 < 0 || c->nu2 < 0 || c->nu1 + c->nu2 < 1 || c->nu1 > 64 || c->nu2 > 64)
+        return set_err(H, RECON_E_INVALID, "nu1, nu2 must be in [0, 64] with nu1 + nu2 >= 1");
+    if (c->coarse_max_sweeps < 1 || c->coarse_max_sweeps > 100000)
+        return set_err(H, RECON_E_INVALID, "coarse_max_sweeps must be in [1, 100000]");
+    if (!(c->coarse_rtol >= 0.0 && c->coarse_rtol < 1.0))
+        return set_err(H, RECON_E_INVALID, "coarse_rtol must be in [0, 1)");
+    if (c->rule != RECON_RULE_NEWTON1 && c->rule != RECON_RULE_EXACT)
+        return set_err(H, RECON_E_INVALID, "unknown rule");
+    if (c->start != RECON_START_FMG && c->start != RECON_START_GUESS)
+        return set_err(H, RECON_E_INVALID, "unknown start");
+    if (!(c->scale_floor < 1.0) || !std::isfinite(c->scale_floor))
+        return set_err(H, RECON_E_INVALID, "scale_floor must be < 1");
+    if (!(c->mixed_switch_rtol > 0.0) || c->mixed_fas_max_cycles < 0 || c->mixed_linear_vcycles < 1)
+        return set_err(H, RECON_E_INVALID, "bad mixed-precision options");
+    H->cfg = *c;
+    return RECON_OK;
+}
+
+recon_status recon_deposit_cic(recon_handle *H, const double *pos, long long n_part, double mass,
+                               double *rho)
+{
+    if (!H) return RECON_E_INVALID;
+    if (n_part < 0 || (n_part > 0 && !pos) || !rho)
+        return set_err(H, RECON_E_INVALID, "bad particle count or NULL pointer");
+    return cuda_status(H, cic_deposit(pos, n_part, H->N, H->L, mass, rho, H->stream), "cic");
+}
+
+recon_status recon_solve(recon_handle *H, const double *b, double *phi, double tol, int max_cycles,
+                         recon_stats *stats)
+{
+    if (!H) return RECON_E_INVALID;
+    if (!b || !phi) return set_err(H, RECON_E_INVALID, "b and phi must be device pointers");
+    if (!(tol > 0.0) || max_cycles < 1 || max_cycles > 100000)
+        return set_err(H, RECON_E_INVALID, "tol must be > 0 and max_cycles in [1, 100000]");
+    H->err.clear();
+    H->have_solve = false;
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    recon_status s = check_domain(H, b);
+    if (s != RECON_OK) return s;
+    s = H->dtype == RECON_F64 ? solve_f64(H, b, phi, tol, max_cycles, stats)
+                              : solve_mixed(H, b, phi, tol, max_cycles, stats);
+    if (s == RECON_OK) {
+        H->last_phi = phi;
+        H->last_b = b;
+        H->have_solve = true;
+    }
+    return s;
+}
+
+recon_status recon_displace(recon_handle *H, const double *phi, const double *b, double *psi,
+                            double *deltaL)
+{
+    if (!H) return RECON_E_INVALID;
+    if (!phi || !b || !psi || !deltaL) return set_err(H, RECON_E_INVALID, "NULL pointer");
+    return cuda_status(H, displace(H->N, H->L, phi, b, psi, deltaL, H->work64, H->work64b, H->stream),
+                       "displace");
+}
+
+recon_status recon_adjoint(recon_handle *H, const double *gbar_phi, double *gbar_b)
+{
+    if (!H) return RECON_E_INVALID;
+    if (!gbar_phi || !gbar_b) return set_err(H, RECON_E_INVALID, "NULL pointer");
+    if (!H->have_solve) return set_err(H, RECON_E_INVALID, "no successful recon_solve on this handle");
+    return set_err(H, RECON_E_UNIMPLEMENTED, "the adjoint is not built yet");
+}
+
+const char *recon_last_error(const recon_handle *H)
+{
+    return H ? H->err.c_str() : g_create_err.c_str();
+}
+
+// ---------------------------------------------------------------- steps
+static bool step_size_ok(int N) { return N >= 4 && N % 2 == 0 && N <= 4096; }
+
+recon_status recon_step_sweep(int N, double h, int prec, int rule, void *theta, const void *g,
+                              double c, int sweeps, void *work, void *stream)
+{
+    if (!step_size_ok(N) || !(h > 0) || sweeps < 0 || !theta || !g || !work || (rule != 0 && rule != 1))
+        return RECON_E_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = prec == 0
+        ? sweep<double>(N, h, rule, (double *)theta, (const double *)g, nullptr, c, sweeps, (double *)work, s)
+        : prec == 1 ? sweep<float>(N, h, rule, (float *)theta, (const float *)g, nullptr, c, sweeps, (float *)work, s)
+                    : cudaErrorInvalidValue;
+    if (prec != 0 && prec != 1) return RECON_E_INVALID;
+    return e == cudaSuccess ? RECON_OK : RECON_E_CUDA;
+}
+
+recon_status recon_step_residual(int N, double h, const double *theta, const double *g, double c,
+                                 double *r, void *stream)
+{
+    if (!step_size_ok(N) || !(h > 0) || !theta || !g || !r) return RECON_E_INVALID;
+    return residual_write(N, h, theta, g, nullptr, c, r, (cudaStream_t)stream) == cudaSuccess
+               ? RECON_OK : RECON_E_CUDA;
+}
+
+recon_status recon_step_det(int N, double h, const double *theta, double *det, void *stream)
+{
+    if (!step_size_ok(N) || !(h > 0) || !theta || !det) return RECON_E_INVALID;
+    return det_write(N, h, theta, det, (cudaStream_t)stream) == cudaSuccess ? RECON_OK : RECON_E_CUDA;
+}
+
+recon_status recon_step_restrict(int Nf, int prec, const void *fine, void *coarse, void *stream)
+{
+    if (Nf < 2 || Nf % 2 != 0 || Nf > 4096 || !fine || !coarse || (prec != 0 && prec != 1))
+        return RECON_E_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = prec == 0 ? restrict_plain<double>(Nf, (const double *)fine, (double *)coarse, s)
+                              : restrict_plain<float>(Nf, (const float *)fine, (float *)coarse, s);
+    return e == cudaSuccess ? RECON_OK : RECON_E_CUDA;
+}
+
+recon_status recon_step_prolong_add(int Nc, int prec, const void *cnew, const void *cold,
+                                    double scale, void *fine, void *stream)
+{
+    if (Nc < 1 || Nc > 2048 || !cnew || !fine || (prec != 0 && prec != 1)) return RECON_E_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = prec == 0
+        ? prolong_add<double>(Nc, (const double *)cnew, (const double *)cold, nullptr, scale, (double *)fine, s)
+        : prolong_add<float>(Nc, (const float *)cnew, (const float *)cold, nullptr, scale, (float *)fine, s);
+    return e == cudaSuccess ? RECON_OK : RECON_E_CUDA;
+}
+
+recon_status recon_step_coarse_solve(int N, double h, int prec, int rule, void *theta,
+                                     const void *g, double c, int max_sweeps, double rtol,
+                                     void *work, int *sweeps_done, void *stream)
+{
+    if (!step_size_ok(N) || (long)N * N * N > kMaxCoarseCells || !(h > 0) || max_sweeps < 1 ||
+        !(rtol >= 0) || !theta || !g || !work || (rule != 0 && rule != 1) || (prec != 0 && prec != 1))
+        return RECON_E_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = prec == 0
+        ? coarse_solve<double>(N, h, rule, (double *)theta, (const double *)g, nullptr, c, max_sweeps,
+                               rtol, (double *)work, sweeps_done, s)
+        : coarse_solve<float>(N, h, rule, (float *)theta, (const float *)g, nullptr, c, max_sweeps,
+                              rtol, (float *)work, sweeps_done, s);
+    return e == cudaSuccess ? RECON_OK : RECON_E_CUDA;
+}
+
+recon_status recon_step_cic_cells(const double *pos, long long n, int N, double L, int *cells,
+                                  double *frac, void *stream)
+{
+    if (n < 0 || N < 1 || !(L > 0) || (n > 0 && (!pos || !cells || !frac))) return RECON_E_INVALID;
+    return cic_cells(pos, n, N, L, cells, frac, (cudaStream_t)stream) == cudaSuccess ? RECON_OK
+                                                                                     : RECON_E_CUDA;
+}
+
+recon_status recon_step_jacobian_apply(int N, double h, const double *theta, const double *v,
+                                       double *out, void *stream)
+{
+    if (!step_size_ok(N) || !(h > 0) || !theta || !v || !out) return RECON_E_INVALID;
+    return jacobian_apply(N, h, theta, v, out, (cudaStream_t)stream) == cudaSuccess ? RECON_OK
+                                                                                    : RECON_E_CUDA;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- diagnostics
+#include <atomic>
+static std::atomic<unsigned long long> g_launches{0};
+void recon::note_launch(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+extern "C" unsigned long long recon_kernel_launches(void) { return g_launches.load(); }

@@ -1,0 +1,1024 @@
+// recon_mg.cu -- multigrid kernels and the two solve drivers of librecon.
+//
+// Method (Shi, Cautun & Li, Sec. II.A): Gauss-Seidel relaxation of the cell
+// cubic (eq. update) inside FAS V-cycles (eqs. PDE_h_w_error, PDE_H,
+// corrections) down to a coarsest grid of at most 16^3.
+//
+// Layout: every level is a dense N_l^3 array in C order; the finest level
+// uses the caller's phi and b directly.  Red-black passes use a ping-pong
+// buffer so that every update of one colour reads the values held at the
+// start of the pass (the same-colour edge neighbours enter the cubic's
+// coefficients, so an in-place parallel pass would race).
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+
+#include "cellmath.cuh"
+#include "internal.cuh"
+
+namespace recon {
+
+static inline unsigned red_blocks(size_t work, int threads = kThreads)
+{
+    size_t b = (work + threads - 1) / threads;
+    return (unsigned)(b < (size_t)kMaxRedBlocks ? (b == 0 ? 1 : b) : kMaxRedBlocks);
+}
+
+// ======================================================================
+// smoother: one colour pass, one thread per (k even, k odd) cell pair
+// ======================================================================
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_rb_pass(const T *__restrict__ src, T *__restrict__ dst, const T *__restrict__ g,
+          const double *__restrict__ cptr, double cval, int N, T ih2, T h2_6, int colour,
+          int rule)
+{
+    const size_t half = (size_t)(N >> 1);
+    const size_t npairs = (size_t)N * (size_t)N * half;
+    const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= npairs) return;
+    const int m = (int)(tid % half);
+    const size_t r = tid / half;
+    const int j = (int)(r % (size_t)N), i = (int)(r / (size_t)N);
+    const int par = (colour + i + j) & 1;   // (i + j + k) % 2 == colour
+    const int ka = 2 * m + par, kb = 2 * m + 1 - par;
+    const T c = (T)(cptr ? *cptr : cval);
+    const Nb19<T> nb = load19<T>(src, N, i, j, ka);
+    T s, p, q;
+    cubic_coeffs(nb, ih2, g[offs(N, i, j, ka)] + c, s, p, q);
+    dst[offs(N, i, j, ka)] = point_update(nb.c, h2_6, s, p, q, rule);
+    dst[offs(N, i, j, kb)] = src[offs(N, i, j, kb)];
+}
+
+template <typename T>
+cudaError_t sweep(int N, double h, int rule, T *t, const T *g, const double *cptr,
+                  double cval, int sweeps, T *work, cudaStream_t s)
+{
+    const size_t npairs = (size_t)N * N * (N / 2);
+    const T ih2 = (T)(1.0 / (h * h)), h2_6 = (T)(h * h / 6.0);
+    for (int it = 0; it < sweeps; ++it) {
+        note_launch();
+        k_rb_pass<T><<<blocks_for(npairs), kThreads, 0, s>>>(t, work, g, cptr, cval, N, ih2, h2_6, 0, rule);
+        note_launch();
+        k_rb_pass<T><<<blocks_for(npairs), kThreads, 0, s>>>(work, t, g, cptr, cval, N, ih2, h2_6, 1, rule);
+    }
+    return cudaGetLastError();
+}
+template cudaError_t sweep<double>(int, double, int, double *, const double *, const double *, double, int, double *, cudaStream_t);
+template cudaError_t sweep<float>(int, double, int, float *, const float *, const double *, double, int, float *, cudaStream_t);
+
+// ======================================================================
+// residuals
+// ======================================================================
+__global__ void __launch_bounds__(kThreads)
+k_residual_write(const double *__restrict__ t, const double *__restrict__ g,
+                 const double *__restrict__ cptr, double cval, int N, double ih2,
+                 double *__restrict__ r)
+{
+    const size_t n = (size_t)N * N * N;
+    const size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= n) return;
+    const int k = (int)(id % N);
+    const size_t q = id / N;
+    const int j = (int)(q % N), i = (int)(q / N);
+    const double c = cptr ? *cptr : cval;
+    r[id] = (g[id] + c) - det_IH(load19<double>(t, N, i, j, k), ih2);
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_det_write(const double *__restrict__ t, int N, double ih2, double *__restrict__ out)
+{
+    const size_t n = (size_t)N * N * N;
+    const size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= n) return;
+    const int k = (int)(id % N);
+    const size_t q = id / N;
+    const int j = (int)(q % N), i = (int)(q / N);
+    out[id] = det_IH(load19<double>(t, N, i, j, k), ih2);
+}
+
+// partials[4 b + 0..2] = sum r, sum r^2, sum theta over this block's cells,
+// r = g + c - det(I + H theta).  When f32out is set (mixed path, T = double)
+// the residual is also stored as float and theta as float in t32out.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_residual_norms(const T *__restrict__ t, const T *__restrict__ g,
+                 const double *__restrict__ cptr, int N, T ih2, double *__restrict__ partials,
+                 float *__restrict__ f32out, float *__restrict__ t32out)
+{
+    __shared__ double sh[32];
+    const size_t n = (size_t)N * N * N;
+    const T c = (T)(*cptr);
+    double sr = 0.0, sr2 = 0.0, st = 0.0;
+    for (size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x; id < n;
+         id += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(id % N);
+        const size_t q = id / N;
+        const int j = (int)(q % N), i = (int)(q / N);
+        const Nb19<T> nb = load19<T>(t, N, i, j, k);
+        const T res = (g[id] + c) - det_IH(nb, ih2);
+        sr += (double)res;
+        sr2 += (double)res * (double)res;
+        st += (double)nb.c;
+        if (f32out) {
+            f32out[id] = (float)res;
+            t32out[id] = (float)nb.c;
+        }
+    }
+    double v = block_sum<kThreads>(sr, sh);
+    if (threadIdx.x == 0) partials[4 * blockIdx.x + 0] = v;
+    v = block_sum<kThreads>(sr2, sh);
+    if (threadIdx.x == 0) partials[4 * blockIdx.x + 1] = v;
+    v = block_sum<kThreads>(st, sh);
+    if (threadIdx.x == 0) partials[4 * blockIdx.x + 2] = v;
+}
+
+// Single block: total of column `col` of the partials, in a fixed order.
+__device__ double sum_partials(const double *partials, int nb, int col, double *sh)
+{
+    double v = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) v += partials[4 * b + col];
+    return block_sum<kReduceThreads>(v, sh);
+}
+
+// After a cycle on a level with n cells: m = mean r; c -= m;
+// rel = sqrt(sum (r - m)^2) / denom; mean theta for the gauge.
+__global__ void __launch_bounds__(kReduceThreads)
+k_finalize_cycle(const double *__restrict__ partials, int nb, double n, double *scal)
+{
+    __shared__ double sh[32];
+    const double sr = sum_partials(partials, nb, 0, sh);
+    const double sr2 = sum_partials(partials, nb, 1, sh);
+    const double st = sum_partials(partials, nb, 2, sh);
+    if (threadIdx.x == 0) {
+        const double m = sr / n;
+        const double var = sr2 - n * m * m;
+        scal[S_MEAN_R] = m;
+        scal[S_C] -= m;
+        scal[S_REL] = sqrt(var > 0.0 ? var : 0.0) / scal[S_DENOM];
+        scal[S_MEAN_T] = st / n;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_gauge(T *__restrict__ t, size_t n, const double *__restrict__ scal)
+{
+    const size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id < n) t[id] -= (T)scal[S_MEAN_T];
+}
+
+// ======================================================================
+// transfers
+// ======================================================================
+// Fused residual + restriction: per coarse cell, the 8 sons' residuals
+// r = g + c - det(I + H theta) and values are averaged (Sec. II.A.3: coarse
+// value = mean of the 8 son cells); the fine residual is never stored.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_restrict_residual(const T *__restrict__ t, const T *__restrict__ g,
+                    const double *__restrict__ cptr, int Nf, T ih2, T *__restrict__ tH,
+                    T *__restrict__ toldH, T *__restrict__ rrH, double *__restrict__ partials)
+{
+    __shared__ double sh[32];
+    const int Nc = Nf >> 1;
+    const size_t nc = (size_t)Nc * Nc * Nc;
+    const T c = (T)(*cptr);
+    double srr = 0.0;
+    for (size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x; id < nc;
+         id += (size_t)gridDim.x * blockDim.x) {
+        const int K = (int)(id % Nc);
+        const size_t q = id / Nc;
+        const int J = (int)(q % Nc), I = (int)(q / Nc);
+        T at = T(0), ar = T(0);
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b)
+                for (int cc = 0; cc < 2; ++cc) {
+                    const int i = 2 * I + a, j = 2 * J + b, k = 2 * K + cc;
+                    const Nb19<T> nb = load19<T>(t, Nf, i, j, k);
+                    at += nb.c;
+                    ar += (g[offs(Nf, i, j, k)] + c) - det_IH(nb, ih2);
+                }
+        const T vt = at * T(0.125), vr = ar * T(0.125);
+        tH[id] = vt;
+        toldH[id] = vt;
+        rrH[id] = vr;
+        srr += (double)vr;
+    }
+    const double v = block_sum<kThreads>(srr, sh);
+    if (threadIdx.x == 0) partials[4 * blockIdx.x + 0] = v;
+}
+
+__global__ void __launch_bounds__(kReduceThreads)
+k_finalize_mean(const double *__restrict__ partials, int nb, double n, double *out)
+{
+    __shared__ double sh[32];
+    const double s = sum_partials(partials, nb, 0, sh);
+    if (threadIdx.x == 0) *out = s / n;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_restrict_plain(const T *__restrict__ f, int Nf, T *__restrict__ cr)
+{
+    const int Nc = Nf >> 1;
+    const size_t nc = (size_t)Nc * Nc * Nc;
+    const size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= nc) return;
+    const int K = (int)(id % Nc);
+    const size_t q = id / Nc;
+    const int J = (int)(q % Nc), I = (int)(q / Nc);
+    T acc = T(0);
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+            for (int cc = 0; cc < 2; ++cc) acc += f[offs(Nf, 2 * I + a, 2 * J + b, 2 * K + cc)];
+    cr[id] = acc * T(0.125);
+}
+
+template <typename T>
+cudaError_t restrict_plain(int Nf, const T *fine, T *coarse, cudaStream_t s)
+{
+    const size_t nc = (size_t)(Nf / 2) * (Nf / 2) * (Nf / 2);
+    note_launch();
+    k_restrict_plain<T><<<blocks_for(nc), kThreads, 0, s>>>(fine, Nf, coarse);
+    return cudaGetLastError();
+}
+template cudaError_t restrict_plain<double>(int, const double *, double *, cudaStream_t);
+template cudaError_t restrict_plain<float>(int, const float *, float *, cudaStream_t);
+
+// Coarse right side, first half: rr = R r - mean(R r) (stored back in gH),
+// dH = det_H(I + H theta_H) (stored in aux), and the block minimum of the
+// scaled-defect ratio floor * max(dH, 0) / (-rr) over cells with rr < 0.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_coarse_rhs(const T *__restrict__ tH, T *__restrict__ gH, T *__restrict__ dH,
+             const double *__restrict__ mean_ptr, int Nc, T ih2, double floor_,
+             double *__restrict__ partials)
+{
+    __shared__ double sh[32];
+    const size_t nc = (size_t)Nc * Nc * Nc;
+    const T m = (T)(*mean_ptr);
+    double mn = INFINITY;
+    for (size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x; id < nc;
+         id += (size_t)gridDim.x * blockDim.x) {
+        const int K = (int)(id % Nc);
+        const size_t q = id / Nc;
+        const int J = (int)(q % Nc), I = (int)(q / Nc);
+        const T rr = gH[id] - m;
+        const T d = det_IH(load19<T>(tH, Nc, I, J, K), ih2);
+        gH[id] = rr;
+        dH[id] = d;
+        if (rr < T(0)) {
+            const double cand = floor_ * (double)(d > T(0) ? d : T(0)) / (double)(-rr);
+            mn = fmin(mn, cand);
+        }
+    }
+    const double v = block_min<kThreads>(mn, sh);
+    if (threadIdx.x == 0) partials[4 * blockIdx.x + 3] = v;
+}
+
+// s = min(1, min ratio) (1 when the safeguard is off); s < 1e-3 -> 0 (skip).
+__global__ void __launch_bounds__(kReduceThreads)
+k_finalize_scale(const double *__restrict__ partials, int nb, double floor_, double *sslot,
+                 double *pslot)
+{
+    __shared__ double sh[32];
+    double v = INFINITY;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) v = fmin(v, partials[4 * b + 3]);
+    v = block_min<kReduceThreads>(v, sh);
+    if (threadIdx.x == 0) {
+        double s = floor_ <= 0.0 ? 1.0 : fmin(1.0, v);
+        if (s < 1e-3) s = 0.0;
+        *sslot = s;
+        *pslot = s > 0.0 ? 1.0 / s : 0.0;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_form_rhs(T *__restrict__ gH, const T *__restrict__ dH, size_t nc,
+           const double *__restrict__ sslot)
+{
+    const size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id < nc) gH[id] = dH[id] + (T)(*sslot) * gH[id];
+}
+
+// fine += scale * P(cnew - cold), P cell-centred trilinear: per axis the
+// parent weighs 3/4 and the coarse neighbour on the fine cell's side 1/4.
+// scale = *pscale when pscale is given (0 = no correction), else `scale`.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_prolong_add(const T *__restrict__ cnew, const T *__restrict__ cold, int Nc,
+              const double *__restrict__ pscale, double scale, T *__restrict__ fine)
+{
+    const double sc = pscale ? *pscale : scale;
+    if (sc == 0.0) return;
+    const int Nf = 2 * Nc;
+    const size_t nf = (size_t)Nf * Nf * Nf;
+    const size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= nf) return;
+    const int k = (int)(id % Nf);
+    const size_t q = id / Nf;
+    const int j = (int)(q % Nf), i = (int)(q / Nf);
+    const int I = i >> 1, J = j >> 1, K = k >> 1;
+    const int I1 = (i & 1) ? (I + 1 == Nc ? 0 : I + 1) : (I == 0 ? Nc - 1 : I - 1);
+    const int J1 = (j & 1) ? (J + 1 == Nc ? 0 : J + 1) : (J == 0 ? Nc - 1 : J - 1);
+    const int K1 = (k & 1) ? (K + 1 == Nc ? 0 : K + 1) : (K == 0 ? Nc - 1 : K - 1);
+    T acc = T(0);
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+            for (int cc = 0; cc < 2; ++cc) {
+                const T w = (a ? T(0.25) : T(0.75)) * (b ? T(0.25) : T(0.75)) * (cc ? T(0.25) : T(0.75));
+                const size_t o = offs(Nc, a ? I1 : I, b ? J1 : J, cc ? K1 : K);
+                acc += w * (cold ? cnew[o] - cold[o] : cnew[o]);
+            }
+    fine[id] += (T)sc * acc;
+}
+
+template <typename T>
+cudaError_t prolong_add(int Nc, const T *cnew, const T *cold, const double *pscale,
+                        double scale, T *fine, cudaStream_t s)
+{
+    const size_t nf = (size_t)8 * Nc * Nc * Nc;
+    note_launch();
+    k_prolong_add<T><<<blocks_for(nf), kThreads, 0, s>>>(cnew, cold, Nc, pscale, scale, fine);
+    return cudaGetLastError();
+}
+template cudaError_t prolong_add<double>(int, const double *, const double *, const double *, double, double *, cudaStream_t);
+template cudaError_t prolong_add<float>(int, const float *, const float *, const double *, double, float *, cudaStream_t);
+
+// ======================================================================
+// coarsest grid: one thread block, N^3 <= 4096, sweeps until the mean-free
+// rms residual drops by rtol or max_sweeps ran (at least one sweep).
+// t and work are read and written by different threads of the block across
+// __syncthreads(), so they are plain (not read-only) pointers.
+// ======================================================================
+template <typename T>
+__device__ double coarse_proj_rms(const T *t, T *work, const T *g, T c, int N, T ih2,
+                                  double *sh, double *sval)
+{
+    const int n = N * N * N;
+    double sr = 0.0;
+    for (int id = threadIdx.x; id < n; id += blockDim.x) {
+        const int k = id % N, j = (id / N) % N, i = id / (N * N);
+        const T r = (g[id] + c) - det_IH(load19<T>(t, N, i, j, k), ih2);
+        work[id] = r;
+        sr += (double)r;
+    }
+    double tot = block_sum<kCoarseThreads>(sr, sh);
+    if (threadIdx.x == 0) *sval = tot / n;
+    __syncthreads();
+    const double m = *sval;
+    double s2 = 0.0;
+    for (int id = threadIdx.x; id < n; id += blockDim.x) {
+        const double d = (double)work[id] - m;
+        s2 += d * d;
+    }
+    tot = block_sum<kCoarseThreads>(s2, sh);
+    if (threadIdx.x == 0) *sval = sqrt(tot / n);
+    __syncthreads();
+    const double v = *sval;
+    __syncthreads();
+    return v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kCoarseThreads)
+k_coarse_solve(T *t, T *work, const T *g, const double *cptr, double cval, int N, T ih2, T h2_6,
+               int rule, int max_sweeps, double rtol, int *sweeps_out)
+{
+    __shared__ double sh[32];
+    __shared__ double sval;
+    const T c = (T)(cptr ? *cptr : cval);
+    const int half = N >> 1;
+    const int npairs = N * N * half;
+    const double r0 = coarse_proj_rms<T>(t, work, g, c, N, ih2, sh, &sval);
+    int sw = 0;
+    while (sw < max_sweeps) {
+        for (int colour = 0; colour < 2; ++colour) {
+            const T *src = colour == 0 ? t : work;
+            T *dst = colour == 0 ? work : t;
+            for (int pi = threadIdx.x; pi < npairs; pi += blockDim.x) {
+                const int m = pi % half, r = pi / half;
+                const int j = r % N, i = r / N;
+                const int par = (colour + i + j) & 1;
+                const int ka = 2 * m + par, kb = 2 * m + 1 - par;
+                const Nb19<T> nb = load19<T>(src, N, i, j, ka);
+                T s, p, q;
+                cubic_coeffs(nb, ih2, g[offs(N, i, j, ka)] + c, s, p, q);
+                const T vnew = point_update(nb.c, h2_6, s, p, q, rule);
+                const T vcopy = src[offs(N, i, j, kb)];
+                dst[offs(N, i, j, ka)] = vnew;
+                dst[offs(N, i, j, kb)] = vcopy;
+            }
+            __syncthreads();
+        }
+        ++sw;
+        const double cur = coarse_proj_rms<T>(t, work, g, c, N, ih2, sh, &sval);
+        if (cur <= rtol * r0) break;
+    }
+    if (threadIdx.x == 0 && sweeps_out) *sweeps_out = sw;
+}
+
+template <typename T>
+cudaError_t coarse_solve(int N, double h, int rule, T *t, const T *g, const double *cptr,
+                         double cval, int max_sweeps, double rtol, T *work, int *sweeps_out,
+                         cudaStream_t s)
+{
+    const T ih2 = (T)(1.0 / (h * h)), h2_6 = (T)(h * h / 6.0);
+    note_launch();
+    k_coarse_solve<T><<<1, kCoarseThreads, 0, s>>>(t, work, g, cptr, cval, N, ih2, h2_6, rule,
+                                                   max_sweeps, rtol, sweeps_out);
+    return cudaGetLastError();
+}
+template cudaError_t coarse_solve<double>(int, double, int, double *, const double *, const double *, double, int, double, double *, int *, cudaStream_t);
+template cudaError_t coarse_solve<float>(int, double, int, float *, const float *, const double *, double, int, double, float *, int *, cudaStream_t);
+
+// ======================================================================
+// Jacobian (linearisation of det(I + H theta))
+// ======================================================================
+__global__ void __launch_bounds__(kThreads)
+k_jacobian_apply(const double *__restrict__ t, const double *__restrict__ v, int N, double ih2,
+                 double *__restrict__ out)
+{
+    const size_t n = (size_t)N * N * N;
+    const size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= n) return;
+    const int k = (int)(id % N);
+    const size_t q = id / N;
+    const int j = (int)(q % N), i = (int)(q / N);
+    const Cof<double> a = cofactors(load19<double>(t, N, i, j, k), ih2);
+    out[id] = jac_apply(a, load19<double>(v, N, i, j, k), ih2);
+}
+
+cudaError_t jacobian_apply(int N, double h, const double *t, const double *v, double *out,
+                           cudaStream_t s)
+{
+    const size_t n = (size_t)N * N * N;
+    note_launch();
+    k_jacobian_apply<<<blocks_for(n), kThreads, 0, s>>>(t, v, N, 1.0 / (h * h), out);
+    return cudaGetLastError();
+}
+
+cudaError_t residual_write(int N, double h, const double *t, const double *g,
+                           const double *cptr, double cval, double *r, cudaStream_t s)
+{
+    const size_t n = (size_t)N * N * N;
+    note_launch();
+    k_residual_write<<<blocks_for(n), kThreads, 0, s>>>(t, g, cptr, cval, N, 1.0 / (h * h), r);
+    return cudaGetLastError();
+}
+
+cudaError_t det_write(int N, double h, const double *t, double *out, cudaStream_t s)
+{
+    const size_t n = (size_t)N * N * N;
+    note_launch();
+    k_det_write<<<blocks_for(n), kThreads, 0, s>>>(t, N, 1.0 / (h * h), out);
+    return cudaGetLastError();
+}
+
+// ======================================================================
+// domain check of b and the stop-rule denominator ||b - 1||_2
+// ======================================================================
+__global__ void __launch_bounds__(kThreads)
+k_b_stats(const double *__restrict__ b, size_t n, double *__restrict__ partials)
+{
+    __shared__ double sh[32];
+    double s2 = 0.0, mn = INFINITY, bad = 0.0;
+    for (size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x; id < n;
+         id += (size_t)gridDim.x * blockDim.x) {
+        const double v = b[id];
+        if (!isfinite(v)) bad += 1.0;
+        else {
+            s2 += (v - 1.0) * (v - 1.0);
+            mn = fmin(mn, v);
+        }
+    }
+    double v = block_sum<kThreads>(s2, sh);
+    if (threadIdx.x == 0) partials[4 * blockIdx.x + 0] = v;
+    v = block_sum<kThreads>(bad, sh);
+    if (threadIdx.x == 0) partials[4 * blockIdx.x + 1] = v;
+    v = block_min<kThreads>(mn, sh);
+    if (threadIdx.x == 0) partials[4 * blockIdx.x + 3] = v;
+}
+
+__global__ void __launch_bounds__(kReduceThreads)
+k_finalize_b(const double *__restrict__ partials, int nb, double *scal)
+{
+    __shared__ double sh[32];
+    const double s2 = sum_partials(partials, nb, 0, sh);
+    const double bad = sum_partials(partials, nb, 1, sh);
+    double mn = INFINITY;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) mn = fmin(mn, partials[4 * b + 3]);
+    mn = block_min<kReduceThreads>(mn, sh);
+    if (threadIdx.x == 0) {
+        scal[S_DENOM] = s2 > 0.0 ? sqrt(s2) : 1.0;
+        scal[S_BBAD] = bad;
+        scal[S_BMIN] = mn;
+    }
+}
+
+// ======================================================================
+// mixed-precision helpers
+// ======================================================================
+__global__ void __launch_bounds__(kThreads)
+k_to_float(const double *__restrict__ a, float *__restrict__ out, size_t n)
+{
+    const size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id < n) out[id] = (float)a[id];
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_to_double(const float *__restrict__ a, double *__restrict__ out, size_t n)
+{
+    const size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id < n) out[id] = (double)a[id];
+}
+
+// theta64 += e - mean(theta64) (defect-correction update with the gauge)
+__global__ void __launch_bounds__(kThreads)
+k_update_theta(double *__restrict__ t, const float *__restrict__ e, size_t n,
+               const double *__restrict__ scal)
+{
+    const size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id < n) t[id] = (t[id] - scal[S_MEAN_T]) + (double)e[id];
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_sub_scalar(float *__restrict__ a, size_t n, const double *__restrict__ v)
+{
+    const size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id < n) a[id] -= (float)(*v);
+}
+
+// ---- linear multigrid for J e = f in FP32 (J from the FP32 theta of the level)
+// One colour pass of Gauss-Seidel on J: e_c += (f - J e)_c / J_cc,
+// J_cc = -2 (adj_xx + adj_yy + adj_zz) / h^2.
+__global__ void __launch_bounds__(kThreads)
+k_lin_pass(const float *__restrict__ src, float *__restrict__ dst, const float *__restrict__ f,
+           const float *__restrict__ th, int N, float ih2, int colour)
+{
+    const size_t half = (size_t)(N >> 1);
+    const size_t npairs = (size_t)N * (size_t)N * half;
+    const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= npairs) return;
+    const int m = (int)(tid % half);
+    const size_t r = tid / half;
+    const int j = (int)(r % (size_t)N), i = (int)(r / (size_t)N);
+    const int par = (colour + i + j) & 1;
+    const int ka = 2 * m + par, kb = 2 * m + 1 - par;
+    const Cof<float> a = cofactors(load19<float>(th, N, i, j, ka), ih2);
+    const Nb19<float> ev = load19<float>(src, N, i, j, ka);
+    const float Je = jac_apply(a, ev, ih2);
+    const float diag = -2.0f * (a.xx + a.yy + a.zz) * ih2;
+    dst[offs(N, i, j, ka)] = ev.c + (f[offs(N, i, j, ka)] - Je) / diag;
+    dst[offs(N, i, j, kb)] = src[offs(N, i, j, kb)];
+}
+
+static cudaError_t lin_sweep(int N, double h, float *e, const float *f, const float *th,
+                             int sweeps, float *work, cudaStream_t s)
+{
+    const size_t npairs = (size_t)N * N * (N / 2);
+    const float ih2 = (float)(1.0 / (h * h));
+    for (int it = 0; it < sweeps; ++it) {
+        note_launch();
+        k_lin_pass<<<blocks_for(npairs), kThreads, 0, s>>>(e, work, f, th, N, ih2, 0);
+        note_launch();
+        k_lin_pass<<<blocks_for(npairs), kThreads, 0, s>>>(work, e, f, th, N, ih2, 1);
+    }
+    return cudaGetLastError();
+}
+
+// fH = R (f - J e), block partial sums for the mean projection.
+__global__ void __launch_bounds__(kThreads)
+k_lin_restrict_residual(const float *__restrict__ e, const float *__restrict__ f,
+                        const float *__restrict__ th, int Nf, float ih2, float *__restrict__ fH,
+                        double *__restrict__ partials)
+{
+    __shared__ double sh[32];
+    const int Nc = Nf >> 1;
+    const size_t nc = (size_t)Nc * Nc * Nc;
+    double sacc = 0.0;
+    for (size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x; id < nc;
+         id += (size_t)gridDim.x * blockDim.x) {
+        const int K = (int)(id % Nc);
+        const size_t q = id / Nc;
+        const int J = (int)(q % Nc), I = (int)(q / Nc);
+        float acc = 0.0f;
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b)
+                for (int cc = 0; cc < 2; ++cc) {
+                    const int i = 2 * I + a, j = 2 * J + b, k = 2 * K + cc;
+                    const Cof<float> co = cofactors(load19<float>(th, Nf, i, j, k), ih2);
+                    acc += f[offs(Nf, i, j, k)] - jac_apply(co, load19<float>(e, Nf, i, j, k), ih2);
+                }
+        const float v = acc * 0.125f;
+        fH[id] = v;
+        sacc += (double)v;
+    }
+    const double v = block_sum<kThreads>(sacc, sh);
+    if (threadIdx.x == 0) partials[4 * blockIdx.x + 0] = v;
+}
+
+__global__ void __launch_bounds__(kCoarseThreads)
+k_lin_coarse(float *e, float *work, const float *f, const float *th, int N, float ih2,
+             int max_sweeps, double rtol)
+{
+    __shared__ double sh[32];
+    __shared__ double sval;
+    const int n = N * N * N, half = N >> 1, npairs = N * N * half;
+    auto proj_rms = [&]() -> double {
+        double sr = 0.0;
+        for (int id = threadIdx.x; id < n; id += blockDim.x) {
+            const int k = id % N, j = (id / N) % N, i = id / (N * N);
+            const Cof<float> co = cofactors(load19<float>(th, N, i, j, k), ih2);
+            const float r = f[id] - jac_apply(co, load19<float>(e, N, i, j, k), ih2);
+            work[id] = r;
+            sr += (double)r;
+        }
+        double tot = block_sum<kCoarseThreads>(sr, sh);
+        if (threadIdx.x == 0) sval = tot / n;
+        __syncthreads();
+        const double m = sval;
+        double s2 = 0.0;
+        for (int id = threadIdx.x; id < n; id += blockDim.x) {
+            const double d = (double)work[id] - m;
+            s2 += d * d;
+        }
+        tot = block_sum<kCoarseThreads>(s2, sh);
+        if (threadIdx.x == 0) sval = sqrt(tot / n);
+        __syncthreads();
+        const double v = sval;
+        __syncthreads();
+        return v;
+    };
+    const double r0 = proj_rms();
+    for (int sw = 0; sw < max_sweeps; ++sw) {
+        for (int colour = 0; colour < 2; ++colour) {
+            const float *src = colour == 0 ? e : work;
+            float *dst = colour == 0 ? work : e;
+            for (int pi = threadIdx.x; pi < npairs; pi += blockDim.x) {
+                const int m = pi % half, r = pi / half;
+                const int j = r % N, i = r / N;
+                const int par = (colour + i + j) & 1;
+                const int ka = 2 * m + par, kb = 2 * m + 1 - par;
+                const Cof<float> a = cofactors(load19<float>(th, N, i, j, ka), ih2);
+                const Nb19<float> ev = load19<float>(src, N, i, j, ka);
+                const float Je = jac_apply(a, ev, ih2);
+                const float diag = -2.0f * (a.xx + a.yy + a.zz) * ih2;
+                const float vnew = ev.c + (f[offs(N, i, j, ka)] - Je) / diag;
+                const float vcopy = src[offs(N, i, j, kb)];
+                dst[offs(N, i, j, ka)] = vnew;
+                dst[offs(N, i, j, kb)] = vcopy;
+            }
+            __syncthreads();
+        }
+        if (proj_rms() <= rtol * r0) break;
+    }
+}
+
+// ======================================================================
+// drivers
+// ======================================================================
+namespace {
+
+template <typename T>
+struct Hier {
+    T **t, **g, **told, **aux;
+    T *work;
+};
+
+Hier<double> hier64(recon_handle *H)
+{
+    return {H->t64, H->g64, H->told64, H->aux64, H->work64};
+}
+Hier<float> hier32(recon_handle *H)
+{
+    return {H->t32, H->g32, H->told32, H->aux32, H->work32};
+}
+
+inline size_t ncell(int N) { return (size_t)N * N * N; }
+
+#define CK(expr)                                                                   \
+    do {                                                                           \
+        cudaError_t e_ = (expr);                                                   \
+        if (e_ != cudaSuccess) return e_;                                          \
+    } while (0)
+
+// FAS V-cycle from level l (Sec. II.A.3).
+template <typename T>
+cudaError_t vcycle(recon_handle *H, const Hier<T> &Y, int l, const double *cptr)
+{
+    cudaStream_t s = H->stream;
+    const recon_config &cf = H->cfg;
+    const int N = H->Nl[l];
+    const double h = H->hl[l];
+    if (l == H->nlev - 1)
+        return coarse_solve<T>(N, h, cf.rule, Y.t[l], Y.g[l], cptr, 0.0, cf.coarse_max_sweeps,
+                               cf.coarse_rtol, Y.work, nullptr, s);
+    CK(sweep<T>(N, h, cf.rule, Y.t[l], Y.g[l], cptr, 0.0, cf.nu1, Y.work, s));
+
+    const int Nc = H->Nl[l + 1];
+    const size_t nc = ncell(Nc);
+    const unsigned nbr = red_blocks(nc);
+    note_launch();
+    k_restrict_residual<T><<<nbr, kThreads, 0, s>>>(Y.t[l], Y.g[l], cptr, N, (T)(1.0 / (h * h)),
+                                                    Y.t[l + 1], Y.told[l + 1], Y.g[l + 1],
+                                                    H->partials);
+    note_launch();
+    k_finalize_mean<<<1, kReduceThreads, 0, s>>>(H->partials, nbr, (double)nc,
+                                                 H->scal + slot_rmean(l + 1));
+    const double hc = H->hl[l + 1];
+    note_launch();
+    k_coarse_rhs<T><<<nbr, kThreads, 0, s>>>(Y.t[l + 1], Y.g[l + 1], Y.aux[l + 1],
+                                             H->scal + slot_rmean(l + 1), Nc,
+                                             (T)(1.0 / (hc * hc)), cf.scale_floor, H->partials);
+    note_launch();
+    k_finalize_scale<<<1, kReduceThreads, 0, s>>>(H->partials, nbr, cf.scale_floor,
+                                                  H->scal + slot_scale(l + 1),
+                                                  H->scal + slot_pscale(l + 1));
+    note_launch();
+    k_form_rhs<T><<<blocks_for(nc), kThreads, 0, s>>>(Y.g[l + 1], Y.aux[l + 1], nc,
+                                                      H->scal + slot_scale(l + 1));
+    CK(cudaGetLastError());
+    CK(vcycle<T>(H, Y, l + 1, H->scal + S_ZERO));
+    CK(prolong_add<T>(Nc, Y.t[l + 1], Y.told[l + 1], H->scal + slot_pscale(l + 1), 1.0,
+                      Y.t[l], s));
+    return sweep<T>(N, h, cf.rule, Y.t[l], Y.g[l], cptr, 0.0, cf.nu2, Y.work, s);
+}
+
+// residual norms of level l, then c -= mean r, rel, and theta -= mean theta.
+template <typename T>
+cudaError_t compat_gauge(recon_handle *H, const Hier<T> &Y, int l)
+{
+    cudaStream_t s = H->stream;
+    const int N = H->Nl[l];
+    const size_t n = ncell(N);
+    const unsigned nbr = red_blocks(n);
+    const double h = H->hl[l];
+    note_launch();
+    k_residual_norms<T><<<nbr, kThreads, 0, s>>>(Y.t[l], Y.g[l], H->scal + S_C, N,
+                                                 (T)(1.0 / (h * h)), H->partials, nullptr,
+                                                 nullptr);
+    note_launch();
+    k_finalize_cycle<<<1, kReduceThreads, 0, s>>>(H->partials, nbr, (double)n, H->scal);
+    note_launch();
+    k_gauge<T><<<blocks_for(n), kThreads, 0, s>>>(Y.t[l], n, H->scal);
+    return cudaGetLastError();
+}
+
+// Nested iteration: restrict b to every level, solve the coarsest from 0,
+// prolong up with one V-cycle per level; leaves the prolonged start on level 0.
+template <typename T>
+cudaError_t fmg_start(recon_handle *H, const Hier<T> &Y)
+{
+    cudaStream_t s = H->stream;
+    const int lc = H->nlev - 1;
+    for (int l = 1; l <= lc; ++l) CK(restrict_plain<T>(H->Nl[l - 1], Y.g[l - 1], Y.g[l], s));
+    CK(cudaMemsetAsync(Y.t[lc], 0, sizeof(T) * ncell(H->Nl[lc]), s));
+    CK(cudaMemsetAsync(H->scal + S_C, 0, sizeof(double), s));
+    CK(vcycle<T>(H, Y, lc, H->scal + S_C));
+    CK(compat_gauge<T>(H, Y, lc));
+    for (int l = lc - 1; l >= 0; --l) {
+        CK(cudaMemsetAsync(Y.t[l], 0, sizeof(T) * ncell(H->Nl[l]), s));
+        CK(prolong_add<T>(H->Nl[l + 1], Y.t[l + 1], (const T *)nullptr, nullptr, 1.0, Y.t[l], s));
+        if (l == 0) break;
+        CK(vcycle<T>(H, Y, l, H->scal + S_C));
+        CK(compat_gauge<T>(H, Y, l));
+    }
+    return cudaSuccess;
+}
+
+cudaError_t read_scalars(recon_handle *H)
+{
+    CK(cudaMemcpyAsync(H->hscal, H->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost,
+                       H->stream));
+    return cudaStreamSynchronize(H->stream);
+}
+
+recon_status fail_cuda(recon_handle *H, cudaError_t e, const char *where)
+{
+    H->err = std::string(where) + ": " + cudaGetErrorString(e);
+    return RECON_E_CUDA;
+}
+
+double now_s()
+{
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+void hist_push(recon_stats *st, double v)
+{
+    if (st && st->n_history < RECON_HISTORY_MAX) st->history[st->n_history++] = v;
+}
+
+}  // namespace
+
+recon_status check_domain(recon_handle *H, const double *b)
+{
+    const size_t n = ncell(H->N);
+    const unsigned nbr = red_blocks(n);
+    note_launch();
+    k_b_stats<<<nbr, kThreads, 0, H->stream>>>(b, n, H->partials);
+    note_launch();
+    k_finalize_b<<<1, kReduceThreads, 0, H->stream>>>(H->partials, nbr, H->scal);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = read_scalars(H);
+    if (e != cudaSuccess) return fail_cuda(H, e, "domain check");
+    if (H->hscal[S_BBAD] > 0.0) {
+        H->err = "b has non-finite entries";
+        return RECON_E_DOMAIN;
+    }
+    if (!(H->hscal[S_BMIN] > 0.0)) {
+        H->err = "b must be > 0 everywhere (min(b) = " + std::to_string(H->hscal[S_BMIN]) + ")";
+        return RECON_E_DOMAIN;
+    }
+    return RECON_OK;
+}
+
+// ---------------------------------------------------------------- FP64
+recon_status solve_f64(recon_handle *H, const double *b, double *phi, double tol,
+                       int max_cycles, recon_stats *st)
+{
+    const double t0 = now_s();
+    H->t64[0] = phi;
+    H->g64[0] = const_cast<double *>(b);
+    const Hier<double> Y = hier64(H);
+    cudaError_t e = cudaSuccess;
+    if (H->cfg.start == RECON_START_FMG) e = fmg_start<double>(H, Y);
+    else e = cudaMemsetAsync(H->scal + S_C, 0, sizeof(double), H->stream);
+    if (e != cudaSuccess) return fail_cuda(H, e, "fmg start");
+
+    const size_t n = ncell(H->N);
+    recon_status status = RECON_E_NOCONV;
+    double best = INFINITY;
+    int cyc = 0;
+    for (cyc = 1; cyc <= max_cycles; ++cyc) {
+        e = vcycle<double>(H, Y, 0, H->scal + S_C);
+        if (e == cudaSuccess) e = compat_gauge<double>(H, Y, 0);
+        if (e == cudaSuccess) e = read_scalars(H);
+        if (e != cudaSuccess) return fail_cuda(H, e, "V-cycle");
+        const double rel = H->hscal[S_REL];
+        hist_push(st, rel);
+        (void)n;
+        if (!std::isfinite(rel) || rel > 1e3 * best) {
+            H->err = "residual diverged";
+            status = RECON_E_DIVERGED;
+            break;
+        }
+        best = rel < best ? rel : best;
+        if (rel < tol) {
+            status = RECON_OK;
+            break;
+        }
+    }
+    if (cyc > max_cycles) cyc = max_cycles;
+    if (status == RECON_E_NOCONV) H->err = "max_cycles reached before the tolerance";
+    if (st) {
+        st->cycles = cyc;
+        st->outer_iterations = 0;
+        st->rel_residual = H->hscal[S_REL];
+        st->compat_c = H->hscal[S_C];
+        st->seconds = now_s() - t0;
+    }
+    return status;
+}
+
+// ---------------------------------------------------------------- MIXED
+// (i) FP32 FAS (same cycle as above) until the FP32 residual reaches
+//     mixed_switch_rtol, stagnates, or mixed_fas_max_cycles ran;
+// (ii) defect correction: r64 = b + c - det(I + H phi) in FP64, then
+//     mixed_linear_vcycles FP32 linear V-cycles on J(phi) e = r64 - mean,
+//     phi += e, until ||r64 - mean|| / ||b - 1|| < tol.
+namespace {
+
+cudaError_t lin_vcycle(recon_handle *H, int l)
+{
+    cudaStream_t s = H->stream;
+    const recon_config &cf = H->cfg;
+    const int N = H->Nl[l];
+    const double h = H->hl[l];
+    const float ih2 = (float)(1.0 / (h * h));
+    if (l == H->nlev - 1) {
+        note_launch();
+        k_lin_coarse<<<1, kCoarseThreads, 0, s>>>(H->e32[l], H->work32, H->f32[l], H->t32[l], N,
+                                                  ih2, cf.coarse_max_sweeps, cf.coarse_rtol);
+        return cudaGetLastError();
+    }
+    CK(lin_sweep(N, h, H->e32[l], H->f32[l], H->t32[l], cf.nu1, H->work32, s));
+    const int Nc = H->Nl[l + 1];
+    const size_t nc = ncell(Nc);
+    const unsigned nbr = red_blocks(nc);
+    note_launch();
+    k_lin_restrict_residual<<<nbr, kThreads, 0, s>>>(H->e32[l], H->f32[l], H->t32[l], N, ih2,
+                                                     H->f32[l + 1], H->partials);
+    note_launch();
+    k_finalize_mean<<<1, kReduceThreads, 0, s>>>(H->partials, nbr, (double)nc,
+                                                 H->scal + slot_rmean(l + 1));
+    note_launch();
+    k_sub_scalar<<<blocks_for(nc), kThreads, 0, s>>>(H->f32[l + 1], nc, H->scal + slot_rmean(l + 1));
+    CK(cudaMemsetAsync(H->e32[l + 1], 0, sizeof(float) * nc, s));
+    CK(lin_vcycle(H, l + 1));
+    CK(prolong_add<float>(Nc, H->e32[l + 1], (const float *)nullptr, nullptr, 1.0, H->e32[l], s));
+    return lin_sweep(N, h, H->e32[l], H->f32[l], H->t32[l], cf.nu2, H->work32, s);
+}
+
+}  // namespace
+
+recon_status solve_mixed(recon_handle *H, const double *b, double *phi, double tol,
+                         int max_cycles, recon_stats *st)
+{
+    const double t0 = now_s();
+    cudaStream_t s = H->stream;
+    const recon_config &cf = H->cfg;
+    const size_t n = ncell(H->N);
+    const Hier<float> Y = hier32(H);
+    cudaError_t e = cudaSuccess;
+
+    // ---- (i) FP32 FAS
+    note_launch();
+    k_to_float<<<blocks_for(n), kThreads, 0, s>>>(b, H->g32[0], n);
+    if (cf.start == RECON_START_FMG) {
+        e = fmg_start<float>(H, Y);
+    } else {
+        note_launch();
+        k_to_float<<<blocks_for(n), kThreads, 0, s>>>(phi, H->t32[0], n);
+        e = cudaMemsetAsync(H->scal + S_C, 0, sizeof(double), s);
+    }
+    if (e != cudaSuccess) return fail_cuda(H, e, "mixed start");
+    int fas = 0;
+    double prev = INFINITY;
+    for (fas = 1; fas <= cf.mixed_fas_max_cycles; ++fas) {
+        e = vcycle<float>(H, Y, 0, H->scal + S_C);
+        if (e == cudaSuccess) e = compat_gauge<float>(H, Y, 0);
+        if (e == cudaSuccess) e = read_scalars(H);
+        if (e != cudaSuccess) return fail_cuda(H, e, "FP32 V-cycle");
+        const double rel = H->hscal[S_REL];
+        hist_push(st, rel);
+        if (!std::isfinite(rel)) {
+            H->err = "FP32 residual diverged";
+            return RECON_E_DIVERGED;
+        }
+        if (rel < cf.mixed_switch_rtol || rel > 0.7 * prev) break;
+        prev = rel;
+    }
+    if (fas > cf.mixed_fas_max_cycles) fas = cf.mixed_fas_max_cycles;
+    note_launch();
+    k_to_double<<<blocks_for(n), kThreads, 0, s>>>(H->t32[0], phi, n);
+
+    // ---- (ii) FP64 defect correction with FP32 linear multigrid
+    const unsigned nbr = red_blocks(n);
+    const double ih2 = 1.0 / (H->h * H->h);
+    recon_status status = RECON_E_NOCONV;
+    double best = INFINITY;
+    int o = 0;
+    for (o = 1; o <= max_cycles; ++o) {
+        note_launch();
+        k_residual_norms<double><<<nbr, kThreads, 0, s>>>(phi, b, H->scal + S_C, H->N, ih2,
+                                                          H->partials, H->f32[0], H->t32[0]);
+        note_launch();
+        k_finalize_cycle<<<1, kReduceThreads, 0, s>>>(H->partials, nbr, (double)n, H->scal);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = read_scalars(H);
+        if (e != cudaSuccess) return fail_cuda(H, e, "FP64 residual");
+        const double rel = H->hscal[S_REL];
+        hist_push(st, rel);
+        if (!std::isfinite(rel) || rel > 1e3 * best) {
+            H->err = "residual diverged";
+            status = RECON_E_DIVERGED;
+            break;
+        }
+        best = rel < best ? rel : best;
+        if (rel < tol) {
+            note_launch();
+            k_gauge<double><<<blocks_for(n), kThreads, 0, s>>>(phi, n, H->scal);
+            status = RECON_OK;
+            break;
+        }
+        note_launch();
+        k_sub_scalar<<<blocks_for(n), kThreads, 0, s>>>(H->f32[0], n, H->scal + S_MEAN_R);
+        for (int l = 1; l < H->nlev; ++l) {
+            e = restrict_plain<float>(H->Nl[l - 1], H->t32[l - 1], H->t32[l], s);
+            if (e != cudaSuccess) return fail_cuda(H, e, "theta hierarchy");
+        }
+        e = cudaMemsetAsync(H->e32[0], 0, sizeof(float) * n, s);
+        for (int v = 0; v < cf.mixed_linear_vcycles && e == cudaSuccess; ++v) e = lin_vcycle(H, 0);
+        if (e != cudaSuccess) return fail_cuda(H, e, "linear V-cycle");
+        note_launch();
+        k_update_theta<<<blocks_for(n), kThreads, 0, s>>>(phi, H->e32[0], n, H->scal);
+    }
+    if (o > max_cycles) o = max_cycles;
+    if (status == RECON_E_NOCONV) H->err = "max_cycles reached before the tolerance";
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail_cuda(H, e, "mixed solve");
+    if (st) {
+        st->cycles = fas;
+        st->outer_iterations = o;
+        st->rel_residual = H->hscal[S_REL];
+        st->compat_c = H->hscal[S_C];
+        st->seconds = now_s() - t0;
+    }
+    return status;
+}
+
+}  // namespace recon

@@ -1,0 +1,338 @@
+"""Thin Python binding of librecon (include/recon.h, include/recon_steps.h).
+
+Argument marshalling only: every function forwards device pointers of torch
+CUDA tensors to the C ABI and raises ``ReconError`` on a non-OK status.  No
+computation happens here, and there is no CPU fallback: without a built
+``librecon.so`` (``paper_1709_06350_gb300.build.build()``) every call raises.
+
+The function names follow the C ABI (``recon_create`` ...); ``Solver`` wraps a
+handle for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "librecon.so")
+
+RECON_F64, RECON_MIXED = 0, 1
+RULE_NEWTON1, RULE_EXACT = 0, 1
+START_FMG, START_GUESS = 0, 1
+STATUS = {0: "RECON_OK", 1: "RECON_E_INVALID", 2: "RECON_E_DOMAIN", 3: "RECON_E_NOCONV",
+          4: "RECON_E_DIVERGED", 5: "RECON_E_CUDA", 6: "RECON_E_OOM", 7: "RECON_E_TIMEOUT",
+          8: "RECON_E_UNIMPLEMENTED"}
+HISTORY_MAX = 64
+
+_lock = threading.Lock()
+_lib = None
+
+
+class ReconError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class recon_config(ctypes.Structure):
+    _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
+                ("coarse_max_sweeps", ctypes.c_int), ("coarse_rtol", ctypes.c_double),
+                ("rule", ctypes.c_int), ("start", ctypes.c_int),
+                ("scale_floor", ctypes.c_double), ("mixed_switch_rtol", ctypes.c_double),
+                ("mixed_fas_max_cycles", ctypes.c_int), ("mixed_linear_vcycles", ctypes.c_int)]
+
+
+class recon_stats(ctypes.Structure):
+    _fields_ = [("cycles", ctypes.c_int), ("outer_iterations", ctypes.c_int),
+                ("rel_residual", ctypes.c_double), ("compat_c", ctypes.c_double),
+                ("seconds", ctypes.c_double), ("n_history", ctypes.c_int),
+                ("history", ctypes.c_double * HISTORY_MAX)]
+
+    def as_dict(self):
+        return dict(cycles=self.cycles, outer_iterations=self.outer_iterations,
+                    rel_residual=self.rel_residual, compat_c=self.compat_c,
+                    seconds=self.seconds, history=list(self.history[:self.n_history]))
+
+
+_P, _I, _D, _LL = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+_SIGS = {
+    "recon_create": (_I, [_I, _D, _I, ctypes.POINTER(_P)]),
+    "recon_destroy": (None, [_P]),
+    "recon_workspace_bytes": (ctypes.c_size_t, [_I, _I]),
+    "recon_set_stream": (_I, [_P, _P]),
+    "recon_get_config": (_I, [_P, ctypes.POINTER(recon_config)]),
+    "recon_set_config": (_I, [_P, ctypes.POINTER(recon_config)]),
+    "recon_deposit_cic": (_I, [_P, _P, _LL, _D, _P]),
+    "recon_solve": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(recon_stats)]),
+    "recon_displace": (_I, [_P, _P, _P, _P, _P]),
+    "recon_adjoint": (_I, [_P, _P, _P]),
+    "recon_last_error": (ctypes.c_char_p, [_P]),
+    "recon_status_string": (ctypes.c_char_p, [_I]),
+    "recon_kernel_launches": (ctypes.c_ulonglong, []),
+    "recon_step_sweep": (_I, [_I, _D, _I, _I, _P, _P, _D, _I, _P, _P]),
+    "recon_step_residual": (_I, [_I, _D, _P, _P, _D, _P, _P]),
+    "recon_step_det": (_I, [_I, _D, _P, _P, _P]),
+    "recon_step_restrict": (_I, [_I, _I, _P, _P, _P]),
+    "recon_step_prolong_add": (_I, [_I, _I, _P, _P, _D, _P, _P]),
+    "recon_step_coarse_solve": (_I, [_I, _D, _I, _I, _P, _P, _D, _I, _D, _P, _P, _P]),
+    "recon_step_cic_cells": (_I, [_P, _LL, _I, _D, _P, _P, _P]),
+    "recon_step_jacobian_apply": (_I, [_I, _D, _P, _P, _P, _P]),
+}
+EXPORTS = tuple(_SIGS)
+
+
+def load():
+    """Load librecon.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "paper_1709_06350_gb300.build.build() (no CPU fallback exists)")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+# ---------------------------------------------------------------- marshalling
+def _dev_ptr(t, dtype=None, numel=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"expected dtype {dtype}, got {t.dtype}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"expected {numel} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check(status, handle=None):
+    if status != 0:
+        msg = load().recon_last_error(handle)
+        raise ReconError(status, (msg or b"").decode())
+
+
+# ---------------------------------------------------------------- C ABI, 1:1
+def recon_create(N: int, L: float, dtype: int = RECON_F64):
+    h = ctypes.c_void_p()
+    _check(load().recon_create(int(N), float(L), int(dtype), ctypes.byref(h)), None)
+    return h
+
+
+def recon_destroy(h) -> None:
+    load().recon_destroy(h)
+
+
+def recon_workspace_bytes(N: int, dtype: int = RECON_F64) -> int:
+    return int(load().recon_workspace_bytes(int(N), int(dtype)))
+
+
+def recon_set_stream(h, stream=None) -> None:
+    _check(load().recon_set_stream(h, _stream(stream)), h)
+
+
+def recon_get_config(h) -> recon_config:
+    c = recon_config()
+    _check(load().recon_get_config(h, ctypes.byref(c)), h)
+    return c
+
+
+def recon_set_config(h, cfg: recon_config) -> None:
+    _check(load().recon_set_config(h, ctypes.byref(cfg)), h)
+
+
+def recon_deposit_cic(h, N: int, pos, mass: float, rho) -> None:
+    import torch
+    n = pos.numel() // 3
+    _check(load().recon_deposit_cic(h, _dev_ptr(pos, torch.float64) if n else None, n,
+                                    float(mass), _dev_ptr(rho, torch.float64, N ** 3)), h)
+
+
+def recon_solve(h, N: int, b, phi, tol: float, max_cycles: int, raise_on_noconv=True):
+    import torch
+    st = recon_stats()
+    status = load().recon_solve(h, _dev_ptr(b, torch.float64, N ** 3),
+                                _dev_ptr(phi, torch.float64, N ** 3), float(tol),
+                                int(max_cycles), ctypes.byref(st))
+    if status == 3 and not raise_on_noconv:
+        return status, st.as_dict()
+    _check(status, h)
+    return status, st.as_dict()
+
+
+def recon_displace(h, N: int, phi, b, psi, deltaL) -> None:
+    import torch
+    _check(load().recon_displace(h, _dev_ptr(phi, torch.float64, N ** 3),
+                                 _dev_ptr(b, torch.float64, N ** 3),
+                                 _dev_ptr(psi, torch.float64, 3 * N ** 3),
+                                 _dev_ptr(deltaL, torch.float64, N ** 3)), h)
+
+
+def recon_adjoint(h, N: int, gbar_phi, gbar_b) -> None:
+    import torch
+    _check(load().recon_adjoint(h, _dev_ptr(gbar_phi, torch.float64, N ** 3),
+                                _dev_ptr(gbar_b, torch.float64, N ** 3)), h)
+
+
+def recon_kernel_launches() -> int:
+    return int(load().recon_kernel_launches())
+
+
+# ---------------------------------------------------------------- steps
+def _prec(t):
+    import torch
+    if t.dtype == torch.float64:
+        return 0
+    if t.dtype == torch.float32:
+        return 1
+    raise TypeError("grids must be float64 or float32")
+
+
+def recon_step_sweep(theta, g, c, h, sweeps=1, rule=RULE_NEWTON1, work=None, stream=None):
+    import torch
+    N = theta.shape[0]
+    work = torch.empty_like(theta) if work is None else work
+    _check(load().recon_step_sweep(N, float(h), _prec(theta), int(rule), _dev_ptr(theta, theta.dtype),
+                                   _dev_ptr(g, theta.dtype, theta.numel()), float(c), int(sweeps),
+                                   _dev_ptr(work, theta.dtype, theta.numel()), _stream(stream)))
+
+
+def recon_step_residual(theta, g, c, h, r, stream=None):
+    import torch
+    N = theta.shape[0]
+    _check(load().recon_step_residual(N, float(h), _dev_ptr(theta, torch.float64),
+                                      _dev_ptr(g, torch.float64, N ** 3), float(c),
+                                      _dev_ptr(r, torch.float64, N ** 3), _stream(stream)))
+
+
+def recon_step_det(theta, h, out, stream=None):
+    import torch
+    N = theta.shape[0]
+    _check(load().recon_step_det(N, float(h), _dev_ptr(theta, torch.float64),
+                                 _dev_ptr(out, torch.float64, N ** 3), _stream(stream)))
+
+
+def recon_step_restrict(fine, coarse, stream=None):
+    Nf = fine.shape[0]
+    _check(load().recon_step_restrict(Nf, _prec(fine), _dev_ptr(fine, fine.dtype),
+                                      _dev_ptr(coarse, fine.dtype, (Nf // 2) ** 3), _stream(stream)))
+
+
+def recon_step_prolong_add(cnew, cold, fine, scale=1.0, stream=None):
+    Nc = cnew.shape[0]
+    _check(load().recon_step_prolong_add(
+        Nc, _prec(cnew), _dev_ptr(cnew, cnew.dtype),
+        _dev_ptr(cold, cnew.dtype, Nc ** 3) if cold is not None else None, float(scale),
+        _dev_ptr(fine, cnew.dtype, 8 * Nc ** 3), _stream(stream)))
+
+
+def recon_step_coarse_solve(theta, g, c, h, max_sweeps=200, rtol=1e-3, rule=RULE_NEWTON1,
+                            stream=None):
+    """Returns the number of sweeps done (synchronises to read it)."""
+    import torch
+    N = theta.shape[0]
+    work = torch.empty_like(theta)
+    done = torch.zeros(1, dtype=torch.int32, device=theta.device)
+    _check(load().recon_step_coarse_solve(N, float(h), _prec(theta), int(rule),
+                                          _dev_ptr(theta, theta.dtype),
+                                          _dev_ptr(g, theta.dtype, N ** 3), float(c),
+                                          int(max_sweeps), float(rtol),
+                                          _dev_ptr(work, theta.dtype, N ** 3),
+                                          _dev_ptr(done, torch.int32), _stream(stream)))
+    return int(done.item())
+
+
+def recon_step_cic_cells(pos, N, L, cells, frac, stream=None):
+    import torch
+    n = pos.numel() // 3
+    _check(load().recon_step_cic_cells(_dev_ptr(pos, torch.float64), n, int(N), float(L),
+                                       _dev_ptr(cells, torch.int32, 3 * n),
+                                       _dev_ptr(frac, torch.float64, 3 * n), _stream(stream)))
+
+
+def recon_step_jacobian_apply(theta, v, h, out, stream=None):
+    import torch
+    N = theta.shape[0]
+    _check(load().recon_step_jacobian_apply(N, float(h), _dev_ptr(theta, torch.float64),
+                                            _dev_ptr(v, torch.float64, N ** 3),
+                                            _dev_ptr(out, torch.float64, N ** 3),
+                                            _stream(stream)))
+
+
+# ---------------------------------------------------------------- convenience
+class Solver:
+    """One librecon handle (N^3 grid of side L, FP64 or MIXED)."""
+
+    def __init__(self, N: int, L: float, dtype: int = RECON_F64, stream=None, **config):
+        self.N, self.L, self.dtype = int(N), float(L), int(dtype)
+        self.h = recon_create(self.N, self.L, self.dtype)
+        recon_set_stream(self.h, stream)
+        if config:
+            self.configure(**config)
+
+    def configure(self, **kw):
+        c = recon_get_config(self.h)
+        for k, v in kw.items():
+            if not hasattr(c, k):
+                raise KeyError(k)
+            setattr(c, k, v)
+        recon_set_config(self.h, c)
+        return self
+
+    def config(self) -> dict:
+        c = recon_get_config(self.h)
+        return {name: getattr(c, name) for name, _ in c._fields_}
+
+    def deposit_cic(self, pos, mass=None, rho=None):
+        import torch
+        n = pos.numel() // 3
+        if rho is None:
+            rho = torch.zeros((self.N,) * 3, dtype=torch.float64, device=pos.device)
+        m = float(self.N) ** 3 / max(n, 1) if mass is None else float(mass)
+        recon_deposit_cic(self.h, self.N, pos, m, rho)
+        return rho
+
+    def solve(self, b, phi=None, tol=1e-8, max_cycles=50, raise_on_noconv=True):
+        import torch
+        if phi is None:
+            phi = torch.zeros_like(b)
+        _, stats = recon_solve(self.h, self.N, b, phi, tol, max_cycles, raise_on_noconv)
+        return phi, stats
+
+    def displace(self, phi, b):
+        import torch
+        psi = torch.empty((3,) + tuple(phi.shape), dtype=torch.float64, device=phi.device)
+        dl = torch.empty_like(phi)
+        recon_displace(self.h, self.N, phi, b, psi, dl)
+        return psi, dl
+
+    def adjoint(self, gbar_phi):
+        import torch
+        out = torch.empty_like(gbar_phi)
+        recon_adjoint(self.h, self.N, gbar_phi, out)
+        return out
+
+    def close(self):
+        if self.h is not None:
+            recon_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

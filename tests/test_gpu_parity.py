@@ -1,0 +1,236 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: FP64 steps agree to 1e-12 relative (only the order of rounding
+differs); index work (restriction sums, CIC cells) is bit-exact; a full FP64
+solve agrees to 1e-10 relative L2 and a MIXED solve to 1e-6 (both converge to
+the same discrete solution; the bound is the stated target of each path).
+"""
+import numpy as np
+import pytest
+
+from tests.workloads import smooth_density, zeldovich_density
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def R():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1709_06350_gb300 import build, recon
+    build.build()
+    recon.load()
+    return recon
+
+
+def dev(a, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.double().cpu().numpy()
+
+
+def rel_max(a, b):
+    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+
+
+def rel_l2(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+# ------------------------------------------------------------------ steps
+@pytest.mark.parametrize("N", [4, 6, 10, 48])
+@pytest.mark.parametrize("rule", ["newton1", "exact"])
+def test_sweep_parity(R, O, N, rule):
+    L = 1.5 * N
+    h = L / N
+    from paper_1709_06350_gb300 import synth
+    t0 = synth.smooth_field(N, 3, 0.4 * h * h, kmax=2)
+    g = smooth_density(N, 4, 0.8)
+    c = 0.013
+    ref = O.sweep(t0, g, c, h, rule=rule, sweeps=3)
+    th = dev(t0)
+    R.recon_step_sweep(th, dev(g), c, h, sweeps=3, rule=R.RULE_EXACT if rule == "exact" else R.RULE_NEWTON1)
+    assert rel_max(host(th), ref) < 1e-12
+
+
+def test_sweep_fp32_tracks_fp64(R, O):
+    N, L = 32, 32.0
+    h = L / N
+    from paper_1709_06350_gb300 import synth
+    t0 = synth.smooth_field(N, 5, 0.3, kmax=2)
+    g = smooth_density(N, 6, 0.8)
+    ref = O.sweep(t0, g, 0.0, h, sweeps=2)
+    th = dev(t0, torch.float32)
+    R.recon_step_sweep(th, dev(g, torch.float32), 0.0, h, sweeps=2)
+    assert rel_max(host(th), ref) < 1e-4
+
+
+@pytest.mark.parametrize("N", [4, 12, 48])
+def test_residual_det_jacobian_parity(R, O, N):
+    L = 2.0 * N
+    h = L / N
+    from paper_1709_06350_gb300 import synth
+    t = synth.smooth_field(N, 7, 0.5 * h * h, kmax=3)
+    g = smooth_density(N, 8)
+    v = np.random.default_rng(9).standard_normal((N,) * 3)
+    out = torch.empty((N,) * 3, dtype=torch.float64, device="cuda")
+    R.recon_step_residual(dev(t), dev(g), 0.02, h, out)
+    assert np.max(np.abs(host(out) - O.residual(t, g, 0.02, h))) < 1e-13
+    R.recon_step_det(dev(t), h, out)
+    assert np.max(np.abs(host(out) - O.det_grid(t, h))) < 1e-13
+    R.recon_step_jacobian_apply(dev(t), dev(v), h, out)
+    assert rel_max(host(out), O.jacobian_apply(t, v, h)) < 1e-12
+
+
+@pytest.mark.parametrize("Nf", [4, 10, 48])
+def test_restriction_bit_exact(R, O, Nf):
+    f = np.random.default_rng(Nf).standard_normal((Nf,) * 3)
+    out = torch.empty((Nf // 2,) * 3, dtype=torch.float64, device="cuda")
+    R.recon_step_restrict(dev(f), out)
+    assert np.array_equal(host(out), O.restrict(f))
+
+
+@pytest.mark.parametrize("Nc", [2, 5, 24])
+def test_prolongation_parity(R, O, Nc):
+    rng = np.random.default_rng(Nc)
+    cn, co, fi = rng.standard_normal((Nc,) * 3), rng.standard_normal((Nc,) * 3), rng.standard_normal((2 * Nc,) * 3)
+    ref = O.prolong_add(cn, co, fi, scale=1.7)
+    out = dev(fi)
+    R.recon_step_prolong_add(dev(cn), dev(co), out, scale=1.7)
+    assert np.max(np.abs(host(out) - ref)) < 1e-14
+
+
+@pytest.mark.parametrize("N", [4, 6, 16])
+def test_coarse_solve_parity(R, O, N):
+    L = 3.0 * N
+    h = L / N
+    g = smooth_density(N, 10 + N, 0.7)
+    ref, n_ref = O.coarse_solve(np.zeros((N,) * 3), g, 0.0, h, max_sweeps=9, rtol=0.0, rule="newton1")
+    th = torch.zeros((N,) * 3, dtype=torch.float64, device="cuda")
+    n = R.recon_step_coarse_solve(th, dev(g), 0.0, h, max_sweeps=9, rtol=0.0)
+    assert n == n_ref == 9
+    assert rel_max(host(th), ref) < 1e-12
+    # to-tolerance mode: same decision on when to stop (allow one sweep)
+    ref2, n2 = O.coarse_solve(np.zeros((N,) * 3), g, 0.0, h, max_sweeps=200, rtol=1e-3)
+    th2 = torch.zeros((N,) * 3, dtype=torch.float64, device="cuda")
+    m2 = R.recon_step_coarse_solve(th2, dev(g), 0.0, h, max_sweeps=200, rtol=1e-3)
+    assert abs(m2 - n2) <= 1
+
+
+def test_cic_cells_bit_exact(R, O):
+    from paper_1709_06350_gb300 import synth
+    N, L = 32, 100.0
+    _, dh = synth.linear_field(N, L, 0.8, 77)
+    pos = synth.zeldovich_positions(dh, N, L)
+    edge = np.array([[0.0, L - 1e-13, 50.0], [L / N * 3, L / N * 0.5, 99.999999999]])
+    pos = np.concatenate([pos, edge])
+    cells_ref, frac_ref = O.cic_cells(pos, N, L)
+    cells = torch.empty(pos.shape, dtype=torch.int32, device="cuda")
+    frac = torch.empty(pos.shape, dtype=torch.float64, device="cuda")
+    R.recon_step_cic_cells(dev(pos), N, L, cells, frac)
+    torch.cuda.synchronize()
+    assert np.array_equal(cells.cpu().numpy(), cells_ref)
+    assert np.array_equal(frac.cpu().numpy(), frac_ref)
+
+
+@pytest.mark.parametrize("N,L", [(32, 100.0), (48, 96.0)])
+def test_cic_deposit_parity(R, O, N, L):
+    from paper_1709_06350_gb300 import synth
+    _, dh = synth.linear_field(N, L, 1.0, 78)
+    pos = synth.zeldovich_positions(dh, N, L)
+    ref = O.cic_deposit(pos, N, L)
+    s = R.Solver(N, L)
+    rho = s.deposit_cic(dev(pos))
+    got = host(rho)
+    assert np.max(np.abs(got - ref)) < 1e-12 * ref.max()
+    assert abs(got.sum() - N ** 3) < 1e-8
+    # empty input deposits nothing
+    empty = s.deposit_cic(torch.zeros((0, 3), dtype=torch.float64, device="cuda"))
+    assert host(empty).sum() == 0.0
+    s.close()
+
+
+# ------------------------------------------------------------------ solves
+def test_solve_delta_zero_is_exactly_zero(R):
+    N, L = 16, 64.0
+    s = R.Solver(N, L)
+    phi, st = s.solve(torch.ones((N,) * 3, dtype=torch.float64, device="cuda"), tol=1e-10)
+    assert torch.count_nonzero(phi).item() == 0 and st["compat_c"] == 0.0
+    s.close()
+
+
+@pytest.mark.parametrize("N,L,sig,Rs", [(32, 100.0, 0.5, 5.0), (48, 48.0, 1.0, 2.0)])
+def test_solve_f64_parity(R, O, N, L, sig, Rs):
+    b, _, _ = zeldovich_density(O, N, L, sig, Rs, 1000 + N)
+    ref, info = O.solve(b, L, tol=1e-10, max_cycles=40)
+    assert info["status"] == 0
+    s = R.Solver(N, L)
+    phi, st = s.solve(dev(b), tol=1e-10, max_cycles=40)
+    got = host(phi)
+    assert rel_l2(got, ref) < 1e-10
+    assert abs(st["cycles"] - info["cycles"]) <= 1
+    assert st["compat_c"] == pytest.approx(info["c"], rel=1e-6, abs=1e-13)
+    np.testing.assert_allclose(st["history"][:3], info["history"][:3], rtol=1e-6)
+    s.close()
+
+
+@pytest.mark.parametrize("N,L,sig,Rs", [(32, 100.0, 0.5, 5.0), (64, 64.0, 1.0, 2.0)])
+def test_solve_mixed_parity(R, O, N, L, sig, Rs):
+    b, _, _ = zeldovich_density(O, N, L, sig, Rs, 2000 + N)
+    ref, info = O.solve(b, L, tol=1e-10, max_cycles=40)
+    s = R.Solver(N, L, R.RECON_MIXED)
+    phi, st = s.solve(dev(b), tol=1e-10, max_cycles=30)
+    assert st["rel_residual"] < 1e-10
+    assert rel_l2(host(phi), ref) < 1e-6
+    s.close()
+
+
+def test_solve_exact_rule_and_resume(R, O):
+    N, L = 32, 64.0
+    b, _, _ = zeldovich_density(O, N, L, 0.8, 4.0, 31)
+    ref, _ = O.solve(b, L, tol=1e-11, rule="exact")
+    s = R.Solver(N, L, rule=R.RULE_EXACT)
+    phi, st = s.solve(dev(b), tol=1e-11)
+    assert rel_l2(host(phi), ref) < 1e-9
+    # resume from the answer: one cycle suffices
+    s.configure(start=R.START_GUESS)
+    phi2, st2 = s.solve(dev(b), phi=phi.clone(), tol=1e-10)
+    assert st2["cycles"] == 1
+    s.close()
+
+
+def test_solve_domain_and_limits(R):
+    N, L = 16, 16.0
+    s = R.Solver(N, L)
+    b = torch.ones((N,) * 3, dtype=torch.float64, device="cuda")
+    b[3, 4, 5] = 0.0
+    with pytest.raises(R.ReconError) as e:
+        s.solve(b)
+    assert e.value.status == 2
+    b[3, 4, 5] = float("nan")
+    with pytest.raises(R.ReconError) as e:
+        s.solve(b)
+    assert e.value.status == 2
+    b[3, 4, 5] = 1.5
+    status, st = R.recon_solve(s.h, N, b, torch.zeros_like(b), 1e-14, 1, raise_on_noconv=False)
+    assert status == 3 and st["cycles"] == 1
+    s.close()
+
+
+# ------------------------------------------------------------------ output
+def test_displace_parity(R, O):
+    N, L = 32, 64.0
+    b, _, _ = zeldovich_density(O, N, L, 0.8, 4.0, 41)
+    t, _ = O.solve(b, L, tol=1e-11)
+    psi_ref, dl_ref = O.displace(t, b, L)
+    s = R.Solver(N, L)
+    psi, dl = s.displace(dev(t), dev(b))
+    assert np.max(np.abs(host(psi) - psi_ref)) < 1e-13 * np.abs(psi_ref).max()
+    assert np.max(np.abs(host(dl) - dl_ref)) < 1e-10
+    assert host(dl).max() < 3.0
+    s.close()
