@@ -515,7 +515,8 @@ static void vcycle(or_hier *Hh, int l, double c, const or_params *P)
 /*            grid the prolonged coarse answer starts one V-cycle (with   */
 /*            its compatibility / gauge update); theta_in is ignored.     */
 /*   fmg = 0: V-cycles start from the caller's theta (0 in the paper;     */
-/*            any earlier answer to resume).                              */
+/*            any earlier answer to resume); c and the gauge are first    */
+/*            re-derived from it as after a cycle.                        */
 /* After every cycle on a grid (reading; the paper is silent):            */
 /*   r = b + c - det(theta);  c <- c - mean(r);  theta <- theta - mean.   */
 /* Stop rule: ||r - mean r||_2 / ||b - 1||_2 < tol (denominator 1 when    */
@@ -569,6 +570,10 @@ int or_solve(const double *b, int N, double L, double *theta, double *c_io,
             vcycle(&Hh, l, c, P);
             compat_and_gauge(&Hh, l, &c);
         }
+    } else {
+        /* resuming from the caller's theta: c follows from it the same way it
+         * is updated after every cycle (c <- c - mean r) */
+        compat_and_gauge(&Hh, 0, &c);
     }
 
     double denom = norm2_centered(b, n, 1.0);

@@ -845,8 +845,13 @@ recon_status solve_f64(recon_handle *H, const double *b, double *phi, double tol
     H->g64[0] = const_cast<double *>(b);
     const Hier<double> Y = hier64(H);
     cudaError_t e = cudaSuccess;
-    if (H->cfg.start == RECON_START_FMG) e = fmg_start<double>(H, Y);
-    else e = cudaMemsetAsync(H->scal + S_C, 0, sizeof(double), H->stream);
+    if (H->cfg.start == RECON_START_FMG) {
+        e = fmg_start<double>(H, Y);
+    } else {
+        // resume: c (and the gauge) follow from the initial guess, as after a cycle
+        e = cudaMemsetAsync(H->scal + S_C, 0, sizeof(double), H->stream);
+        if (e == cudaSuccess) e = compat_gauge<double>(H, Y, 0);
+    }
     if (e != cudaSuccess) return fail_cuda(H, e, "fmg start");
 
     const size_t n = ncell(H->N);
@@ -944,6 +949,7 @@ recon_status solve_mixed(recon_handle *H, const double *b, double *phi, double t
         note_launch();
         k_to_float<<<blocks_for(n), kThreads, 0, s>>>(phi, H->t32[0], n);
         e = cudaMemsetAsync(H->scal + S_C, 0, sizeof(double), s);
+        if (e == cudaSuccess) e = compat_gauge<float>(H, Y, 0);
     }
     if (e != cudaSuccess) return fail_cuda(H, e, "mixed start");
     int fas = 0;

@@ -84,7 +84,7 @@ def linear_field(N: int, L: float, sigma_lin: float, seed: int,
     amp = np.sqrt(_power(k))
     if backend == "numpy":
         dh = np.fft.rfftn(white) * amp
-        d = np.fft.irfftn(dh, s=(N, N, N))
+        d = np.fft.irfftn(dh, s=(N, N, N), axes=(0, 1, 2))
         s = sigma_lin / d.std()
         return d * s, dh * s
     import torch
@@ -106,7 +106,7 @@ def zeldovich_positions(delta_hat, N: int, L: float):
     if isinstance(delta_hat, np.ndarray):
         comps = []
         for kk in (kx, ky, kz):
-            comps.append(np.fft.irfftn(1j * kk / k2 * delta_hat, s=(N, N, N)))
+            comps.append(np.fft.irfftn(1j * kk / k2 * delta_hat, s=(N, N, N), axes=(0, 1, 2)))
         q = np.meshgrid(cell, cell, cell, indexing="ij")
         pos = np.stack([np.mod(q[d] + comps[d], L) for d in range(3)], axis=-1)
         return np.ascontiguousarray(pos.reshape(-1, 3))
@@ -134,7 +134,7 @@ def smooth_and_floor(rho, L: float, R: float, floor: float = 0.05):
     kx, ky, kz = _kgrid(N, L)
     W = np.exp(-0.5 * (kx * kx + ky * ky + kz * kz) * R * R)
     if isinstance(rho, np.ndarray):
-        b = np.fft.irfftn(np.fft.rfftn(rho) * W, s=rho.shape) if R > 0 else rho.copy()
+        b = np.fft.irfftn(np.fft.rfftn(rho) * W, s=rho.shape, axes=(0, 1, 2)) if R > 0 else rho.copy()
         b = np.maximum(b, floor)
         return b / b.mean()
     import torch
