@@ -44,6 +44,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-n", type=int, default=128)
+    p.add_argument("--kernel-only", type=int, default=0, metavar="N",
+                   help="only time the roofline kernel at N^3 (small case for profilers)")
     return p.parse_args()
 
 
@@ -160,6 +162,15 @@ def main():
 
     from paper_1709_06350_gb300 import build as pbuild
     from paper_1709_06350_gb300 import recon, synth
+
+    if args.kernel_only:
+        pbuild.build()
+        torch.cuda.set_device(0)
+        n = args.kernel_only
+        roof = kernel_roofline(recon, torch, n, float(n), torch.device("cuda", 0),
+                               torch.cuda.current_stream())
+        print(json.dumps({"kernel_only": n, **roof}), flush=True)
+        return 0
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

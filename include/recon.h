@@ -103,7 +103,7 @@ typedef struct {
 typedef struct recon_handle recon_handle;
 
 /* Create a solver for an N^3 grid of side L (Mpc/h or any length unit;
- * phi comes out in that unit squared).  N must be even and >= 4, and the
+ * phi comes out in that unit squared).  N must be even, 4 <= N <= 1024, and the
  * multigrid hierarchy (halve N while the half is even and >= 4) must end at
  * a coarsest grid of at most 16^3; L > 0.  Allocates the whole workspace
  * (recon_workspace_bytes) with cudaMalloc on the current device.

@@ -34,32 +34,35 @@ struct Nb19 {
     T xpzp, xmzm, xmzp, xpzm;  // (i+-1, j, k+-1)
 };
 
+// 32-bit offsets: grids are limited to N <= 1024 (N^3 < 2^32).
 template <typename T, typename P>
 __device__ __forceinline__ Nb19<T> load19(P a, int N, int i, int j, int k)
 {
-    const int ip = wp(i, N), im = wm(i, N), jp = wp(j, N), jm = wm(j, N);
-    const int kp = wp(k, N), km = wm(k, N);
-    Nb19<T> n;
-    n.c = a[offs(N, i, j, k)];
-    n.xp = a[offs(N, ip, j, k)];
-    n.xm = a[offs(N, im, j, k)];
-    n.yp = a[offs(N, i, jp, k)];
-    n.ym = a[offs(N, i, jm, k)];
-    n.zp = a[offs(N, i, j, kp)];
-    n.zm = a[offs(N, i, j, km)];
-    n.xpyp = a[offs(N, ip, jp, k)];
-    n.xmym = a[offs(N, im, jm, k)];
-    n.xmyp = a[offs(N, im, jp, k)];
-    n.xpym = a[offs(N, ip, jm, k)];
-    n.ypzp = a[offs(N, i, jp, kp)];
-    n.ymzm = a[offs(N, i, jm, km)];
-    n.ymzp = a[offs(N, i, jm, kp)];
-    n.ypzm = a[offs(N, i, jp, km)];
-    n.xpzp = a[offs(N, ip, j, kp)];
-    n.xmzm = a[offs(N, im, j, km)];
-    n.xmzp = a[offs(N, im, j, kp)];
-    n.xpzm = a[offs(N, ip, j, km)];
-    return n;
+    const unsigned n = (unsigned)N, nn = n * n;
+    const unsigned ri = (unsigned)i * nn, rip = (unsigned)wp(i, N) * nn, rim = (unsigned)wm(i, N) * nn;
+    const unsigned cj = (unsigned)j * n, cjp = (unsigned)wp(j, N) * n, cjm = (unsigned)wm(j, N) * n;
+    const unsigned kk = (unsigned)k, kp = (unsigned)wp(k, N), km = (unsigned)wm(k, N);
+    Nb19<T> v;
+    v.c = a[ri + cj + kk];
+    v.xp = a[rip + cj + kk];
+    v.xm = a[rim + cj + kk];
+    v.yp = a[ri + cjp + kk];
+    v.ym = a[ri + cjm + kk];
+    v.zp = a[ri + cj + kp];
+    v.zm = a[ri + cj + km];
+    v.xpyp = a[rip + cjp + kk];
+    v.xmym = a[rim + cjm + kk];
+    v.xmyp = a[rim + cjp + kk];
+    v.xpym = a[rip + cjm + kk];
+    v.ypzp = a[ri + cjp + kp];
+    v.ymzm = a[ri + cjm + km];
+    v.ymzp = a[ri + cjm + kp];
+    v.ypzm = a[ri + cjp + km];
+    v.xpzp = a[rip + cj + kp];
+    v.xmzm = a[rim + cj + km];
+    v.xmzp = a[rim + cj + kp];
+    v.xpzm = a[rip + cj + km];
+    return v;
 }
 
 // Off-diagonal Hessian entries (4-point edge stencils / (4 h^2)).

@@ -11,15 +11,16 @@
 namespace recon {
 
 // ---------------------------------------------------------------- grid
-// C order [i][j][k], k fastest; 64-bit offsets so N^3 may exceed 2^31.
-__host__ __device__ __forceinline__ size_t offs(int N, int i, int j, int k)
+// C order [i][j][k], k fastest.  N <= 1024, so every offset fits 32 bits.
+constexpr int kMaxN = 1024;
+__host__ __device__ __forceinline__ unsigned offs(int N, int i, int j, int k)
 {
-    return ((size_t)i * (size_t)N + (size_t)j) * (size_t)N + (size_t)k;
+    return ((unsigned)i * (unsigned)N + (unsigned)j) * (unsigned)N + (unsigned)k;
 }
 __device__ __forceinline__ int wp(int a, int N) { return a + 1 == N ? 0 : a + 1; }
 __device__ __forceinline__ int wm(int a, int N) { return a == 0 ? N - 1 : a - 1; }
 
-constexpr int kThreads = 256;      // default block size of the grid kernels
+constexpr int kThreads = 256;      // block size of the elementwise kernels
 constexpr int kReduceThreads = 1024;
 constexpr int kCoarseThreads = 512;
 constexpr int kMaxCoarseCells = 4096;  // 16^3: the single-CTA coarsest solve
@@ -28,6 +29,23 @@ inline unsigned blocks_for(size_t work, int threads = kThreads)
 {
     return (unsigned)((work + threads - 1) / threads);
 }
+
+// Row-based launch shape of the grid kernels: 32 threads along k (or along
+// k-pairs), 8 rows (i, j) per block, a grid-stride loop over the N^2 rows.
+// Index arithmetic is a single 32-bit division per row.
+constexpr int kRowX = 32, kRowY = 8;
+constexpr unsigned kMaxRowBlocks = 8192;
+inline dim3 row_block() { return dim3(kRowX, kRowY, 1); }
+inline unsigned row_grid(int N, unsigned cap = kMaxRowBlocks)
+{
+    const unsigned rows = (unsigned)N * (unsigned)N;
+    const unsigned b = (rows + kRowY - 1) / kRowY;
+    return b < cap ? b : cap;
+}
+#define FOR_ROWS(N, i, j)                                                              \
+    for (unsigned row_ = blockIdx.x * blockDim.y + threadIdx.y;                        \
+         row_ < (unsigned)(N) * (unsigned)(N); row_ += gridDim.x * blockDim.y)          \
+        if (const int i = (int)(row_ / (unsigned)(N)), j = (int)(row_ % (unsigned)(N)); true)
 
 // ---------------------------------------------------------------- scalars
 // Device-resident scalars of one handle (doubles), so that a cycle needs no
@@ -51,11 +69,14 @@ __host__ __device__ __forceinline__ int slot_scale(int l) { return S_LEVEL + 4 *
 __host__ __device__ __forceinline__ int slot_pscale(int l) { return S_LEVEL + 4 * l + 2; }
 
 // ---------------------------------------------------------------- reductions
+// Linear thread index (blocks may be 2-D); reductions return in ltid() == 0.
+__device__ __forceinline__ int ltid() { return threadIdx.x + threadIdx.y * blockDim.x; }
+
 template <int NT>
 __device__ __forceinline__ double block_sum(double v, double *sh)
 {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int t = ltid(), lane = t & 31, warp = t >> 5;
     __syncthreads();
     if (lane == 0) sh[warp] = v;
     __syncthreads();
@@ -64,14 +85,14 @@ __device__ __forceinline__ double block_sum(double v, double *sh)
         r = lane < NT / 32 ? sh[lane] : 0.0;
         for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
     }
-    return r;   // valid in thread 0
+    return r;   // valid in ltid() == 0
 }
 
 template <int NT>
 __device__ __forceinline__ double block_min(double v, double *sh)
 {
     for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_down_sync(0xffffffffu, v, o));
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int t = ltid(), lane = t & 31, warp = t >> 5;
     __syncthreads();
     if (lane == 0) sh[warp] = v;
     __syncthreads();

@@ -28,7 +28,7 @@ int level_sizes(int N, int *Nl)
 const char *check_size(int N, int *Nl, int *nlev)
 {
     if (N < 4 || N % 2 != 0) return "N must be even and >= 4";
-    if (N > 4096) return "N must be <= 4096";
+    if (N > kMaxN) return "N must be <= 1024";
     *nlev = level_sizes(N, Nl);
     const int Nc = Nl[*nlev - 1];
     if ((long)Nc * Nc * Nc > kMaxCoarseCells)
@@ -329,7 +329,7 @@ const char *recon_last_error(const recon_handle *H)
 }
 
 // ---------------------------------------------------------------- steps
-static bool step_size_ok(int N) { return N >= 4 && N % 2 == 0 && N <= 4096; }
+static bool step_size_ok(int N) { return N >= 4 && N % 2 == 0 && N <= kMaxN; }
 
 recon_status recon_step_sweep(int N, double h, int prec, int rule, void *theta, const void *g,
                               double c, int sweeps, void *work, void *stream)
@@ -361,7 +361,7 @@ recon_status recon_step_det(int N, double h, const double *theta, double *det, v
 
 recon_status recon_step_restrict(int Nf, int prec, const void *fine, void *coarse, void *stream)
 {
-    if (Nf < 2 || Nf % 2 != 0 || Nf > 4096 || !fine || !coarse || (prec != 0 && prec != 1))
+    if (Nf < 2 || Nf % 2 != 0 || Nf > kMaxN || !fine || !coarse || (prec != 0 && prec != 1))
         return RECON_E_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = prec == 0 ? restrict_plain<double>(Nf, (const double *)fine, (double *)coarse, s)
@@ -372,7 +372,7 @@ recon_status recon_step_restrict(int Nf, int prec, const void *fine, void *coars
 recon_status recon_step_prolong_add(int Nc, int prec, const void *cnew, const void *cold,
                                     double scale, void *fine, void *stream)
 {
-    if (Nc < 1 || Nc > 2048 || !cnew || !fine || (prec != 0 && prec != 1)) return RECON_E_INVALID;
+    if (Nc < 1 || 2 * Nc > kMaxN || !cnew || !fine || (prec != 0 && prec != 1)) return RECON_E_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = prec == 0
         ? prolong_add<double>(Nc, (const double *)cnew, (const double *)cold, nullptr, scale, (double *)fine, s)
@@ -399,7 +399,7 @@ recon_status recon_step_coarse_solve(int N, double h, int prec, int rule, void *
 recon_status recon_step_cic_cells(const double *pos, long long n, int N, double L, int *cells,
                                   double *frac, void *stream)
 {
-    if (n < 0 || N < 1 || !(L > 0) || (n > 0 && (!pos || !cells || !frac))) return RECON_E_INVALID;
+    if (n < 0 || N < 1 || N > kMaxN || !(L > 0) || (n > 0 && (!pos || !cells || !frac))) return RECON_E_INVALID;
     return cic_cells(pos, n, N, L, cells, frac, (cudaStream_t)stream) == cudaSuccess ? RECON_OK
                                                                                      : RECON_E_CUDA;
 }

@@ -29,7 +29,7 @@ __device__ __forceinline__ void cic_axis(double x, int N, double inv_h, int &i0,
 
 // Sum `v` over the lanes of the warp that share `key`; the lowest such lane
 // gets the total and true, the others false.  Every lane must call this.
-__device__ __forceinline__ bool warp_aggregate(unsigned long long key, double &v)
+__device__ __forceinline__ bool warp_aggregate(unsigned key, double &v)
 {
     const unsigned peers = __match_any_sync(0xffffffffu, key);
     const int lane = threadIdx.x & 31;
@@ -56,7 +56,7 @@ __device__ __forceinline__ void cic_scatter(bool active, const double xyz[3], do
                 const double w = __dmul_rn(__dmul_rn(a ? f[0] : 1.0 - f[0], b ? f[1] : 1.0 - f[1]),
                                            cc ? f[2] : 1.0 - f[2]);
                 double v = active ? __dmul_rn(val, w) : 0.0;
-                const unsigned long long key = active ? (unsigned long long)offs(N, i, j, k) : ~0ull;
+                const unsigned key = active ? offs(N, i, j, k) : 0xffffffffu;
                 if (warp_aggregate(key, v) && active) atomicAdd(rho + offs(N, i, j, k), v);
             }
 }
@@ -104,41 +104,42 @@ cudaError_t cic_deposit(const double *pos, long long n, int N, double L, double 
 // Per Eulerian cell x_c: psi = -grad phi (central differences), the mapped
 // Lagrangian position q = x + grad phi (mod L), v = 3 - tr((I + H)^-1), and
 // CIC deposits of b v (numerator) and b (denominator) at q.
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kRowX * kRowY)
 k_displace_cells(const double *__restrict__ t, const double *__restrict__ b, int N, double L,
                  double h, double ih2, double *__restrict__ psi, double *__restrict__ num,
                  double *__restrict__ den)
 {
-    const size_t n = (size_t)N * N * N;
-    const size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool active = id < n;
-    double q[3] = {0.0, 0.0, 0.0};
-    double wv = 0.0, wb = 0.0;
-    if (active) {
-        const int k = (int)(id % N);
-        const size_t r = id / N;
-        const int j = (int)(r % N), i = (int)(r / N);
-        const Nb19<double> nb = load19<double>(t, N, i, j, k);
-        const double g[3] = {(nb.xp - nb.xm) / (2.0 * h), (nb.yp - nb.ym) / (2.0 * h),
-                             (nb.zp - nb.zm) / (2.0 * h)};
-        // explicitly rounded so that q (and hence its CIC cell) does not
-        // depend on multiply-add contraction
-        const double x[3] = {__dmul_rn(i + 0.5, h), __dmul_rn(j + 0.5, h), __dmul_rn(k + 0.5, h)};
-        for (int d = 0; d < 3; ++d) {
-            psi[d * n + id] = -g[d];
-            double qq = fmod(__dadd_rn(x[d], g[d]), L);
-            if (qq < 0.0) qq += L;
-            q[d] = qq;
-        }
-        const Cof<double> a = cofactors(nb, ih2);
-        const double D = det_IH(nb, ih2);
-        const double v = 3.0 - (a.xx + a.yy + a.zz) / D;
-        wb = b[id];
-        wv = wb * v;
-    }
+    const unsigned n = (unsigned)N * N * N;
     const double inv_h = (double)N / L;
-    cic_scatter(active, q, wv, N, inv_h, num);
-    cic_scatter(active, q, wb, N, inv_h, den);
+    FOR_ROWS(N, i, j)
+    for (int k0 = 0; k0 < N; k0 += kRowX) {   // uniform trip count: every lane
+        const int k = k0 + threadIdx.x;        // takes part in the aggregation
+        const bool active = k < N;
+        double q[3] = {0.0, 0.0, 0.0};
+        double wv = 0.0, wb = 0.0;
+        if (active) {
+            const unsigned id = offs(N, i, j, k);
+            const Nb19<double> nb = load19<double>(t, N, i, j, k);
+            const double g[3] = {(nb.xp - nb.xm) / (2.0 * h), (nb.yp - nb.ym) / (2.0 * h),
+                                 (nb.zp - nb.zm) / (2.0 * h)};
+            // explicitly rounded so that q (and hence its CIC cell) does not
+            // depend on multiply-add contraction
+            const double x[3] = {__dmul_rn(i + 0.5, h), __dmul_rn(j + 0.5, h), __dmul_rn(k + 0.5, h)};
+            for (int d = 0; d < 3; ++d) {
+                psi[(size_t)d * n + id] = -g[d];
+                double qq = fmod(__dadd_rn(x[d], g[d]), L);
+                if (qq < 0.0) qq += L;
+                q[d] = qq;
+            }
+            const Cof<double> a = cofactors(nb, ih2);
+            const double D = det_IH(nb, ih2);
+            const double v = 3.0 - (a.xx + a.yy + a.zz) / D;
+            wb = b[id];
+            wv = wb * v;
+        }
+        cic_scatter(active, q, wv, N, inv_h, num);
+        cic_scatter(active, q, wb, N, inv_h, den);
+    }
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -158,7 +159,7 @@ cudaError_t displace(int N, double L, const double *phi, const double *b, double
     if (e == cudaSuccess) e = cudaMemsetAsync(den, 0, sizeof(double) * n, s);
     if (e != cudaSuccess) return e;
     note_launch();
-    k_displace_cells<<<blocks_for(n), kThreads, 0, s>>>(phi, b, N, L, h, 1.0 / (h * h), psi, num, den);
+    k_displace_cells<<<row_grid(N), row_block(), 0, s>>>(phi, b, N, L, h, 1.0 / (h * h), psi, num, den);
     note_launch();
     k_displace_finish<<<blocks_for(n), kThreads, 0, s>>>(num, den, n, deltaL);
     return cudaGetLastError();

@@ -9,6 +9,9 @@
 // buffer so that every update of one colour reads the values held at the
 // start of the pass (the same-colour edge neighbours enter the cubic's
 // coefficients, so an in-place parallel pass would race).
+//
+// Launch shape of the grid kernels: blocks of 32 x 8 threads, 32 along k
+// (coalesced), 8 rows (i, j), grid-stride over the N^2 rows (FOR_ROWS).
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -18,6 +21,8 @@
 
 namespace recon {
 
+constexpr int kRowThreads = kRowX * kRowY;
+
 static inline unsigned red_blocks(size_t work, int threads = kThreads)
 {
     size_t b = (work + threads - 1) / threads;
@@ -25,42 +30,41 @@ static inline unsigned red_blocks(size_t work, int threads = kThreads)
 }
 
 // ======================================================================
-// smoother: one colour pass, one thread per (k even, k odd) cell pair
+// smoother: one colour pass; a thread handles the cell pair (2m, 2m+1) of
+// its row, of which exactly one has the pass's colour
 // ======================================================================
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kRowThreads)
 k_rb_pass(const T *__restrict__ src, T *__restrict__ dst, const T *__restrict__ g,
           const double *__restrict__ cptr, double cval, int N, T ih2, T h2_6, int colour,
           int rule)
 {
-    const size_t half = (size_t)(N >> 1);
-    const size_t npairs = (size_t)N * (size_t)N * half;
-    const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (tid >= npairs) return;
-    const int m = (int)(tid % half);
-    const size_t r = tid / half;
-    const int j = (int)(r % (size_t)N), i = (int)(r / (size_t)N);
-    const int par = (colour + i + j) & 1;   // (i + j + k) % 2 == colour
-    const int ka = 2 * m + par, kb = 2 * m + 1 - par;
     const T c = (T)(cptr ? *cptr : cval);
-    const Nb19<T> nb = load19<T>(src, N, i, j, ka);
-    T s, p, q;
-    cubic_coeffs(nb, ih2, g[offs(N, i, j, ka)] + c, s, p, q);
-    dst[offs(N, i, j, ka)] = point_update(nb.c, h2_6, s, p, q, rule);
-    dst[offs(N, i, j, kb)] = src[offs(N, i, j, kb)];
+    const int half = N >> 1;
+    FOR_ROWS(N, i, j)
+    {
+        const int par = (colour + i + j) & 1;   // (i + j + k) % 2 == colour
+        const unsigned base = offs(N, i, j, 0);
+        for (int m = threadIdx.x; m < half; m += kRowX) {
+            const int ka = 2 * m + par, kb = 2 * m + 1 - par;
+            const Nb19<T> nb = load19<T>(src, N, i, j, ka);
+            T s, p, q;
+            cubic_coeffs(nb, ih2, g[base + ka] + c, s, p, q);
+            dst[base + ka] = point_update(nb.c, h2_6, s, p, q, rule);
+            dst[base + kb] = src[base + kb];
+        }
+    }
 }
 
 template <typename T>
 cudaError_t sweep(int N, double h, int rule, T *t, const T *g, const double *cptr,
                   double cval, int sweeps, T *work, cudaStream_t s)
 {
-    const size_t npairs = (size_t)N * N * (N / 2);
     const T ih2 = (T)(1.0 / (h * h)), h2_6 = (T)(h * h / 6.0);
     for (int it = 0; it < sweeps; ++it) {
-        note_launch();
-        k_rb_pass<T><<<blocks_for(npairs), kThreads, 0, s>>>(t, work, g, cptr, cval, N, ih2, h2_6, 0, rule);
-        note_launch();
-        k_rb_pass<T><<<blocks_for(npairs), kThreads, 0, s>>>(work, t, g, cptr, cval, N, ih2, h2_6, 1, rule);
+        note_launch(2);
+        k_rb_pass<T><<<row_grid(N), row_block(), 0, s>>>(t, work, g, cptr, cval, N, ih2, h2_6, 0, rule);
+        k_rb_pass<T><<<row_grid(N), row_block(), 0, s>>>(work, t, g, cptr, cval, N, ih2, h2_6, 1, rule);
     }
     return cudaGetLastError();
 }
@@ -70,51 +74,42 @@ template cudaError_t sweep<float>(int, double, int, float *, const float *, cons
 // ======================================================================
 // residuals
 // ======================================================================
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kRowThreads)
 k_residual_write(const double *__restrict__ t, const double *__restrict__ g,
                  const double *__restrict__ cptr, double cval, int N, double ih2,
                  double *__restrict__ r)
 {
-    const size_t n = (size_t)N * N * N;
-    const size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (id >= n) return;
-    const int k = (int)(id % N);
-    const size_t q = id / N;
-    const int j = (int)(q % N), i = (int)(q / N);
     const double c = cptr ? *cptr : cval;
-    r[id] = (g[id] + c) - det_IH(load19<double>(t, N, i, j, k), ih2);
+    FOR_ROWS(N, i, j)
+    for (int k = threadIdx.x; k < N; k += kRowX) {
+        const unsigned id = offs(N, i, j, k);
+        r[id] = (g[id] + c) - det_IH(load19<double>(t, N, i, j, k), ih2);
+    }
 }
 
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kRowThreads)
 k_det_write(const double *__restrict__ t, int N, double ih2, double *__restrict__ out)
 {
-    const size_t n = (size_t)N * N * N;
-    const size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (id >= n) return;
-    const int k = (int)(id % N);
-    const size_t q = id / N;
-    const int j = (int)(q % N), i = (int)(q / N);
-    out[id] = det_IH(load19<double>(t, N, i, j, k), ih2);
+    FOR_ROWS(N, i, j)
+    for (int k = threadIdx.x; k < N; k += kRowX)
+        out[offs(N, i, j, k)] = det_IH(load19<double>(t, N, i, j, k), ih2);
 }
 
 // partials[4 b + 0..2] = sum r, sum r^2, sum theta over this block's cells,
 // r = g + c - det(I + H theta).  When f32out is set (mixed path, T = double)
 // the residual is also stored as float and theta as float in t32out.
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kRowThreads)
 k_residual_norms(const T *__restrict__ t, const T *__restrict__ g,
                  const double *__restrict__ cptr, int N, T ih2, double *__restrict__ partials,
                  float *__restrict__ f32out, float *__restrict__ t32out)
 {
     __shared__ double sh[32];
-    const size_t n = (size_t)N * N * N;
     const T c = (T)(*cptr);
     double sr = 0.0, sr2 = 0.0, st = 0.0;
-    for (size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x; id < n;
-         id += (size_t)gridDim.x * blockDim.x) {
-        const int k = (int)(id % N);
-        const size_t q = id / N;
-        const int j = (int)(q % N), i = (int)(q / N);
+    FOR_ROWS(N, i, j)
+    for (int k = threadIdx.x; k < N; k += kRowX) {
+        const unsigned id = offs(N, i, j, k);
         const Nb19<T> nb = load19<T>(t, N, i, j, k);
         const T res = (g[id] + c) - det_IH(nb, ih2);
         sr += (double)res;
@@ -125,12 +120,12 @@ k_residual_norms(const T *__restrict__ t, const T *__restrict__ g,
             t32out[id] = (float)nb.c;
         }
     }
-    double v = block_sum<kThreads>(sr, sh);
-    if (threadIdx.x == 0) partials[4 * blockIdx.x + 0] = v;
-    v = block_sum<kThreads>(sr2, sh);
-    if (threadIdx.x == 0) partials[4 * blockIdx.x + 1] = v;
-    v = block_sum<kThreads>(st, sh);
-    if (threadIdx.x == 0) partials[4 * blockIdx.x + 2] = v;
+    double v = block_sum<kRowThreads>(sr, sh);
+    if (ltid() == 0) partials[4 * blockIdx.x + 0] = v;
+    v = block_sum<kRowThreads>(sr2, sh);
+    if (ltid() == 0) partials[4 * blockIdx.x + 1] = v;
+    v = block_sum<kRowThreads>(st, sh);
+    if (ltid() == 0) partials[4 * blockIdx.x + 2] = v;
 }
 
 // Single block: total of column `col` of the partials, in a fixed order.
@@ -150,7 +145,7 @@ k_finalize_cycle(const double *__restrict__ partials, int nb, double n, double *
     const double sr = sum_partials(partials, nb, 0, sh);
     const double sr2 = sum_partials(partials, nb, 1, sh);
     const double st = sum_partials(partials, nb, 2, sh);
-    if (threadIdx.x == 0) {
+    if (ltid() == 0) {
         const double m = sr / n;
         const double var = sr2 - n * m * m;
         scal[S_MEAN_R] = m;
@@ -175,21 +170,17 @@ k_gauge(T *__restrict__ t, size_t n, const double *__restrict__ scal)
 // r = g + c - det(I + H theta) and values are averaged (Sec. II.A.3: coarse
 // value = mean of the 8 son cells); the fine residual is never stored.
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kRowThreads)
 k_restrict_residual(const T *__restrict__ t, const T *__restrict__ g,
                     const double *__restrict__ cptr, int Nf, T ih2, T *__restrict__ tH,
                     T *__restrict__ toldH, T *__restrict__ rrH, double *__restrict__ partials)
 {
     __shared__ double sh[32];
     const int Nc = Nf >> 1;
-    const size_t nc = (size_t)Nc * Nc * Nc;
     const T c = (T)(*cptr);
     double srr = 0.0;
-    for (size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x; id < nc;
-         id += (size_t)gridDim.x * blockDim.x) {
-        const int K = (int)(id % Nc);
-        const size_t q = id / Nc;
-        const int J = (int)(q % Nc), I = (int)(q / Nc);
+    FOR_ROWS(Nc, I, J)
+    for (int K = threadIdx.x; K < Nc; K += kRowX) {
         T at = T(0), ar = T(0);
         for (int a = 0; a < 2; ++a)
             for (int b = 0; b < 2; ++b)
@@ -200,13 +191,14 @@ k_restrict_residual(const T *__restrict__ t, const T *__restrict__ g,
                     ar += (g[offs(Nf, i, j, k)] + c) - det_IH(nb, ih2);
                 }
         const T vt = at * T(0.125), vr = ar * T(0.125);
+        const unsigned id = offs(Nc, I, J, K);
         tH[id] = vt;
         toldH[id] = vt;
         rrH[id] = vr;
         srr += (double)vr;
     }
-    const double v = block_sum<kThreads>(srr, sh);
-    if (threadIdx.x == 0) partials[4 * blockIdx.x + 0] = v;
+    const double v = block_sum<kRowThreads>(srr, sh);
+    if (ltid() == 0) partials[4 * blockIdx.x + 0] = v;
 }
 
 __global__ void __launch_bounds__(kReduceThreads)
@@ -214,33 +206,29 @@ k_finalize_mean(const double *__restrict__ partials, int nb, double n, double *o
 {
     __shared__ double sh[32];
     const double s = sum_partials(partials, nb, 0, sh);
-    if (threadIdx.x == 0) *out = s / n;
+    if (ltid() == 0) *out = s / n;
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kRowThreads)
 k_restrict_plain(const T *__restrict__ f, int Nf, T *__restrict__ cr)
 {
     const int Nc = Nf >> 1;
-    const size_t nc = (size_t)Nc * Nc * Nc;
-    const size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (id >= nc) return;
-    const int K = (int)(id % Nc);
-    const size_t q = id / Nc;
-    const int J = (int)(q % Nc), I = (int)(q / Nc);
-    T acc = T(0);
-    for (int a = 0; a < 2; ++a)
-        for (int b = 0; b < 2; ++b)
-            for (int cc = 0; cc < 2; ++cc) acc += f[offs(Nf, 2 * I + a, 2 * J + b, 2 * K + cc)];
-    cr[id] = acc * T(0.125);
+    FOR_ROWS(Nc, I, J)
+    for (int K = threadIdx.x; K < Nc; K += kRowX) {
+        T acc = T(0);
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b)
+                for (int cc = 0; cc < 2; ++cc) acc += f[offs(Nf, 2 * I + a, 2 * J + b, 2 * K + cc)];
+        cr[offs(Nc, I, J, K)] = acc * T(0.125);
+    }
 }
 
 template <typename T>
 cudaError_t restrict_plain(int Nf, const T *fine, T *coarse, cudaStream_t s)
 {
-    const size_t nc = (size_t)(Nf / 2) * (Nf / 2) * (Nf / 2);
     note_launch();
-    k_restrict_plain<T><<<blocks_for(nc), kThreads, 0, s>>>(fine, Nf, coarse);
+    k_restrict_plain<T><<<row_grid(Nf / 2), row_block(), 0, s>>>(fine, Nf, coarse);
     return cudaGetLastError();
 }
 template cudaError_t restrict_plain<double>(int, const double *, double *, cudaStream_t);
@@ -250,20 +238,17 @@ template cudaError_t restrict_plain<float>(int, const float *, float *, cudaStre
 // dH = det_H(I + H theta_H) (stored in aux), and the block minimum of the
 // scaled-defect ratio floor * max(dH, 0) / (-rr) over cells with rr < 0.
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kRowThreads)
 k_coarse_rhs(const T *__restrict__ tH, T *__restrict__ gH, T *__restrict__ dH,
              const double *__restrict__ mean_ptr, int Nc, T ih2, double floor_,
              double *__restrict__ partials)
 {
     __shared__ double sh[32];
-    const size_t nc = (size_t)Nc * Nc * Nc;
     const T m = (T)(*mean_ptr);
     double mn = INFINITY;
-    for (size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x; id < nc;
-         id += (size_t)gridDim.x * blockDim.x) {
-        const int K = (int)(id % Nc);
-        const size_t q = id / Nc;
-        const int J = (int)(q % Nc), I = (int)(q / Nc);
+    FOR_ROWS(Nc, I, J)
+    for (int K = threadIdx.x; K < Nc; K += kRowX) {
+        const unsigned id = offs(Nc, I, J, K);
         const T rr = gH[id] - m;
         const T d = det_IH(load19<T>(tH, Nc, I, J, K), ih2);
         gH[id] = rr;
@@ -273,8 +258,8 @@ k_coarse_rhs(const T *__restrict__ tH, T *__restrict__ gH, T *__restrict__ dH,
             mn = fmin(mn, cand);
         }
     }
-    const double v = block_min<kThreads>(mn, sh);
-    if (threadIdx.x == 0) partials[4 * blockIdx.x + 3] = v;
+    const double v = block_min<kRowThreads>(mn, sh);
+    if (ltid() == 0) partials[4 * blockIdx.x + 3] = v;
 }
 
 // s = min(1, min ratio) (1 when the safeguard is off); s < 1e-3 -> 0 (skip).
@@ -286,7 +271,7 @@ k_finalize_scale(const double *__restrict__ partials, int nb, double floor_, dou
     double v = INFINITY;
     for (int b = threadIdx.x; b < nb; b += blockDim.x) v = fmin(v, partials[4 * b + 3]);
     v = block_min<kReduceThreads>(v, sh);
-    if (threadIdx.x == 0) {
+    if (ltid() == 0) {
         double s = floor_ <= 0.0 ? 1.0 : fmin(1.0, v);
         if (s < 1e-3) s = 0.0;
         *sslot = s;
@@ -307,41 +292,40 @@ k_form_rhs(T *__restrict__ gH, const T *__restrict__ dH, size_t nc,
 // parent weighs 3/4 and the coarse neighbour on the fine cell's side 1/4.
 // scale = *pscale when pscale is given (0 = no correction), else `scale`.
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kRowThreads)
 k_prolong_add(const T *__restrict__ cnew, const T *__restrict__ cold, int Nc,
               const double *__restrict__ pscale, double scale, T *__restrict__ fine)
 {
     const double sc = pscale ? *pscale : scale;
     if (sc == 0.0) return;
     const int Nf = 2 * Nc;
-    const size_t nf = (size_t)Nf * Nf * Nf;
-    const size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (id >= nf) return;
-    const int k = (int)(id % Nf);
-    const size_t q = id / Nf;
-    const int j = (int)(q % Nf), i = (int)(q / Nf);
-    const int I = i >> 1, J = j >> 1, K = k >> 1;
-    const int I1 = (i & 1) ? (I + 1 == Nc ? 0 : I + 1) : (I == 0 ? Nc - 1 : I - 1);
-    const int J1 = (j & 1) ? (J + 1 == Nc ? 0 : J + 1) : (J == 0 ? Nc - 1 : J - 1);
-    const int K1 = (k & 1) ? (K + 1 == Nc ? 0 : K + 1) : (K == 0 ? Nc - 1 : K - 1);
-    T acc = T(0);
-    for (int a = 0; a < 2; ++a)
-        for (int b = 0; b < 2; ++b)
-            for (int cc = 0; cc < 2; ++cc) {
-                const T w = (a ? T(0.25) : T(0.75)) * (b ? T(0.25) : T(0.75)) * (cc ? T(0.25) : T(0.75));
-                const size_t o = offs(Nc, a ? I1 : I, b ? J1 : J, cc ? K1 : K);
-                acc += w * (cold ? cnew[o] - cold[o] : cnew[o]);
-            }
-    fine[id] += (T)sc * acc;
+    FOR_ROWS(Nf, i, j)
+    {
+        const int I = i >> 1, J = j >> 1;
+        const int I1 = (i & 1) ? (I + 1 == Nc ? 0 : I + 1) : (I == 0 ? Nc - 1 : I - 1);
+        const int J1 = (j & 1) ? (J + 1 == Nc ? 0 : J + 1) : (J == 0 ? Nc - 1 : J - 1);
+        for (int k = threadIdx.x; k < Nf; k += kRowX) {
+            const int K = k >> 1;
+            const int K1 = (k & 1) ? (K + 1 == Nc ? 0 : K + 1) : (K == 0 ? Nc - 1 : K - 1);
+            T acc = T(0);
+            for (int a = 0; a < 2; ++a)
+                for (int b = 0; b < 2; ++b)
+                    for (int cc = 0; cc < 2; ++cc) {
+                        const T w = (a ? T(0.25) : T(0.75)) * (b ? T(0.25) : T(0.75)) * (cc ? T(0.25) : T(0.75));
+                        const unsigned o = offs(Nc, a ? I1 : I, b ? J1 : J, cc ? K1 : K);
+                        acc += w * (cold ? cnew[o] - cold[o] : cnew[o]);
+                    }
+            fine[offs(Nf, i, j, k)] += (T)sc * acc;
+        }
+    }
 }
 
 template <typename T>
 cudaError_t prolong_add(int Nc, const T *cnew, const T *cold, const double *pscale,
                         double scale, T *fine, cudaStream_t s)
 {
-    const size_t nf = (size_t)8 * Nc * Nc * Nc;
     note_launch();
-    k_prolong_add<T><<<blocks_for(nf), kThreads, 0, s>>>(cnew, cold, Nc, pscale, scale, fine);
+    k_prolong_add<T><<<row_grid(2 * Nc), row_block(), 0, s>>>(cnew, cold, Nc, pscale, scale, fine);
     return cudaGetLastError();
 }
 template cudaError_t prolong_add<double>(int, const double *, const double *, const double *, double, double *, cudaStream_t);
@@ -366,7 +350,7 @@ __device__ double coarse_proj_rms(const T *t, T *work, const T *g, T c, int N, T
         sr += (double)r;
     }
     double tot = block_sum<kCoarseThreads>(sr, sh);
-    if (threadIdx.x == 0) *sval = tot / n;
+    if (ltid() == 0) *sval = tot / n;
     __syncthreads();
     const double m = *sval;
     double s2 = 0.0;
@@ -375,7 +359,7 @@ __device__ double coarse_proj_rms(const T *t, T *work, const T *g, T c, int N, T
         s2 += d * d;
     }
     tot = block_sum<kCoarseThreads>(s2, sh);
-    if (threadIdx.x == 0) *sval = sqrt(tot / n);
+    if (ltid() == 0) *sval = sqrt(tot / n);
     __syncthreads();
     const double v = *sval;
     __syncthreads();
@@ -417,7 +401,7 @@ k_coarse_solve(T *t, T *work, const T *g, const double *cptr, double cval, int N
         const double cur = coarse_proj_rms<T>(t, work, g, c, N, ih2, sh, &sval);
         if (cur <= rtol * r0) break;
     }
-    if (threadIdx.x == 0 && sweeps_out) *sweeps_out = sw;
+    if (ltid() == 0 && sweeps_out) *sweeps_out = sw;
 }
 
 template <typename T>
@@ -437,43 +421,37 @@ template cudaError_t coarse_solve<float>(int, double, int, float *, const float 
 // ======================================================================
 // Jacobian (linearisation of det(I + H theta))
 // ======================================================================
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kRowThreads)
 k_jacobian_apply(const double *__restrict__ t, const double *__restrict__ v, int N, double ih2,
                  double *__restrict__ out)
 {
-    const size_t n = (size_t)N * N * N;
-    const size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (id >= n) return;
-    const int k = (int)(id % N);
-    const size_t q = id / N;
-    const int j = (int)(q % N), i = (int)(q / N);
-    const Cof<double> a = cofactors(load19<double>(t, N, i, j, k), ih2);
-    out[id] = jac_apply(a, load19<double>(v, N, i, j, k), ih2);
+    FOR_ROWS(N, i, j)
+    for (int k = threadIdx.x; k < N; k += kRowX) {
+        const Cof<double> a = cofactors(load19<double>(t, N, i, j, k), ih2);
+        out[offs(N, i, j, k)] = jac_apply(a, load19<double>(v, N, i, j, k), ih2);
+    }
 }
 
 cudaError_t jacobian_apply(int N, double h, const double *t, const double *v, double *out,
                            cudaStream_t s)
 {
-    const size_t n = (size_t)N * N * N;
     note_launch();
-    k_jacobian_apply<<<blocks_for(n), kThreads, 0, s>>>(t, v, N, 1.0 / (h * h), out);
+    k_jacobian_apply<<<row_grid(N), row_block(), 0, s>>>(t, v, N, 1.0 / (h * h), out);
     return cudaGetLastError();
 }
 
 cudaError_t residual_write(int N, double h, const double *t, const double *g,
                            const double *cptr, double cval, double *r, cudaStream_t s)
 {
-    const size_t n = (size_t)N * N * N;
     note_launch();
-    k_residual_write<<<blocks_for(n), kThreads, 0, s>>>(t, g, cptr, cval, N, 1.0 / (h * h), r);
+    k_residual_write<<<row_grid(N), row_block(), 0, s>>>(t, g, cptr, cval, N, 1.0 / (h * h), r);
     return cudaGetLastError();
 }
 
 cudaError_t det_write(int N, double h, const double *t, double *out, cudaStream_t s)
 {
-    const size_t n = (size_t)N * N * N;
     note_launch();
-    k_det_write<<<blocks_for(n), kThreads, 0, s>>>(t, N, 1.0 / (h * h), out);
+    k_det_write<<<row_grid(N), row_block(), 0, s>>>(t, N, 1.0 / (h * h), out);
     return cudaGetLastError();
 }
 
@@ -495,11 +473,11 @@ k_b_stats(const double *__restrict__ b, size_t n, double *__restrict__ partials)
         }
     }
     double v = block_sum<kThreads>(s2, sh);
-    if (threadIdx.x == 0) partials[4 * blockIdx.x + 0] = v;
+    if (ltid() == 0) partials[4 * blockIdx.x + 0] = v;
     v = block_sum<kThreads>(bad, sh);
-    if (threadIdx.x == 0) partials[4 * blockIdx.x + 1] = v;
+    if (ltid() == 0) partials[4 * blockIdx.x + 1] = v;
     v = block_min<kThreads>(mn, sh);
-    if (threadIdx.x == 0) partials[4 * blockIdx.x + 3] = v;
+    if (ltid() == 0) partials[4 * blockIdx.x + 3] = v;
 }
 
 __global__ void __launch_bounds__(kReduceThreads)
@@ -511,7 +489,7 @@ k_finalize_b(const double *__restrict__ partials, int nb, double *scal)
     double mn = INFINITY;
     for (int b = threadIdx.x; b < nb; b += blockDim.x) mn = fmin(mn, partials[4 * b + 3]);
     mn = block_min<kReduceThreads>(mn, sh);
-    if (threadIdx.x == 0) {
+    if (ltid() == 0) {
         scal[S_DENOM] = s2 > 0.0 ? sqrt(s2) : 1.0;
         scal[S_BBAD] = bad;
         scal[S_BMIN] = mn;
@@ -554,56 +532,50 @@ k_sub_scalar(float *__restrict__ a, size_t n, const double *__restrict__ v)
 // ---- linear multigrid for J e = f in FP32 (J from the FP32 theta of the level)
 // One colour pass of Gauss-Seidel on J: e_c += (f - J e)_c / J_cc,
 // J_cc = -2 (adj_xx + adj_yy + adj_zz) / h^2.
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kRowThreads)
 k_lin_pass(const float *__restrict__ src, float *__restrict__ dst, const float *__restrict__ f,
            const float *__restrict__ th, int N, float ih2, int colour)
 {
-    const size_t half = (size_t)(N >> 1);
-    const size_t npairs = (size_t)N * (size_t)N * half;
-    const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (tid >= npairs) return;
-    const int m = (int)(tid % half);
-    const size_t r = tid / half;
-    const int j = (int)(r % (size_t)N), i = (int)(r / (size_t)N);
-    const int par = (colour + i + j) & 1;
-    const int ka = 2 * m + par, kb = 2 * m + 1 - par;
-    const Cof<float> a = cofactors(load19<float>(th, N, i, j, ka), ih2);
-    const Nb19<float> ev = load19<float>(src, N, i, j, ka);
-    const float Je = jac_apply(a, ev, ih2);
-    const float diag = -2.0f * (a.xx + a.yy + a.zz) * ih2;
-    dst[offs(N, i, j, ka)] = ev.c + (f[offs(N, i, j, ka)] - Je) / diag;
-    dst[offs(N, i, j, kb)] = src[offs(N, i, j, kb)];
+    const int half = N >> 1;
+    FOR_ROWS(N, i, j)
+    {
+        const int par = (colour + i + j) & 1;
+        const unsigned base = offs(N, i, j, 0);
+        for (int m = threadIdx.x; m < half; m += kRowX) {
+            const int ka = 2 * m + par, kb = 2 * m + 1 - par;
+            const Cof<float> a = cofactors(load19<float>(th, N, i, j, ka), ih2);
+            const Nb19<float> ev = load19<float>(src, N, i, j, ka);
+            const float Je = jac_apply(a, ev, ih2);
+            const float diag = -2.0f * (a.xx + a.yy + a.zz) * ih2;
+            dst[base + ka] = ev.c + (f[base + ka] - Je) / diag;
+            dst[base + kb] = src[base + kb];
+        }
+    }
 }
 
 static cudaError_t lin_sweep(int N, double h, float *e, const float *f, const float *th,
                              int sweeps, float *work, cudaStream_t s)
 {
-    const size_t npairs = (size_t)N * N * (N / 2);
     const float ih2 = (float)(1.0 / (h * h));
     for (int it = 0; it < sweeps; ++it) {
-        note_launch();
-        k_lin_pass<<<blocks_for(npairs), kThreads, 0, s>>>(e, work, f, th, N, ih2, 0);
-        note_launch();
-        k_lin_pass<<<blocks_for(npairs), kThreads, 0, s>>>(work, e, f, th, N, ih2, 1);
+        note_launch(2);
+        k_lin_pass<<<row_grid(N), row_block(), 0, s>>>(e, work, f, th, N, ih2, 0);
+        k_lin_pass<<<row_grid(N), row_block(), 0, s>>>(work, e, f, th, N, ih2, 1);
     }
     return cudaGetLastError();
 }
 
 // fH = R (f - J e), block partial sums for the mean projection.
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kRowThreads)
 k_lin_restrict_residual(const float *__restrict__ e, const float *__restrict__ f,
                         const float *__restrict__ th, int Nf, float ih2, float *__restrict__ fH,
                         double *__restrict__ partials)
 {
     __shared__ double sh[32];
     const int Nc = Nf >> 1;
-    const size_t nc = (size_t)Nc * Nc * Nc;
     double sacc = 0.0;
-    for (size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x; id < nc;
-         id += (size_t)gridDim.x * blockDim.x) {
-        const int K = (int)(id % Nc);
-        const size_t q = id / Nc;
-        const int J = (int)(q % Nc), I = (int)(q / Nc);
+    FOR_ROWS(Nc, I, J)
+    for (int K = threadIdx.x; K < Nc; K += kRowX) {
         float acc = 0.0f;
         for (int a = 0; a < 2; ++a)
             for (int b = 0; b < 2; ++b)
@@ -613,11 +585,11 @@ k_lin_restrict_residual(const float *__restrict__ e, const float *__restrict__ f
                     acc += f[offs(Nf, i, j, k)] - jac_apply(co, load19<float>(e, Nf, i, j, k), ih2);
                 }
         const float v = acc * 0.125f;
-        fH[id] = v;
+        fH[offs(Nc, I, J, K)] = v;
         sacc += (double)v;
     }
-    const double v = block_sum<kThreads>(sacc, sh);
-    if (threadIdx.x == 0) partials[4 * blockIdx.x + 0] = v;
+    const double v = block_sum<kRowThreads>(sacc, sh);
+    if (ltid() == 0) partials[4 * blockIdx.x + 0] = v;
 }
 
 __global__ void __launch_bounds__(kCoarseThreads)
@@ -637,7 +609,7 @@ k_lin_coarse(float *e, float *work, const float *f, const float *th, int N, floa
             sr += (double)r;
         }
         double tot = block_sum<kCoarseThreads>(sr, sh);
-        if (threadIdx.x == 0) sval = tot / n;
+        if (ltid() == 0) sval = tot / n;
         __syncthreads();
         const double m = sval;
         double s2 = 0.0;
@@ -646,7 +618,7 @@ k_lin_coarse(float *e, float *work, const float *f, const float *th, int N, floa
             s2 += d * d;
         }
         tot = block_sum<kCoarseThreads>(s2, sh);
-        if (threadIdx.x == 0) sval = sqrt(tot / n);
+        if (ltid() == 0) sval = sqrt(tot / n);
         __syncthreads();
         const double v = sval;
         __syncthreads();
@@ -676,6 +648,7 @@ k_lin_coarse(float *e, float *work, const float *f, const float *th, int N, floa
         if (proj_rms() <= rtol * r0) break;
     }
 }
+
 
 // ======================================================================
 // drivers
@@ -720,9 +693,9 @@ cudaError_t vcycle(recon_handle *H, const Hier<T> &Y, int l, const double *cptr)
 
     const int Nc = H->Nl[l + 1];
     const size_t nc = ncell(Nc);
-    const unsigned nbr = red_blocks(nc);
+    const unsigned nbr = row_grid(Nc, kMaxRedBlocks);
     note_launch();
-    k_restrict_residual<T><<<nbr, kThreads, 0, s>>>(Y.t[l], Y.g[l], cptr, N, (T)(1.0 / (h * h)),
+    k_restrict_residual<T><<<nbr, row_block(), 0, s>>>(Y.t[l], Y.g[l], cptr, N, (T)(1.0 / (h * h)),
                                                     Y.t[l + 1], Y.told[l + 1], Y.g[l + 1],
                                                     H->partials);
     note_launch();
@@ -730,7 +703,7 @@ cudaError_t vcycle(recon_handle *H, const Hier<T> &Y, int l, const double *cptr)
                                                  H->scal + slot_rmean(l + 1));
     const double hc = H->hl[l + 1];
     note_launch();
-    k_coarse_rhs<T><<<nbr, kThreads, 0, s>>>(Y.t[l + 1], Y.g[l + 1], Y.aux[l + 1],
+    k_coarse_rhs<T><<<nbr, row_block(), 0, s>>>(Y.t[l + 1], Y.g[l + 1], Y.aux[l + 1],
                                              H->scal + slot_rmean(l + 1), Nc,
                                              (T)(1.0 / (hc * hc)), cf.scale_floor, H->partials);
     note_launch();
@@ -754,10 +727,10 @@ cudaError_t compat_gauge(recon_handle *H, const Hier<T> &Y, int l)
     cudaStream_t s = H->stream;
     const int N = H->Nl[l];
     const size_t n = ncell(N);
-    const unsigned nbr = red_blocks(n);
+    const unsigned nbr = row_grid(N, kMaxRedBlocks);
     const double h = H->hl[l];
     note_launch();
-    k_residual_norms<T><<<nbr, kThreads, 0, s>>>(Y.t[l], Y.g[l], H->scal + S_C, N,
+    k_residual_norms<T><<<nbr, row_block(), 0, s>>>(Y.t[l], Y.g[l], H->scal + S_C, N,
                                                  (T)(1.0 / (h * h)), H->partials, nullptr,
                                                  nullptr);
     note_launch();
@@ -913,9 +886,9 @@ cudaError_t lin_vcycle(recon_handle *H, int l)
     CK(lin_sweep(N, h, H->e32[l], H->f32[l], H->t32[l], cf.nu1, H->work32, s));
     const int Nc = H->Nl[l + 1];
     const size_t nc = ncell(Nc);
-    const unsigned nbr = red_blocks(nc);
+    const unsigned nbr = row_grid(Nc, kMaxRedBlocks);
     note_launch();
-    k_lin_restrict_residual<<<nbr, kThreads, 0, s>>>(H->e32[l], H->f32[l], H->t32[l], N, ih2,
+    k_lin_restrict_residual<<<nbr, row_block(), 0, s>>>(H->e32[l], H->f32[l], H->t32[l], N, ih2,
                                                      H->f32[l + 1], H->partials);
     note_launch();
     k_finalize_mean<<<1, kReduceThreads, 0, s>>>(H->partials, nbr, (double)nc,
@@ -973,14 +946,14 @@ recon_status solve_mixed(recon_handle *H, const double *b, double *phi, double t
     k_to_double<<<blocks_for(n), kThreads, 0, s>>>(H->t32[0], phi, n);
 
     // ---- (ii) FP64 defect correction with FP32 linear multigrid
-    const unsigned nbr = red_blocks(n);
+    const unsigned nbr = row_grid(H->N, kMaxRedBlocks);
     const double ih2 = 1.0 / (H->h * H->h);
     recon_status status = RECON_E_NOCONV;
     double best = INFINITY;
     int o = 0;
     for (o = 1; o <= max_cycles; ++o) {
         note_launch();
-        k_residual_norms<double><<<nbr, kThreads, 0, s>>>(phi, b, H->scal + S_C, H->N, ih2,
+        k_residual_norms<double><<<nbr, row_block(), 0, s>>>(phi, b, H->scal + S_C, H->N, ih2,
                                                           H->partials, H->f32[0], H->t32[0]);
         note_launch();
         k_finalize_cycle<<<1, kReduceThreads, 0, s>>>(H->partials, nbr, (double)n, H->scal);

@@ -125,21 +125,40 @@ def zeldovich_positions(delta_hat, N: int, L: float):
     return out.reshape(-1, 3)
 
 
+_WINDOWS = {}
+
+
+def _torch_window(N: int, L: float, R: float, device):
+    """exp(-k^2 R^2 / 2) on the rFFT grid, built on the device and cached."""
+    import torch
+    key = (N, float(L), float(R), str(device))
+    W = _WINDOWS.get(key)
+    if W is None:
+        kf = 2.0 * np.pi / L
+        k1 = torch.fft.fftfreq(N, d=1.0 / N, device=device, dtype=torch.float64) * kf
+        kz = torch.fft.rfftfreq(N, d=1.0 / N, device=device, dtype=torch.float64) * kf
+        k2 = k1[:, None, None] ** 2 + k1[None, :, None] ** 2 + kz[None, None, :] ** 2
+        W = torch.exp(-0.5 * R * R * k2)
+        _WINDOWS.clear()
+        _WINDOWS[key] = W
+    return W
+
+
 def smooth_and_floor(rho, L: float, R: float, floor: float = 0.05):
     """Gaussian-smooth (radius R), floor 1+delta at ``floor``, renormalise to mean 1.
 
     Accepts numpy arrays or torch tensors and returns the same kind.
     """
     N = rho.shape[0]
-    kx, ky, kz = _kgrid(N, L)
-    W = np.exp(-0.5 * (kx * kx + ky * ky + kz * kz) * R * R)
     if isinstance(rho, np.ndarray):
+        kx, ky, kz = _kgrid(N, L)
+        W = np.exp(-0.5 * (kx * kx + ky * ky + kz * kz) * R * R)
         b = np.fft.irfftn(np.fft.rfftn(rho) * W, s=rho.shape, axes=(0, 1, 2)) if R > 0 else rho.copy()
         b = np.maximum(b, floor)
         return b / b.mean()
     import torch
     if R > 0:
-        b = torch.fft.irfftn(torch.fft.rfftn(rho) * torch.from_numpy(W).to(rho.device),
+        b = torch.fft.irfftn(torch.fft.rfftn(rho) * _torch_window(N, L, R, rho.device),
                              s=tuple(rho.shape))
     else:
         b = rho.clone()
