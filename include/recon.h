@@ -169,7 +169,8 @@ recon_status recon_displace(recon_handle *h, const double *phi, const double *b,
 recon_status recon_adjoint(recon_handle *h, const double *gbar_phi, double *gbar_b);
 
 /* Message of the last failing call on this handle ("" if none); a handle
- * of NULL gives the last message of recon_create on this thread. */
+ * of NULL gives the last message of recon_create or
+ * recon_step_coarse_solve_noalloc on this thread. */
 const char *recon_last_error(const recon_handle *h);
 
 /* Name of a status code. */

@@ -55,6 +55,29 @@ recon_status recon_step_coarse_solve(int N, double h, int prec, int rule, void *
                                      double rtol, void *work, int *sweeps_done,
                                      void *stream);
 
+/* The coarsest-grid solve of recon_step_coarse_solve for callers that cannot
+ * allocate device memory (a host that reserves all device memory for its own
+ * pool, a loop that forbids allocation after start-up, code inside a library
+ * that does not own the device).  The paper has no counterpart: this is an
+ * interface variant, not a step of the method.
+ * Same arguments and result as recon_step_coarse_solve, without `work`: the
+ * N^3 scratch lives in a fixed device array of 4096 doubles (32 KiB) compiled
+ * into the library, which every GPU that loads the library holds until the
+ * process exits.  No cudaMalloc, cudaFree or allocating library routine is
+ * called.  N must be even, >= 4, with N^3 <= 4096; larger N returns
+ * RECON_E_INVALID and recon_last_error(NULL) says why.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call uses the same array, which keeps
+ * the last call's contents; the solve writes every scratch entry before
+ * reading it, so nothing has to start at zero.  Calls whose executions
+ * overlap on the GPU (different streams, or several host threads) race on
+ * the array: serialise them. */
+recon_status recon_step_coarse_solve_noalloc(int N, double h, int prec, int rule,
+                                             void *theta, const void *g, double c,
+                                             int max_sweeps, double rtol, int *sweeps_done,
+                                             void *stream);
+
 /* CIC cell of every particle and axis: cells (n x 3 int32) = floor(u) mod N,
  * frac (n x 3 double) = u - floor(u), u = x * (N/L) - 1/2. */
 recon_status recon_step_cic_cells(const double *pos, long long n, int N, double L,

@@ -49,6 +49,9 @@ namespace recon {
 // Kernels launched by this library in this process (diagnostics).
 void note_launch(unsigned long long n = 1);
 
+// Message returned by recon_last_error(NULL) on this thread.
+void set_thread_error(const char *msg);
+
 // ---- multigrid launchers (recon_mg.cu); all asynchronous on `s`.
 template <typename T>
 cudaError_t sweep(int N, double h, int rule, T *t, const T *g, const double *cptr,

@@ -418,4 +418,5 @@ recon_status recon_step_jacobian_apply(int N, double h, const double *theta, con
 #include <atomic>
 static std::atomic<unsigned long long> g_launches{0};
 void recon::note_launch(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+void recon::set_thread_error(const char *msg) { g_create_err = msg ? msg : ""; }
 extern "C" unsigned long long recon_kernel_launches(void) { return g_launches.load(); }

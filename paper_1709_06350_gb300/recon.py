@@ -76,6 +76,7 @@ _SIGS = {
     "recon_step_restrict": (_I, [_I, _I, _P, _P, _P]),
     "recon_step_prolong_add": (_I, [_I, _I, _P, _P, _D, _P, _P]),
     "recon_step_coarse_solve": (_I, [_I, _D, _I, _I, _P, _P, _D, _I, _D, _P, _P, _P]),
+    "recon_step_coarse_solve_noalloc": (_I, [_I, _D, _I, _I, _P, _P, _D, _I, _D, _P, _P]),
     "recon_step_cic_cells": (_I, [_P, _LL, _I, _D, _P, _P, _P]),
     "recon_step_jacobian_apply": (_I, [_I, _D, _P, _P, _P, _P]),
 }
@@ -254,6 +255,23 @@ def recon_step_coarse_solve(theta, g, c, h, max_sweeps=200, rtol=1e-3, rule=RULE
                                           _dev_ptr(work, theta.dtype, N ** 3),
                                           _dev_ptr(done, torch.int32), _stream(stream)))
     return int(done.item())
+
+
+def recon_step_coarse_solve_noalloc(theta, g, c, h, max_sweeps=200, rtol=1e-3,
+                                    rule=RULE_NEWTON1, sweeps_done=None, stream=None):
+    """Coarsest-grid solve without any device allocation by the library.
+
+    For callers that cannot allocate device memory when they run this step;
+    the scratch is a fixed 32 KiB array inside librecon (N^3 <= 4096).
+    ``sweeps_done`` is an optional caller-owned device int32 tensor.
+    """
+    import torch
+    N = theta.shape[0]
+    _check(load().recon_step_coarse_solve_noalloc(
+        N, float(h), _prec(theta), int(rule), _dev_ptr(theta, theta.dtype),
+        _dev_ptr(g, theta.dtype, N ** 3), float(c), int(max_sweeps), float(rtol),
+        _dev_ptr(sweeps_done, torch.int32) if sweeps_done is not None else None,
+        _stream(stream)))
 
 
 def recon_step_cic_cells(pos, N, L, cells, frac, stream=None):
