@@ -396,7 +396,8 @@ static double proj_rms(const double *r, long n)
 /* Coarsest-grid solve (Sec. II.A.3: the hierarchy ends at 4^3; the      */
 /* method there is not given).  Reading: Gauss-Seidel sweeps with the    */
 /* same point update until the mean-free rms residual falls below        */
-/* coarse_rtol times its starting value, or coarse_max_sweeps sweeps.    */
+/* coarse_rtol times its starting value, or a sweep no longer lowers it  */
+/* (round-off floor; only when coarse_rtol > 0), or coarse_max_sweeps.   */
 /* Returns the number of sweeps done.                                    */
 int or_coarse_solve(double *t, const double *g, double c, int N, double h,
                     const or_params *P)
@@ -405,13 +406,18 @@ int or_coarse_solve(double *t, const double *g, double c, int N, double h,
     double *r = (double *)malloc(sizeof(double) * n);
     or_residual(t, g, c, N, h, r);
     double r0 = proj_rms(r, n);
+    double prev = r0;
     int sw = 0;
     while (sw < P->coarse_max_sweeps) {
         or_sweep(t, g, c, N, h, P->ordering, P->rule);
         ++sw;
         or_residual(t, g, c, N, h, r);
-        if (proj_rms(r, n) <= P->coarse_rtol * r0)
+        double cur = proj_rms(r, n);
+        if (cur <= P->coarse_rtol * r0)
             break;
+        if (P->coarse_rtol > 0.0 && cur >= prev)
+            break;              /* no progress: round-off floor reached */
+        prev = cur;
     }
     free(r);
     return sw;

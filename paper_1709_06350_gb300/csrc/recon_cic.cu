@@ -127,8 +127,12 @@ k_displace_cells(const double *__restrict__ t, const double *__restrict__ b, int
             const double x[3] = {__dmul_rn(i + 0.5, h), __dmul_rn(j + 0.5, h), __dmul_rn(k + 0.5, h)};
             for (int d = 0; d < 3; ++d) {
                 psi[(size_t)d * n + id] = -g[d];
-                double qq = fmod(__dadd_rn(x[d], g[d]), L);
-                if (qq < 0.0) qq += L;
+                // q mod L: for q in (-L, 2L) the conditional form gives exactly
+                // fmod's result (q - L is exact there); fmod handles the rest
+                double qq = __dadd_rn(x[d], g[d]);
+                if (qq >= L) qq = qq < 2.0 * L ? __dsub_rn(qq, L) : fmod(qq, L);
+                else if (qq < 0.0 && qq <= -L) qq = fmod(qq, L);
+                if (qq < 0.0) qq = __dadd_rn(qq, L);
                 q[d] = qq;
             }
             const Cof<double> a = cofactors(nb, ih2);

@@ -333,7 +333,8 @@ template cudaError_t prolong_add<float>(int, const float *, const float *, const
 
 // ======================================================================
 // coarsest grid: one thread block, N^3 <= 4096, sweeps until the mean-free
-// rms residual drops by rtol or max_sweeps ran (at least one sweep).
+// rms residual drops by rtol, or a sweep no longer lowers it (round-off
+// floor, only when rtol > 0), or max_sweeps ran (at least one sweep).
 // t and work are read and written by different threads of the block across
 // __syncthreads(), so they are plain (not read-only) pointers.
 // ======================================================================
@@ -377,6 +378,7 @@ k_coarse_solve(T *t, T *work, const T *g, const double *cptr, double cval, int N
     const int half = N >> 1;
     const int npairs = N * N * half;
     const double r0 = coarse_proj_rms<T>(t, work, g, c, N, ih2, sh, &sval);
+    double prev = r0;
     int sw = 0;
     while (sw < max_sweeps) {
         for (int colour = 0; colour < 2; ++colour) {
@@ -400,6 +402,8 @@ k_coarse_solve(T *t, T *work, const T *g, const double *cptr, double cval, int N
         ++sw;
         const double cur = coarse_proj_rms<T>(t, work, g, c, N, ih2, sh, &sval);
         if (cur <= rtol * r0) break;
+        if (rtol > 0.0 && cur >= prev) break;   // no progress: round-off floor
+        prev = cur;
     }
     if (ltid() == 0 && sweeps_out) *sweeps_out = sw;
 }
@@ -625,6 +629,7 @@ k_lin_coarse(float *e, float *work, const float *f, const float *th, int N, floa
         return v;
     };
     const double r0 = proj_rms();
+    double prev = r0;
     for (int sw = 0; sw < max_sweeps; ++sw) {
         for (int colour = 0; colour < 2; ++colour) {
             const float *src = colour == 0 ? e : work;
@@ -645,7 +650,10 @@ k_lin_coarse(float *e, float *work, const float *f, const float *th, int N, floa
             }
             __syncthreads();
         }
-        if (proj_rms() <= rtol * r0) break;
+        const double cur = proj_rms();
+        if (cur <= rtol * r0) break;
+        if (rtol > 0.0 && cur >= prev) break;   // no progress: round-off floor
+        prev = cur;
     }
 }
 
