@@ -56,11 +56,178 @@ k_rb_pass(const T *__restrict__ src, T *__restrict__ dst, const T *__restrict__ 
     }
 }
 
+// ----------------------------------------------------------------------
+// Fused sweep: both colour passes in one kernel, src -> dst, with the same
+// snapshot semantics as two k_rb_pass launches.  A CTA owns a TJ x TK tile
+// of (j, k) and streams a chunk of planes along i through shared memory:
+//   OLD  4 planes (i-1 .. i+2) of src, tile + 2-cell halo
+//   RED  3 planes (i-1 .. i+1) of red-new values, tile + 1-cell halo
+// At step s it loads OLD plane s+2, updates the red cells of plane s+1 on
+// the tile + 1 halo (they read only OLD values), then updates the black
+// cells of plane s on the tile (faces from RED, edges and centre from OLD)
+// and writes plane s.  DRAM traffic: read src and g once, write dst once.
+// Requires N >= kFusedMinN (so one wrap suffices for every halo index).
+// ----------------------------------------------------------------------
+constexpr int kTJ = 16, kTK = 64;
+constexpr int kFusedMinN = 128;
+constexpr int kOJ = kTJ + 4, kOK = kTK + 4;   // OLD plane extent
+constexpr int kRJ = kTJ + 2, kRK = kTK + 2;   // RED plane extent
+
+template <typename T>
+struct FusedSmem {
+    T old_[4][kOJ][kOK];
+    T red_[3][kRJ][kRK];
+};
+
+__device__ __forceinline__ int wrap1(int x, int N) { return x < 0 ? x + N : (x >= N ? x - N : x); }
+
+// 19-point neighbourhood from a shared plane triple (planes m, c, p) at
+// local (r, q) of arrays with row length K.
+template <typename T, int K>
+__device__ __forceinline__ Nb19<T> nb_from(const T (*pm)[K], const T (*pc)[K], const T (*pp)[K],
+                                           int r, int q)
+{
+    Nb19<T> v;
+    v.c = pc[r][q];
+    v.xp = pp[r][q];
+    v.xm = pm[r][q];
+    v.yp = pc[r + 1][q];
+    v.ym = pc[r - 1][q];
+    v.zp = pc[r][q + 1];
+    v.zm = pc[r][q - 1];
+    v.xpyp = pp[r + 1][q];
+    v.xmym = pm[r - 1][q];
+    v.xmyp = pm[r + 1][q];
+    v.xpym = pp[r - 1][q];
+    v.ypzp = pc[r + 1][q + 1];
+    v.ymzm = pc[r - 1][q - 1];
+    v.ymzp = pc[r - 1][q + 1];
+    v.ypzm = pc[r + 1][q - 1];
+    v.xpzp = pp[r][q + 1];
+    v.xmzm = pm[r][q - 1];
+    v.xmzp = pm[r][q + 1];
+    v.xpzm = pp[r][q - 1];
+    return v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_rb_sweep_fused(const T *__restrict__ src, T *__restrict__ dst, const T *__restrict__ g,
+                 const double *__restrict__ cptr, double cval, int N, int CI, T ih2, T h2_6,
+                 int rule)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    FusedSmem<T> &S = *reinterpret_cast<FusedSmem<T> *>(smem_raw);
+    const T c = (T)(cptr ? *cptr : cval);
+    const int k0 = blockIdx.x * kTK, j0 = blockIdx.y * kTJ, i0 = blockIdx.z * CI;
+    const int i1 = min(i0 + CI, N);
+    const int tid = threadIdx.x;
+    const unsigned NN = (unsigned)N * (unsigned)N;
+
+    auto load_old = [&](int slot, int plane) {
+        const unsigned pb = (unsigned)wrap1(plane, N) * NN;
+        for (int e = tid; e < kOJ * kOK; e += 256) {
+            const int r = e / kOK, q = e - r * kOK;
+            const unsigned gj = (unsigned)wrap1(j0 - 2 + r, N), gk = (unsigned)wrap1(k0 - 2 + q, N);
+            S.old_[slot][r][q] = src[pb + gj * (unsigned)N + gk];
+        }
+    };
+    // red cells of plane p on the tile + 1 halo (RED local (r, q) = OLD (r+1, q+1))
+    auto red_plane = [&](int rslot, int om, int oc, int op, int p) {
+        const int pw = wrap1(p, N);
+        const unsigned pb = (unsigned)pw * NN;
+        for (int e = tid; e < kRJ * (kRK / 2); e += 256) {
+            const int r = e / (kRK / 2), m = e - r * (kRK / 2);
+            const int gj = j0 - 1 + r;
+            const int kfirst = k0 - 1 + 2 * m;
+            const int q = 2 * m + ((pw + gj + kfirst) & 1);   // the red cell of the pair
+            const int gk = k0 - 1 + q;
+            const Nb19<T> nb = nb_from<T, kOK>(S.old_[om], S.old_[oc], S.old_[op], r + 1, q + 1);
+            T s, pp, qq;
+            cubic_coeffs(nb, ih2, g[pb + (unsigned)wrap1(gj, N) * (unsigned)N + (unsigned)wrap1(gk, N)] + c,
+                         s, pp, qq);
+            S.red_[rslot][r][q] = point_update(nb.c, h2_6, s, pp, qq, rule);
+        }
+    };
+
+    // prologue: OLD planes i0-2 .. i0+1 in slots 0..3, RED plane i0-1 in slot 0
+    for (int d = 0; d < 4; ++d) load_old(d, i0 - 2 + d);
+    __syncthreads();
+    red_plane(0, 0, 1, 2, i0 - 1);
+
+    for (int s = i0; s < i1; ++s) {
+        const int u = s - i0;
+        __syncthreads();
+        load_old(u & 3, s + 2);
+        __syncthreads();
+        red_plane((u + 2) % 3, (u + 2) & 3, (u + 3) & 3, u & 3, s + 1);
+        __syncthreads();
+        // black cells of plane s on the tile; write the plane
+        const int om = (u + 1) & 3, oc = (u + 2) & 3, op = (u + 3) & 3;
+        const int rm = u % 3, rc = (u + 1) % 3, rp = (u + 2) % 3;
+        const unsigned pb = (unsigned)s * NN;
+        for (int e = tid; e < kTJ * (kTK / 2); e += 256) {
+            const int r = e / (kTK / 2), m = e - r * (kTK / 2);
+            const int gj = j0 + r, gk0 = k0 + 2 * m;
+            if (gj >= N || gk0 >= N) continue;
+            const int par = (s + gj + gk0) & 1;       // 0: first cell red, second black
+            const int qb = 2 * m + 1 - par;           // black cell, tile-local k
+            const int qr = 2 * m + par;               // red cell
+            // OLD local = tile + 2, RED local = tile + 1
+            Nb19<T> nb = nb_from<T, kOK>(S.old_[om], S.old_[oc], S.old_[op], r + 2, qb + 2);
+            nb.xp = S.red_[rp][r + 1][qb + 1];
+            nb.xm = S.red_[rm][r + 1][qb + 1];
+            nb.yp = S.red_[rc][r + 2][qb + 1];
+            nb.ym = S.red_[rc][r][qb + 1];
+            nb.zp = S.red_[rc][r + 1][qb + 2];
+            nb.zm = S.red_[rc][r + 1][qb];
+            const unsigned gb = pb + (unsigned)gj * (unsigned)N + (unsigned)k0;
+            T sv, pv, qv;
+            cubic_coeffs(nb, ih2, g[gb + qb] + c, sv, pv, qv);
+            const T vb = point_update(nb.c, h2_6, sv, pv, qv, rule);
+            const T vr = S.red_[rc][r + 1][qr + 1];
+            dst[gb + qb] = vb;
+            dst[gb + qr] = vr;
+        }
+    }
+}
+
+template <typename T>
+static cudaError_t fused_sweep_launch(int N, const T *src, T *dst, const T *g, const double *cptr,
+                                      double cval, T ih2, T h2_6, int rule, cudaStream_t s)
+{
+    static bool attr_set = false;
+    const size_t smem = sizeof(FusedSmem<T>);
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_rb_sweep_fused<T>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const int CI = N >= 512 ? 64 : (N >= 256 ? 32 : 16);
+    const dim3 grid((N + kTK - 1) / kTK, (N + kTJ - 1) / kTJ, (N + CI - 1) / CI);
+    note_launch();
+    k_rb_sweep_fused<T><<<grid, 256, smem, s>>>(src, dst, g, cptr, cval, N, CI, ih2, h2_6, rule);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t sweep(int N, double h, int rule, T *t, const T *g, const double *cptr,
                   double cval, int sweeps, T *work, cudaStream_t s)
 {
     const T ih2 = (T)(1.0 / (h * h)), h2_6 = (T)(h * h / 6.0);
+    if (N >= kFusedMinN) {
+        T *a = t, *b = work;
+        for (int it = 0; it < sweeps; ++it) {
+            const cudaError_t e = fused_sweep_launch<T>(N, a, b, g, cptr, cval, ih2, h2_6, rule, s);
+            if (e != cudaSuccess) return e;
+            T *tmp = a;
+            a = b;
+            b = tmp;
+        }
+        if (a != t) return cudaMemcpyAsync(t, a, sizeof(T) * (size_t)N * N * N, cudaMemcpyDeviceToDevice, s);
+        return cudaSuccess;
+    }
     for (int it = 0; it < sweeps; ++it) {
         note_launch(2);
         k_rb_pass<T><<<row_grid(N), row_block(), 0, s>>>(t, work, g, cptr, cval, N, ih2, h2_6, 0, rule);

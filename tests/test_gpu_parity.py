@@ -43,9 +43,10 @@ def rel_l2(a, b):
 
 
 # ------------------------------------------------------------------ steps
-@pytest.mark.parametrize("N", [4, 6, 10, 48])
+@pytest.mark.parametrize("N", [4, 6, 10, 48, 128, 160])
 @pytest.mark.parametrize("rule", ["newton1", "exact"])
 def test_sweep_parity(R, O, N, rule):
+    """N >= 128 runs the fused shared-memory sweep (160: a ragged k-tile)."""
     L = 1.5 * N
     h = L / N
     from paper_1709_06350_gb300 import synth
@@ -58,8 +59,9 @@ def test_sweep_parity(R, O, N, rule):
     assert rel_max(host(th), ref) < 1e-12
 
 
-def test_sweep_fp32_tracks_fp64(R, O):
-    N, L = 32, 32.0
+@pytest.mark.parametrize("N", [32, 128])
+def test_sweep_fp32_tracks_fp64(R, O, N):
+    L = float(N)
     h = L / N
     from paper_1709_06350_gb300 import synth
     t0 = synth.smooth_field(N, 5, 0.3, kmax=2)
