@@ -150,10 +150,12 @@ k_rb_sweep_fused(const T *__restrict__ src, T *__restrict__ dst, const T *__rest
         }
     };
 
-    // prologue: OLD planes i0-2 .. i0+1 in slots 0..3, RED plane i0-1 in slot 0
+    // prologue: OLD planes i0-2 .. i0+1 in slots 0..3; RED planes i0-1, i0
+    // in slots 0, 1 (plane p lives in OLD slot (p-i0+2)&3, RED slot (p-i0+1)%3)
     for (int d = 0; d < 4; ++d) load_old(d, i0 - 2 + d);
     __syncthreads();
     red_plane(0, 0, 1, 2, i0 - 1);
+    red_plane(1, 1, 2, 3, i0);
 
     for (int s = i0; s < i1; ++s) {
         const int u = s - i0;
