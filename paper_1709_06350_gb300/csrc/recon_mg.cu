@@ -60,26 +60,48 @@ k_rb_pass(const T *__restrict__ src, T *__restrict__ dst, const T *__restrict__ 
 // Fused sweep: both colour passes in one kernel, src -> dst, with the same
 // snapshot semantics as two k_rb_pass launches.  A CTA owns a TJ x TK tile
 // of (j, k) and streams a chunk of planes along i through shared memory:
-//   OLD  4 planes (i-1 .. i+2) of src, tile + 2-cell halo
-//   RED  3 planes (i-1 .. i+1) of red-new values, tile + 1-cell halo
-// At step s it loads OLD plane s+2, updates the red cells of plane s+1 on
-// the tile + 1 halo (they read only OLD values), then updates the black
-// cells of plane s on the tile (faces from RED, edges and centre from OLD)
-// and writes plane s.  DRAM traffic: read src and g once, write dst once.
+//   OLD  ring of 5 planes of src, tile + 2-cell halo (planes s-1 .. s+2 in
+//        use, plane s+3 arriving by cp.async while step s computes)
+//   RED  ring of 3 planes of red-new values, tile + 1-cell halo
+// Step s: update the red cells of plane s+1 on the tile + 1 halo (they read
+// only OLD values), then the black cells of plane s on the tile (faces from
+// RED, edges and centre from OLD) and write plane s.  DRAM traffic: src and
+// g read once, dst written once.  The linear variant (LIN) relaxes J e = f:
+// the staged unknown is e, a second OLD ring holds theta (cofactors of
+// I + H theta at every cell), and g is f.
 // Requires N >= kFusedMinN (so one wrap suffices for every halo index).
 // ----------------------------------------------------------------------
 constexpr int kTJ = 16, kTK = 64;
 constexpr int kFusedMinN = 128;
 constexpr int kOJ = kTJ + 4, kOK = kTK + 4;   // OLD plane extent
 constexpr int kRJ = kTJ + 2, kRK = kTK + 2;   // RED plane extent
+constexpr int kFT = 256;                      // threads per CTA
+constexpr int kOElem = kOJ * kOK;             // 1360 elements per OLD plane
+constexpr int kLoadsPerThread = (kOElem + kFT - 1) / kFT;   // 6
+constexpr int kOSlots = 5, kRSlots = 3;
 
-template <typename T>
+template <typename T, bool LIN>
 struct FusedSmem {
-    T old_[4][kOJ][kOK];
-    T red_[3][kRJ][kRK];
+    T old_[kOSlots][kOJ][kOK];
+    T red_[kRSlots][kRJ][kRK];
+    T th_[LIN ? kOSlots : 1][LIN ? kOJ : 1][LIN ? kOK : 1];
 };
 
 __device__ __forceinline__ int wrap1(int x, int N) { return x < 0 ? x + N : (x >= N ? x - N : x); }
+
+__device__ __forceinline__ void cp_async_elem(float *sdst, const float *gsrc)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gsrc));
+}
+__device__ __forceinline__ void cp_async_elem(double *sdst, const double *gsrc)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gsrc));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int K>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(K)); }
 
 // 19-point neighbourhood from a shared plane triple (planes m, c, p) at
 // local (r, q) of arrays with row length K.
@@ -110,65 +132,102 @@ __device__ __forceinline__ Nb19<T> nb_from(const T (*pm)[K], const T (*pc)[K], c
     return v;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256)
-k_rb_sweep_fused(const T *__restrict__ src, T *__restrict__ dst, const T *__restrict__ g,
-                 const double *__restrict__ cptr, double cval, int N, int CI, T ih2, T h2_6,
-                 int rule)
+// The cell update of one colour: nonlinear (eq. update) or linear Gauss-Seidel on J.
+template <typename T, bool LIN>
+__device__ __forceinline__ T cell_update(const Nb19<T> &nb, const Nb19<T> *thn, T rhs, T ih2,
+                                         T h2_6, int rule)
+{
+    if constexpr (LIN) {
+        const Cof<T> a = cofactors(*thn, ih2);
+        const T Je = jac_apply(a, nb, ih2);
+        const T diag = T(-2) * (a.xx + a.yy + a.zz) * ih2;
+        return nb.c + (rhs - Je) / diag;
+    } else {
+        T s, p, q;
+        cubic_coeffs(nb, ih2, rhs, s, p, q);
+        return point_update(nb.c, h2_6, s, p, q, rule);
+    }
+}
+
+template <typename T, bool LIN>
+__global__ void __launch_bounds__(kFT)
+k_sweep_fused(const T *__restrict__ src, T *__restrict__ dst, const T *__restrict__ g,
+              const T *__restrict__ th, const double *__restrict__ cptr, double cval, int N,
+              int CI, T ih2, T h2_6, int rule)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    FusedSmem<T> &S = *reinterpret_cast<FusedSmem<T> *>(smem_raw);
-    const T c = (T)(cptr ? *cptr : cval);
+    FusedSmem<T, LIN> &S = *reinterpret_cast<FusedSmem<T, LIN> *>(smem_raw);
+    const T c = LIN ? T(0) : (T)(cptr ? *cptr : cval);
     const int k0 = blockIdx.x * kTK, j0 = blockIdx.y * kTJ, i0 = blockIdx.z * CI;
     const int i1 = min(i0 + CI, N);
     const int tid = threadIdx.x;
     const unsigned NN = (unsigned)N * (unsigned)N;
 
-    auto load_old = [&](int slot, int plane) {
+    // in-plane offsets of this thread's OLD elements (the same for every plane)
+    unsigned goff[kLoadsPerThread];
+    int soff[kLoadsPerThread];
+#pragma unroll
+    for (int t = 0; t < kLoadsPerThread; ++t) {
+        const int e = tid + t * kFT;
+        const int r = e / kOK, q = e - r * kOK;
+        soff[t] = e < kOElem ? e : -1;
+        goff[t] = (unsigned)wrap1(j0 - 2 + (r < kOJ ? r : 0), N) * (unsigned)N +
+                  (unsigned)wrap1(k0 - 2 + q, N);
+    }
+    auto issue_plane = [&](int slot, int plane) {
         const unsigned pb = (unsigned)wrap1(plane, N) * NN;
-        for (int e = tid; e < kOJ * kOK; e += 256) {
-            const int r = e / kOK, q = e - r * kOK;
-            const unsigned gj = (unsigned)wrap1(j0 - 2 + r, N), gk = (unsigned)wrap1(k0 - 2 + q, N);
-            S.old_[slot][r][q] = src[pb + gj * (unsigned)N + gk];
+        T *so = &S.old_[slot][0][0];
+#pragma unroll
+        for (int t = 0; t < kLoadsPerThread; ++t)
+            if (soff[t] >= 0) cp_async_elem(so + soff[t], src + pb + goff[t]);
+        if constexpr (LIN) {
+            T *st = &S.th_[slot][0][0];
+#pragma unroll
+            for (int t = 0; t < kLoadsPerThread; ++t)
+                if (soff[t] >= 0) cp_async_elem(st + soff[t], th + pb + goff[t]);
         }
+        cp_async_commit();
     };
     // red cells of plane p on the tile + 1 halo (RED local (r, q) = OLD (r+1, q+1))
     auto red_plane = [&](int rslot, int om, int oc, int op, int p) {
         const int pw = wrap1(p, N);
         const unsigned pb = (unsigned)pw * NN;
-        for (int e = tid; e < kRJ * (kRK / 2); e += 256) {
+        for (int e = tid; e < kRJ * (kRK / 2); e += kFT) {
             const int r = e / (kRK / 2), m = e - r * (kRK / 2);
             const int gj = j0 - 1 + r;
             const int kfirst = k0 - 1 + 2 * m;
             const int q = 2 * m + ((pw + gj + kfirst) & 1);   // the red cell of the pair
             const int gk = k0 - 1 + q;
             const Nb19<T> nb = nb_from<T, kOK>(S.old_[om], S.old_[oc], S.old_[op], r + 1, q + 1);
-            T s, pp, qq;
-            cubic_coeffs(nb, ih2, g[pb + (unsigned)wrap1(gj, N) * (unsigned)N + (unsigned)wrap1(gk, N)] + c,
-                         s, pp, qq);
-            S.red_[rslot][r][q] = point_update(nb.c, h2_6, s, pp, qq, rule);
+            Nb19<T> thn;
+            if constexpr (LIN) thn = nb_from<T, kOK>(S.th_[om], S.th_[oc], S.th_[op], r + 1, q + 1);
+            const T rhs = g[pb + (unsigned)wrap1(gj, N) * (unsigned)N + (unsigned)wrap1(gk, N)] + c;
+            S.red_[rslot][r][q] = cell_update<T, LIN>(nb, &thn, rhs, ih2, h2_6, rule);
         }
     };
 
-    // prologue: OLD planes i0-2 .. i0+1 in slots 0..3; RED planes i0-1, i0
-    // in slots 0, 1 (plane p lives in OLD slot (p-i0+2)&3, RED slot (p-i0+1)%3)
-    for (int d = 0; d < 4; ++d) load_old(d, i0 - 2 + d);
+    // prologue: OLD planes i0-2 .. i0+2 (plane p in slot (p - i0 + 2) % 5),
+    // RED planes i0-1, i0 (plane p in slot (p - i0 + 1) % 3)
+    for (int d = 0; d < 4; ++d) issue_plane(d, i0 - 2 + d);
+    cp_async_wait<0>();
     __syncthreads();
+    issue_plane(4, i0 + 2);
     red_plane(0, 0, 1, 2, i0 - 1);
     red_plane(1, 1, 2, 3, i0);
 
     for (int s = i0; s < i1; ++s) {
         const int u = s - i0;
+        __syncthreads();                                  // slot of plane s-2 is free
+        issue_plane((u + 5) % kOSlots, s + 3);            // prefetch for the next step
+        cp_async_wait<1>();                               // plane s+2 has landed
         __syncthreads();
-        load_old(u & 3, s + 2);
-        __syncthreads();
-        red_plane((u + 2) % 3, (u + 2) & 3, (u + 3) & 3, u & 3, s + 1);
+        red_plane((u + 2) % 3, (u + 2) % kOSlots, (u + 3) % kOSlots, (u + 4) % kOSlots, s + 1);
         __syncthreads();
         // black cells of plane s on the tile; write the plane
-        const int om = (u + 1) & 3, oc = (u + 2) & 3, op = (u + 3) & 3;
+        const int om = (u + 1) % kOSlots, oc = (u + 2) % kOSlots, op = (u + 3) % kOSlots;
         const int rm = u % 3, rc = (u + 1) % 3, rp = (u + 2) % 3;
         const unsigned pb = (unsigned)s * NN;
-        for (int e = tid; e < kTJ * (kTK / 2); e += 256) {
+        for (int e = tid; e < kTJ * (kTK / 2); e += kFT) {
             const int r = e / (kTK / 2), m = e - r * (kTK / 2);
             const int gj = j0 + r, gk0 = k0 + 2 * m;
             if (gj >= N || gk0 >= N) continue;
@@ -183,25 +242,27 @@ k_rb_sweep_fused(const T *__restrict__ src, T *__restrict__ dst, const T *__rest
             nb.ym = S.red_[rc][r][qb + 1];
             nb.zp = S.red_[rc][r + 1][qb + 2];
             nb.zm = S.red_[rc][r + 1][qb];
+            Nb19<T> thn;
+            if constexpr (LIN) thn = nb_from<T, kOK>(S.th_[om], S.th_[oc], S.th_[op], r + 2, qb + 2);
             const unsigned gb = pb + (unsigned)gj * (unsigned)N + (unsigned)k0;
-            T sv, pv, qv;
-            cubic_coeffs(nb, ih2, g[gb + qb] + c, sv, pv, qv);
-            const T vb = point_update(nb.c, h2_6, sv, pv, qv, rule);
+            const T vb = cell_update<T, LIN>(nb, &thn, g[gb + qb] + c, ih2, h2_6, rule);
             const T vr = S.red_[rc][r + 1][qr + 1];
             dst[gb + qb] = vb;
             dst[gb + qr] = vr;
         }
     }
+    cp_async_wait<0>();   // drain the last prefetch before the CTA exits
 }
 
-template <typename T>
-static cudaError_t fused_sweep_launch(int N, const T *src, T *dst, const T *g, const double *cptr,
-                                      double cval, T ih2, T h2_6, int rule, cudaStream_t s)
+template <typename T, bool LIN>
+static cudaError_t fused_sweep_launch(int N, const T *src, T *dst, const T *g, const T *th,
+                                      const double *cptr, double cval, T ih2, T h2_6, int rule,
+                                      cudaStream_t s)
 {
     static bool attr_set = false;
-    const size_t smem = sizeof(FusedSmem<T>);
+    const size_t smem = sizeof(FusedSmem<T, LIN>);
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_rb_sweep_fused<T>,
+        cudaError_t e = cudaFuncSetAttribute(k_sweep_fused<T, LIN>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr_set = true;
@@ -209,7 +270,7 @@ static cudaError_t fused_sweep_launch(int N, const T *src, T *dst, const T *g, c
     const int CI = N >= 512 ? 64 : (N >= 256 ? 32 : 16);
     const dim3 grid((N + kTK - 1) / kTK, (N + kTJ - 1) / kTJ, (N + CI - 1) / CI);
     note_launch();
-    k_rb_sweep_fused<T><<<grid, 256, smem, s>>>(src, dst, g, cptr, cval, N, CI, ih2, h2_6, rule);
+    k_sweep_fused<T, LIN><<<grid, kFT, smem, s>>>(src, dst, g, th, cptr, cval, N, CI, ih2, h2_6, rule);
     return cudaGetLastError();
 }
 
@@ -221,7 +282,7 @@ cudaError_t sweep(int N, double h, int rule, T *t, const T *g, const double *cpt
     if (N >= kFusedMinN) {
         T *a = t, *b = work;
         for (int it = 0; it < sweeps; ++it) {
-            const cudaError_t e = fused_sweep_launch<T>(N, a, b, g, cptr, cval, ih2, h2_6, rule, s);
+            const cudaError_t e = fused_sweep_launch<T, false>(N, a, b, g, (const T *)nullptr, cptr, cval, ih2, h2_6, rule, s);
             if (e != cudaSuccess) return e;
             T *tmp = a;
             a = b;
@@ -730,6 +791,19 @@ static cudaError_t lin_sweep(int N, double h, float *e, const float *f, const fl
                              int sweeps, float *work, cudaStream_t s)
 {
     const float ih2 = (float)(1.0 / (h * h));
+    if (N >= kFusedMinN) {
+        float *a = e, *b = work;
+        for (int it = 0; it < sweeps; ++it) {
+            const cudaError_t err = fused_sweep_launch<float, true>(N, a, b, f, th, nullptr, 0.0, ih2,
+                                                                   0.0f, 0, s);
+            if (err != cudaSuccess) return err;
+            float *tmp = a;
+            a = b;
+            b = tmp;
+        }
+        if (a != e) return cudaMemcpyAsync(e, a, sizeof(float) * (size_t)N * N * N, cudaMemcpyDeviceToDevice, s);
+        return cudaSuccess;
+    }
     for (int it = 0; it < sweeps; ++it) {
         note_launch(2);
         k_lin_pass<<<row_grid(N), row_block(), 0, s>>>(e, work, f, th, N, ih2, 0);

@@ -166,7 +166,8 @@ def test_solve_delta_zero_is_exactly_zero(R):
     s.close()
 
 
-@pytest.mark.parametrize("N,L,sig,Rs", [(32, 100.0, 0.5, 5.0), (48, 48.0, 1.0, 2.0)])
+@pytest.mark.parametrize("N,L,sig,Rs", [(32, 100.0, 0.5, 5.0), (48, 48.0, 1.0, 2.0),
+                                        (128, 256.0, 0.8, 4.0)])
 def test_solve_f64_parity(R, O, N, L, sig, Rs):
     b, _, _ = zeldovich_density(O, N, L, sig, Rs, 1000 + N)
     ref, info = O.solve(b, L, tol=1e-10, max_cycles=40)
@@ -181,8 +182,10 @@ def test_solve_f64_parity(R, O, N, L, sig, Rs):
     s.close()
 
 
-@pytest.mark.parametrize("N,L,sig,Rs", [(32, 100.0, 0.5, 5.0), (64, 64.0, 1.0, 2.0)])
+@pytest.mark.parametrize("N,L,sig,Rs", [(32, 100.0, 0.5, 5.0), (64, 64.0, 1.0, 2.0),
+                                        (128, 256.0, 0.8, 4.0)])
 def test_solve_mixed_parity(R, O, N, L, sig, Rs):
+    """N = 128 runs the fused FP32 FAS and linear smoothers."""
     b, _, _ = zeldovich_density(O, N, L, sig, Rs, 2000 + N)
     ref, info = O.solve(b, L, tol=1e-10, max_cycles=40)
     s = R.Solver(N, L, R.RECON_MIXED)
