@@ -169,7 +169,7 @@ def main():
         n = args.kernel_only
         roof = kernel_roofline(recon, torch, n, float(n), torch.device("cuda", 0),
                                torch.cuda.current_stream())
-        print(json.dumps({"kernel_only": n, **roof}), flush=True)
+        print(json.dumps({"kernel_only": n, "kernels": roof}), flush=True)
         return 0
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -295,9 +295,9 @@ def main():
         s64.close()
         del p64
 
-    # ---- roofline of the dominant kernel: the FP32 red-black smoother pass,
-    # timed on the level-0 FP32 arrays with CUDA events on its own stream
-    roof = kernel_roofline(recon, torch, N, L, dev, stream)
+    # ---- rooflines of the two FP32 smoothers, timed in isolation at N^3
+    kern = kernel_roofline(recon, torch, N, L, dev, stream)
+    roof = dict(kern[0])
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -331,6 +331,7 @@ def main():
             "fp64_path": fp64,
             "gs_cell_updates_per_s": roof.pop("cell_updates_per_s", None),
             "roofline": roof,
+            "other_kernels": kern[1:],
             "gpu_launches": launches,
             "clocks": clk.summary(),
             "e2e": e2e,
@@ -343,12 +344,23 @@ def main():
     return 0
 
 
-def kernel_roofline(recon, torch, N, L, dev, stream):
-    """FP32 smoother pass at N^3: average duration over repeated launches.
+def _time_launches(torch, stream, fn, reps):
+    fn(2)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    fn(reps)
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / 1e3 / reps
 
-    Algorithmic bytes of one colour pass: the FP32 smoother moves 12 B per
-    cell per full sweep at minimum (read theta, read b, write theta), i.e.
-    6 B per cell per colour pass."""
+
+def kernel_roofline(recon, torch, N, L, dev, stream):
+    """The two FP32 smoothers at N^3, each timed in isolation with CUDA events
+    on its stream (one launch = one fused red+black sweep for N >= 128).
+
+    Algorithmic bytes per sweep: FAS smoother 12 B/cell (read theta and b,
+    write theta); linear smoother 16 B/cell (read theta, e, f; write e)."""
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -357,27 +369,28 @@ def kernel_roofline(recon, torch, N, L, dev, stream):
     hbm = peaks.get("hbm_gbs")
     src = "measured (MEASURED_PEAKS.json hbm_gbs, burst)" if hbm else "fallback 6800 GB/s"
     hbm = hbm or 6800.0
+    from paper_1709_06350_gb300 import synth
     h = L / N
-    th = torch.zeros((N, N, N), dtype=torch.float32, device=dev)
-    g = torch.ones_like(th)
+    th = torch.from_numpy(synth.smooth_field(N, 1, 0.3 * h * h, kmax=4)).to(dev, torch.float32)
+    g = torch.from_numpy(1.0 + synth.smooth_field(N, 2, 0.4, kmax=4)).to(dev, torch.float32)
     work = torch.empty_like(th)
     reps = 10
-    recon.recon_step_sweep(th, g, 0.0, h, sweeps=2, work=work, stream=stream)
-    torch.cuda.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    recon.recon_step_sweep(th, g, 0.0, h, sweeps=reps, work=work, stream=stream)
-    b.record(stream)
-    torch.cuda.synchronize()
-    per_launch_s = a.elapsed_time(b) / 1e3 / (2 * reps)
-    alg_bytes = 6.0 * N ** 3
-    achieved = alg_bytes / per_launch_s / 1e9
-    del th, g, work
-    return {"kernel": "k_rb_pass<float> (FP32 red-black smoother, one colour pass)",
-            "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": None, "peak_source": src,
-            "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": per_launch_s * 1e3,
-            "cell_updates_per_s": N ** 3 / (2 * per_launch_s)}
+    t_fas = _time_launches(torch, stream, lambda k: recon.recon_step_sweep(
+        th, g, 0.0, h, sweeps=k, work=work, stream=stream), reps)
+    e = torch.zeros_like(th)
+    t_lin = _time_launches(torch, stream, lambda k: recon.recon_step_linear_sweep(
+        e, g, th, h, sweeps=k, work=work, stream=stream), reps)
+    del th, g, work, e
+    out = []
+    for name, t, bpc in (("k_sweep_fused<float, FAS> (FP32 red-black Newton smoother, one sweep)", t_fas, 12.0),
+                         ("k_sweep_fused<float, LIN> (FP32 red-black smoother of J e = f, one sweep)", t_lin, 16.0)):
+        alg = bpc * N ** 3
+        ach = alg / t / 1e9
+        out.append({"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                    "frac": ach / hbm, "traffic": None, "peak_source": src,
+                    "algorithmic_bytes_per_launch": alg, "avg_launch_ms": t * 1e3,
+                    "cell_updates_per_s": N ** 3 / t})
+    return out
 
 
 if __name__ == "__main__":

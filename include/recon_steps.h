@@ -84,6 +84,16 @@ recon_status recon_step_coarse_solve_noalloc(int N, double h, int prec, int rule
 recon_status recon_step_cic_cells(const double *pos, long long n, int N, double L,
                                   int *cells, double *frac, void *stream);
 
+/* `sweeps` red-black Gauss-Seidel sweeps on the linear system J(theta) e = f
+ * (FP32 grids), the smoother of the mixed-precision defect correction:
+ * e_c += (f - J e)_c / J_cc with J_cc = -2 (adj_xx + adj_yy + adj_zz) / h^2,
+ * red then black, each colour reading the values held at the start of its
+ * pass.  theta: the FP32 potential whose cofactors define J.  work: N^3
+ * float scratch.  N even. */
+recon_status recon_step_linear_sweep(int N, double h, float *e, const float *f,
+                                     const float *theta, int sweeps, float *work,
+                                     void *stream);
+
 /* J v = sum_ab adj(I + H theta)_ab D_ab v, the linearisation of
  * det(I + H theta) in theta (FP64). */
 recon_status recon_step_jacobian_apply(int N, double h, const double *theta,

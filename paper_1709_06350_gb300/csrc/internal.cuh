@@ -70,6 +70,8 @@ cudaError_t coarse_solve(int N, double h, int rule, T *t, const T *g, const doub
                          cudaStream_t s);
 cudaError_t jacobian_apply(int N, double h, const double *t, const double *v, double *out,
                            cudaStream_t s);
+cudaError_t linear_sweep(int N, double h, float *e, const float *f, const float *th, int sweeps,
+                         float *work, cudaStream_t s);
 
 // ---- the solvers (recon_mg.cu)
 recon_status solve_f64(recon_handle *H, const double *b, double *phi, double tol,

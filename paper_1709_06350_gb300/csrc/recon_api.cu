@@ -404,6 +404,15 @@ recon_status recon_step_cic_cells(const double *pos, long long n, int N, double 
                                                                                      : RECON_E_CUDA;
 }
 
+recon_status recon_step_linear_sweep(int N, double h, float *e, const float *f, const float *theta,
+                                     int sweeps, float *work, void *stream)
+{
+    if (!step_size_ok(N) || !(h > 0) || sweeps < 0 || !e || !f || !theta || !work)
+        return RECON_E_INVALID;
+    return linear_sweep(N, h, e, f, theta, sweeps, work, (cudaStream_t)stream) == cudaSuccess
+               ? RECON_OK : RECON_E_CUDA;
+}
+
 recon_status recon_step_jacobian_apply(int N, double h, const double *theta, const double *v,
                                        double *out, void *stream)
 {

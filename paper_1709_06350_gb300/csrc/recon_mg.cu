@@ -812,6 +812,12 @@ static cudaError_t lin_sweep(int N, double h, float *e, const float *f, const fl
     return cudaGetLastError();
 }
 
+cudaError_t linear_sweep(int N, double h, float *e, const float *f, const float *th, int sweeps,
+                         float *work, cudaStream_t s)
+{
+    return lin_sweep(N, h, e, f, th, sweeps, work, s);
+}
+
 // fH = R (f - J e), block partial sums for the mean projection.
 __global__ void __launch_bounds__(kRowThreads)
 k_lin_restrict_residual(const float *__restrict__ e, const float *__restrict__ f,

@@ -79,6 +79,7 @@ _SIGS = {
     "recon_step_coarse_solve_noalloc": (_I, [_I, _D, _I, _I, _P, _P, _D, _I, _D, _P, _P]),
     "recon_step_cic_cells": (_I, [_P, _LL, _I, _D, _P, _P, _P]),
     "recon_step_jacobian_apply": (_I, [_I, _D, _P, _P, _P, _P]),
+    "recon_step_linear_sweep": (_I, [_I, _D, _P, _P, _P, _I, _P, _P]),
 }
 EXPORTS = tuple(_SIGS)
 
@@ -280,6 +281,16 @@ def recon_step_cic_cells(pos, N, L, cells, frac, stream=None):
     _check(load().recon_step_cic_cells(_dev_ptr(pos, torch.float64), n, int(N), float(L),
                                        _dev_ptr(cells, torch.int32, 3 * n),
                                        _dev_ptr(frac, torch.float64, 3 * n), _stream(stream)))
+
+
+def recon_step_linear_sweep(e, f, theta, h, sweeps=1, work=None, stream=None):
+    import torch
+    N = e.shape[0]
+    work = torch.empty_like(e) if work is None else work
+    _check(load().recon_step_linear_sweep(N, float(h), _dev_ptr(e, torch.float32),
+                                          _dev_ptr(f, torch.float32, N ** 3),
+                                          _dev_ptr(theta, torch.float32, N ** 3), int(sweeps),
+                                          _dev_ptr(work, torch.float32, N ** 3), _stream(stream)))
 
 
 def recon_step_jacobian_apply(theta, v, h, out, stream=None):

@@ -45,6 +45,7 @@ class Workload:
 WORKLOADS = {
     "fp64-32": Workload("fp64-32", 32, 100.0, 0.5, 5.0, 1e-10, 1000),
     "zel-128": Workload("zel-128", 128, 256.0, 0.8, 4.0, 1e-10, 2000),
+    "mixed-384": Workload("mixed-384", 384, 384.0, 1.0, 2.0, 1e-8, 3002),
     "mixed-512": Workload("mixed-512", 512, 512.0, 1.0, 2.0, 1e-8, 3000),
     "mixed-1024": Workload("mixed-1024", 1024, 1024.0, 1.0, 2.0, 1e-8, 3001),
     "adjoint-256": Workload("adjoint-256", 256, 512.0, 0.8, 4.0, 1e-10, 5000),

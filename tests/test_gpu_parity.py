@@ -72,6 +72,31 @@ def test_sweep_fp32_tracks_fp64(R, O, N):
     assert rel_max(host(th), ref) < 1e-4
 
 
+@pytest.mark.parametrize("N", [6, 48, 128])
+def test_linear_sweep_vs_oracle_jacobian(R, O, N):
+    """Red-black Gauss-Seidel on J e = f against the same sweep written with
+    the oracle's sparse Jacobian (N = 128 runs the fused kernel)."""
+    L = 2.0 * N
+    h = L / N
+    from paper_1709_06350_gb300 import synth
+    t = synth.smooth_field(N, 21, 0.4 * h * h, kmax=3).astype(np.float32).astype(np.float64)
+    rng = np.random.default_rng(22)
+    f = rng.standard_normal((N,) * 3).astype(np.float32).astype(np.float64)
+    e0 = (0.1 * rng.standard_normal((N,) * 3)).astype(np.float32).astype(np.float64)
+    J = O.jacobian_matrix(t, h)
+    d = J.diagonal()
+    i, j, k = np.meshgrid(np.arange(N), np.arange(N), np.arange(N), indexing="ij")
+    red = ((i + j + k) % 2 == 0).ravel()
+    e = e0.ravel().copy()
+    for _ in range(2):
+        for col in (red, ~red):
+            upd = e + (f.ravel() - J @ e) / d
+            e = np.where(col, upd, e)
+    ev = dev(e0, torch.float32)
+    R.recon_step_linear_sweep(ev, dev(f, torch.float32), dev(t, torch.float32), h, sweeps=2)
+    assert rel_max(host(ev).ravel(), e) < 2e-5
+
+
 @pytest.mark.parametrize("N", [4, 12, 48])
 def test_residual_det_jacobian_parity(R, O, N):
     L = 2.0 * N
