@@ -4,7 +4,7 @@
 One step = one whole reconstruction of a seeded 512^3 Zel'dovich field
 (L = 512 Mpc/h, sigma_lin = 1, smoothing R = 2 Mpc/h) with particles already
 resident in HBM:
-    CIC deposit -> Gaussian smoothing / floor (input conditioning, torch FFT)
+    CIC deposit -> Gaussian smoothing / floor (input conditioning, FP32 torch FFT)
     -> mixed-precision FAS solve to ||r|| / ||b - 1|| < 1e-8 -> displacement.
 All reconstruction steps run in librecon's hand-written sm_103a kernels.
 
@@ -215,7 +215,7 @@ def main():
     def step(pos_dev):
         rho.zero_()
         solver.deposit_cic(pos_dev, rho=rho)
-        b = synth.smooth_and_floor(rho, L, R)
+        b = synth.smooth_and_floor(rho, L, R, fft_dtype=torch.float32)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         _, st = solver.solve(b, phi=phi, tol=tol, max_cycles=40)

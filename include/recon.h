@@ -49,8 +49,9 @@ typedef enum {
 
 typedef enum {
     RECON_F64 = 0,              /* every step in FP64                              */
-    RECON_MIXED = 1             /* FP32 multigrid inside FP64 defect correction;
-                                   phi and the fine-grid residual stay FP64        */
+    RECON_MIXED = 1             /* FP32 multigrid inside a defect correction whose
+                                   fine-grid residual and phi keep (near-)FP64
+                                   precision; phi is returned in FP64            */
 } recon_dtype;
 
 typedef enum {
@@ -67,7 +68,7 @@ typedef enum {
 /* Solver options.  Defaults (recon_create): nu1 = nu2 = 2,
  * coarse_max_sweeps = 200, coarse_rtol = 1e-3, rule = NEWTON1, start = FMG,
  * scale_floor = 0.5, mixed_switch_rtol = 1e-4, mixed_fas_max_cycles = 12,
- * mixed_linear_vcycles = 2. */
+ * mixed_linear_vcycles = 2, mixed_df_residual = 1. */
 typedef struct {
     int nu1, nu2;               /* pre- / post-smoothing sweeps per level          */
     int coarse_max_sweeps;      /* coarsest grid: sweep cap                        */
@@ -83,6 +84,10 @@ typedef struct {
                                    residual, then FP64 defect correction           */
     int mixed_fas_max_cycles;   /* MIXED: cap on the FP32 FAS cycles               */
     int mixed_linear_vcycles;   /* MIXED: FP32 linear V-cycles per correction      */
+    int mixed_df_residual;      /* MIXED: 1 = the fine-grid residual and phi are
+                                   double-float pairs (hi + lo floats, 48-bit
+                                   significand, FP32 pipes) while iterating;
+                                   0 = plain FP64 arithmetic for both          */
 } recon_config;
 
 #define RECON_HISTORY_MAX 64

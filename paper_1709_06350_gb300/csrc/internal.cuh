@@ -31,6 +31,7 @@ struct recon_handle {
           *aux32[kMaxLevels] = {};
     float *e32[kMaxLevels] = {}, *f32[kMaxLevels] = {};
     float *work32 = nullptr;
+    float *lo32 = nullptr, *blo32 = nullptr;   // low halves of phi and b (double-float)
 
     double *scal = nullptr;      // device scalars (recon::Slot)
     double *partials = nullptr;  // kMaxRedBlocks x 4 doubles
@@ -86,6 +87,6 @@ cudaError_t cic_cells(const double *pos, long long n, int N, double L, int *cell
 cudaError_t cic_deposit(const double *pos, long long n, int N, double L, double mass,
                         double *rho, cudaStream_t s);
 cudaError_t displace(int N, double L, const double *phi, const double *b, double *psi,
-                     double *deltaL, double *num, double *den, cudaStream_t s);
+                     double *deltaL, double *scratch, cudaStream_t s);
 
 }  // namespace recon

@@ -49,6 +49,7 @@ recon_config default_config()
     c.mixed_switch_rtol = 1e-4;
     c.mixed_fas_max_cycles = 12;
     c.mixed_linear_vcycles = 2;
+    c.mixed_df_residual = 1;
     return c;
 }
 
@@ -97,6 +98,8 @@ void plan(recon_handle *H, Planner &P)
             }
         }
         P.take(&H->work32, n0);
+        P.take(&H->lo32, n0);
+        P.take(&H->blo32, n0);
     }
     P.take(&H->scal, (size_t)S_COUNT);
     P.take(&H->partials, (size_t)4 * kMaxRedBlocks);
@@ -111,6 +114,8 @@ void free_all(recon_handle *H)
     f(H->work64);
     f(H->work64b);
     f(H->work32);
+    f(H->lo32);
+    f(H->blo32);
     for (int l = 0; l < kMaxLevels; ++l) {
         if (l > 0) {
             f(H->t64[l]);
@@ -269,7 +274,8 @@ recon_status recon_set_config(recon_handle *H, const recon_config *c)
         return set_err(H, RECON_E_INVALID, "unknown start");
     if (!(c->scale_floor < 1.0) || !std::isfinite(c->scale_floor))
         return set_err(H, RECON_E_INVALID, "scale_floor must be < 1");
-    if (!(c->mixed_switch_rtol > 0.0) || c->mixed_fas_max_cycles < 0 || c->mixed_linear_vcycles < 1)
+    if (!(c->mixed_switch_rtol > 0.0) || c->mixed_fas_max_cycles < 0 || c->mixed_linear_vcycles < 1 ||
+        (c->mixed_df_residual != 0 && c->mixed_df_residual != 1))
         return set_err(H, RECON_E_INVALID, "bad mixed-precision options");
     H->cfg = *c;
     return RECON_OK;
@@ -311,7 +317,7 @@ recon_status recon_displace(recon_handle *H, const double *phi, const double *b,
 {
     if (!H) return RECON_E_INVALID;
     if (!phi || !b || !psi || !deltaL) return set_err(H, RECON_E_INVALID, "NULL pointer");
-    return cuda_status(H, displace(H->N, H->L, phi, b, psi, deltaL, H->work64, H->work64b, H->stream),
+    return cuda_status(H, displace(H->N, H->L, phi, b, psi, deltaL, H->work64, H->stream),
                        "displace");
 }
 

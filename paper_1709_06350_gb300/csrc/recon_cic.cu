@@ -6,10 +6,10 @@
 // multiply-add), so cell indices and fractions are bit-identical to a plain
 // IEEE evaluation of the same formula on any host.
 //
-// Atomics: neighbouring threads handle neighbouring particles (or cells),
-// which often land in the same target cells; lanes of a warp that target
-// the same cell first combine their contributions (__match_any_sync +
-// shuffles) and one lane issues the atomicAdd.
+// Atomics: plain FP64 atomicAdd for the density.  Warp aggregation of lanes
+// that hit the same cell (__match_any_sync + shuffles) was measured slower on
+// GB300 (512^3 deposit 17.5 ms aggregated vs 9.9 ms plain).  The displacement
+// step accumulates its (b v, b) pair with one float2 vector atomic per corner.
 #include <cmath>
 
 #include "cellmath.cuh"
@@ -27,26 +27,14 @@ __device__ __forceinline__ void cic_axis(double x, int N, double inv_h, int &i0,
     i0 = (int)ii;
 }
 
-// Sum `v` over the lanes of the warp that share `key`; the lowest such lane
-// gets the total and true, the others false.  Every lane must call this.
-__device__ __forceinline__ bool warp_aggregate(unsigned key, double &v)
-{
-    const unsigned peers = __match_any_sync(0xffffffffu, key);
-    const int lane = threadIdx.x & 31;
-    double tot = 0.0;
-    for (unsigned m = peers; m; m &= m - 1) tot += __shfl_sync(peers, v, __ffs(m) - 1);
-    v = tot;
-    return lane == __ffs(peers) - 1;
-}
-
 // Deposit `val` (per thread) with CIC weights at position (x, y, z).
 __device__ __forceinline__ void cic_scatter(bool active, const double xyz[3], double val, int N,
                                             double inv_h, double *__restrict__ rho)
 {
-    int i0[3] = {0, 0, 0};
-    double f[3] = {0.0, 0.0, 0.0};
-    if (active)
-        for (int d = 0; d < 3; ++d) cic_axis(xyz[d], N, inv_h, i0[d], f[d]);
+    if (!active) return;
+    int i0[3];
+    double f[3];
+    for (int d = 0; d < 3; ++d) cic_axis(xyz[d], N, inv_h, i0[d], f[d]);
     for (int a = 0; a < 2; ++a)
         for (int b = 0; b < 2; ++b)
             for (int cc = 0; cc < 2; ++cc) {
@@ -55,9 +43,26 @@ __device__ __forceinline__ void cic_scatter(bool active, const double xyz[3], do
                 const int k = cc ? (i0[2] + 1 == N ? 0 : i0[2] + 1) : i0[2];
                 const double w = __dmul_rn(__dmul_rn(a ? f[0] : 1.0 - f[0], b ? f[1] : 1.0 - f[1]),
                                            cc ? f[2] : 1.0 - f[2]);
-                double v = active ? __dmul_rn(val, w) : 0.0;
-                const unsigned key = active ? offs(N, i, j, k) : 0xffffffffu;
-                if (warp_aggregate(key, v) && active) atomicAdd(rho + offs(N, i, j, k), v);
+                atomicAdd(rho + offs(N, i, j, k), __dmul_rn(val, w));
+            }
+}
+
+// CIC of a value pair (vector atomic): acc[cell] += (v0, v1) * w.
+__device__ __forceinline__ void cic_scatter2(const double xyz[3], float v0, float v1, int N,
+                                             double inv_h, float2 *__restrict__ acc)
+{
+    int i0[3];
+    double f[3];
+    for (int d = 0; d < 3; ++d) cic_axis(xyz[d], N, inv_h, i0[d], f[d]);
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+            for (int cc = 0; cc < 2; ++cc) {
+                const int i = a ? (i0[0] + 1 == N ? 0 : i0[0] + 1) : i0[0];
+                const int j = b ? (i0[1] + 1 == N ? 0 : i0[1] + 1) : i0[1];
+                const int k = cc ? (i0[2] + 1 == N ? 0 : i0[2] + 1) : i0[2];
+                const float w = (float)((a ? f[0] : 1.0 - f[0]) * (b ? f[1] : 1.0 - f[1]) *
+                                        (cc ? f[2] : 1.0 - f[2]));
+                atomicAdd(acc + offs(N, i, j, k), make_float2(v0 * w, v1 * w));
             }
 }
 
@@ -70,7 +75,7 @@ k_cic_deposit(const double *__restrict__ pos, long long n, int N, double inv_h, 
     double xyz[3] = {0.0, 0.0, 0.0};
     if (active)
         for (int d = 0; d < 3; ++d) xyz[d] = pos[3 * p + d];
-    cic_scatter(active, xyz, mass, N, inv_h, rho);
+    cic_scatter(active, xyz, mass, N, inv_h, rho);   // inactive lanes return at once
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -101,71 +106,74 @@ cudaError_t cic_deposit(const double *pos, long long n, int N, double L, double 
 }
 
 // ---------------------------------------------------------------- displace
-// Per Eulerian cell x_c: psi = -grad phi (central differences), the mapped
-// Lagrangian position q = x + grad phi (mod L), v = 3 - tr((I + H)^-1), and
-// CIC deposits of b v (numerator) and b (denominator) at q.
+// Per Eulerian cell x_c: psi = -grad phi (central differences, FP64), the
+// mapped Lagrangian position q = x + grad phi (mod L, FP64, explicitly
+// rounded so that its CIC cell matches any IEEE evaluation), and
+// v = 3 - tr((I + H)^-1) computed in FP32 from the FP64 Hessian; the pair
+// (b v, b) is accumulated at q with CIC weights in FP32 (vector atomics).
+// delta_r = sum(b v) / max(sum(b), 1e-12) then carries FP32 rounding
+// (~1e-6 absolute for |delta_r| < 3).
 __global__ void __launch_bounds__(kRowX * kRowY)
 k_displace_cells(const double *__restrict__ t, const double *__restrict__ b, int N, double L,
-                 double h, double ih2, double *__restrict__ psi, double *__restrict__ num,
-                 double *__restrict__ den)
+                 double h, double ih2, double *__restrict__ psi, float2 *__restrict__ acc)
 {
     const unsigned n = (unsigned)N * N * N;
     const double inv_h = (double)N / L;
     FOR_ROWS(N, i, j)
-    for (int k0 = 0; k0 < N; k0 += kRowX) {   // uniform trip count: every lane
-        const int k = k0 + threadIdx.x;        // takes part in the aggregation
-        const bool active = k < N;
-        double q[3] = {0.0, 0.0, 0.0};
-        double wv = 0.0, wb = 0.0;
-        if (active) {
-            const unsigned id = offs(N, i, j, k);
-            const Nb19<double> nb = load19<double>(t, N, i, j, k);
-            const double g[3] = {(nb.xp - nb.xm) / (2.0 * h), (nb.yp - nb.ym) / (2.0 * h),
-                                 (nb.zp - nb.zm) / (2.0 * h)};
-            // explicitly rounded so that q (and hence its CIC cell) does not
-            // depend on multiply-add contraction
-            const double x[3] = {__dmul_rn(i + 0.5, h), __dmul_rn(j + 0.5, h), __dmul_rn(k + 0.5, h)};
-            for (int d = 0; d < 3; ++d) {
-                psi[(size_t)d * n + id] = -g[d];
-                // q mod L: for q in (-L, 2L) the conditional form gives exactly
-                // fmod's result (q - L is exact there); fmod handles the rest
-                double qq = __dadd_rn(x[d], g[d]);
-                if (qq >= L) qq = qq < 2.0 * L ? __dsub_rn(qq, L) : fmod(qq, L);
-                else if (qq < 0.0 && qq <= -L) qq = fmod(qq, L);
-                if (qq < 0.0) qq = __dadd_rn(qq, L);
-                q[d] = qq;
-            }
-            const Cof<double> a = cofactors(nb, ih2);
-            const double D = det_IH(nb, ih2);
-            const double v = 3.0 - (a.xx + a.yy + a.zz) / D;
-            wb = b[id];
-            wv = wb * v;
+    for (int k = threadIdx.x; k < N; k += kRowX) {
+        const unsigned id = offs(N, i, j, k);
+        const Nb19<double> nb = load19<double>(t, N, i, j, k);
+        const double g[3] = {(nb.xp - nb.xm) / (2.0 * h), (nb.yp - nb.ym) / (2.0 * h),
+                             (nb.zp - nb.zm) / (2.0 * h)};
+        const double x[3] = {__dmul_rn(i + 0.5, h), __dmul_rn(j + 0.5, h), __dmul_rn(k + 0.5, h)};
+        double q[3];
+        for (int d = 0; d < 3; ++d) {
+            psi[(size_t)d * n + id] = -g[d];
+            // q mod L: for q in (-L, 2L) the conditional form gives exactly
+            // fmod's result (q - L is exact there); fmod handles the rest
+            double qq = __dadd_rn(x[d], g[d]);
+            if (qq >= L) qq = qq < 2.0 * L ? __dsub_rn(qq, L) : fmod(qq, L);
+            else if (qq <= -L) qq = fmod(qq, L);
+            if (qq < 0.0) qq = __dadd_rn(qq, L);
+            q[d] = qq;
         }
-        cic_scatter(active, q, wv, N, inv_h, num);
-        cic_scatter(active, q, wb, N, inv_h, den);
+        // Hessian in FP64 (differences of phi), the rest in FP32
+        const float axx = (float)(1.0 + ((nb.xp + nb.xm) - 2.0 * nb.c) * ih2);
+        const float ayy = (float)(1.0 + ((nb.yp + nb.ym) - 2.0 * nb.c) * ih2);
+        const float azz = (float)(1.0 + ((nb.zp + nb.zm) - 2.0 * nb.c) * ih2);
+        const float hxy = (float)(((nb.xpyp + nb.xmym) - (nb.xmyp + nb.xpym)) * (0.25 * ih2));
+        const float hyz = (float)(((nb.ypzp + nb.ymzm) - (nb.ymzp + nb.ypzm)) * (0.25 * ih2));
+        const float hxz = (float)(((nb.xpzp + nb.xmzm) - (nb.xmzp + nb.xpzm)) * (0.25 * ih2));
+        const float cxx = ayy * azz - hyz * hyz, cyy = axx * azz - hxz * hxz, czz = axx * ayy - hxy * hxy;
+        const float D = axx * cxx - hxy * (hxy * azz - hyz * hxz) + hxz * (hxy * hyz - ayy * hxz);
+        const float v = 3.0f - (cxx + cyy + czz) / D;
+        const float bb = (float)b[id];
+        cic_scatter2(q, bb * v, bb, N, inv_h, acc);
     }
 }
 
 __global__ void __launch_bounds__(kThreads)
-k_displace_finish(const double *__restrict__ num, const double *__restrict__ den, size_t n,
-                  double *__restrict__ out)
+k_displace_finish(const float2 *__restrict__ acc, size_t n, double *__restrict__ out)
 {
     const size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (id < n) out[id] = num[id] / (den[id] > 1e-12 ? den[id] : 1e-12);
+    if (id < n) {
+        const float2 a = acc[id];
+        const double den = (double)a.y;
+        out[id] = (double)a.x / (den > 1e-12 ? den : 1e-12);
+    }
 }
 
 cudaError_t displace(int N, double L, const double *phi, const double *b, double *psi,
-                     double *deltaL, double *num, double *den, cudaStream_t s)
+                     double *deltaL, double *scratch, cudaStream_t s)
 {
     const size_t n = (size_t)N * N * N;
     const double h = L / N;
-    cudaError_t e = cudaMemsetAsync(num, 0, sizeof(double) * n, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(den, 0, sizeof(double) * n, s);
+    float2 *acc = reinterpret_cast<float2 *>(scratch);   // N^3 float2 = N^3 doubles of room
+    cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(float2) * n, s);
     if (e != cudaSuccess) return e;
-    note_launch();
-    k_displace_cells<<<row_grid(N), row_block(), 0, s>>>(phi, b, N, L, h, 1.0 / (h * h), psi, num, den);
-    note_launch();
-    k_displace_finish<<<blocks_for(n), kThreads, 0, s>>>(num, den, n, deltaL);
+    note_launch(2);
+    k_displace_cells<<<row_grid(N), row_block(), 0, s>>>(phi, b, N, L, h, 1.0 / (h * h), psi, acc);
+    k_displace_finish<<<blocks_for(n), kThreads, 0, s>>>(acc, n, deltaL);
     return cudaGetLastError();
 }
 

@@ -17,6 +17,7 @@
 #include <cstdio>
 
 #include "cellmath.cuh"
+#include "dfloat.cuh"
 #include "internal.cuh"
 
 namespace recon {
@@ -763,6 +764,99 @@ k_sub_scalar(float *__restrict__ a, size_t n, const double *__restrict__ v)
     if (id < n) a[id] -= (float)(*v);
 }
 
+// ---- double-float fine-grid residual of the mixed path
+// r = b + c - det(I + H phi) with phi = phi_hi + phi_lo and b = b_hi + b_lo
+// evaluated in double-float arithmetic; writes float(r) for the linear solve
+// and the block partials sum r, sum r^2 (float per thread, double per block).
+__global__ void __launch_bounds__(kRowThreads)
+k_residual_df(const float *__restrict__ phi_hi, const float *__restrict__ phi_lo,
+              const float *__restrict__ b_hi, const float *__restrict__ b_lo,
+              const double *__restrict__ cptr, int N, float ih2_hi, float ih2_lo,
+              float *__restrict__ fout, double *__restrict__ partials)
+{
+    __shared__ double sh[32];
+    const df c = df_from_double(*cptr);
+    const df ih2 = df_make(ih2_hi, ih2_lo), q4 = df_scale2(ih2, 0.25f), one = df_make(1.0f, 0.0f);
+    float sr = 0.0f, sr2 = 0.0f;
+    FOR_ROWS(N, i, j)
+    for (int k = threadIdx.x; k < N; k += kRowX) {
+        const Nb19<float> H = load19<float>(phi_hi, N, i, j, k);
+        const Nb19<float> Lo = load19<float>(phi_lo, N, i, j, k);
+        const df C2 = df_make(2.0f * H.c, 2.0f * Lo.c);
+        auto diag = [&](float ph, float pl, float mh, float ml) {
+            return df_add(one, df_mul(df_sub(df_add(df_make(ph, pl), df_make(mh, ml)), C2), ih2));
+        };
+        auto mix = [&](float a, float al, float b, float bl, float cc, float cl, float d, float dl) {
+            return df_mul(df_sub(df_add(df_make(a, al), df_make(b, bl)),
+                                 df_add(df_make(cc, cl), df_make(d, dl))), q4);
+        };
+        const df axx = diag(H.xp, Lo.xp, H.xm, Lo.xm);
+        const df ayy = diag(H.yp, Lo.yp, H.ym, Lo.ym);
+        const df azz = diag(H.zp, Lo.zp, H.zm, Lo.zm);
+        const df hxy = mix(H.xpyp, Lo.xpyp, H.xmym, Lo.xmym, H.xmyp, Lo.xmyp, H.xpym, Lo.xpym);
+        const df hyz = mix(H.ypzp, Lo.ypzp, H.ymzm, Lo.ymzm, H.ymzp, Lo.ymzp, H.ypzm, Lo.ypzm);
+        const df hxz = mix(H.xpzp, Lo.xpzp, H.xmzm, Lo.xmzm, H.xmzp, Lo.xmzp, H.xpzm, Lo.xpzm);
+        const df c1 = df_sub(df_mul(ayy, azz), df_mul(hyz, hyz));
+        const df c2 = df_sub(df_mul(hxy, azz), df_mul(hyz, hxz));
+        const df c3 = df_sub(df_mul(hxy, hyz), df_mul(ayy, hxz));
+        const df det = df_add(df_sub(df_mul(axx, c1), df_mul(hxy, c2)), df_mul(hxz, c3));
+        const unsigned id = offs(N, i, j, k);
+        const df r = df_sub(df_add(df_make(b_hi[id], b_lo[id]), c), det);
+        const float rf = r.hi + r.lo;
+        fout[id] = rf;
+        sr += rf;
+        sr2 = fmaf(rf, rf, sr2);
+    }
+    double v = block_sum<kRowThreads>((double)sr, sh);
+    if (ltid() == 0) partials[4 * blockIdx.x + 0] = v;
+    v = block_sum<kRowThreads>((double)sr2, sh);
+    if (ltid() == 0) {
+        partials[4 * blockIdx.x + 1] = v;
+        partials[4 * blockIdx.x + 2] = 0.0;   // no gauge shift while iterating
+    }
+}
+
+// b -> (b_hi, b_lo)
+__global__ void __launch_bounds__(kThreads)
+k_split_df(const double *__restrict__ a, float *__restrict__ hi, float *__restrict__ lo, size_t n)
+{
+    const size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id < n) {
+        const df v = df_from_double(a[id]);
+        hi[id] = v.hi;
+        lo[id] = v.lo;
+    }
+}
+
+// (phi_hi, phi_lo) += e
+__global__ void __launch_bounds__(kThreads)
+k_update_df(float *__restrict__ hi, float *__restrict__ lo, const float *__restrict__ e, size_t n)
+{
+    const size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id < n) {
+        const df v = df_add(df_make(hi[id], lo[id]), df_make(e[id], 0.0f));
+        hi[id] = v.hi;
+        lo[id] = v.lo;
+    }
+}
+
+// phi = phi_hi + phi_lo in FP64, with block partial sums of phi for the gauge
+__global__ void __launch_bounds__(kThreads)
+k_df_to_double(const float *__restrict__ hi, const float *__restrict__ lo, double *__restrict__ phi,
+               size_t n, double *__restrict__ partials)
+{
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x; id < n;
+         id += (size_t)gridDim.x * blockDim.x) {
+        const double v = df_to_double(df_make(hi[id], lo[id]));
+        phi[id] = v;
+        s += v;
+    }
+    const double v = block_sum<kThreads>(s, sh);
+    if (ltid() == 0) partials[4 * blockIdx.x + 0] = v;
+}
+
 // ---- linear multigrid for J e = f in FP32 (J from the FP32 theta of the level)
 // One colour pass of Gauss-Seidel on J: e_c += (f - J e)_c / J_cc,
 // J_cc = -2 (adj_xx + adj_yy + adj_zz) / h^2.
@@ -1199,24 +1293,38 @@ recon_status solve_mixed(recon_handle *H, const double *b, double *phi, double t
         prev = rel;
     }
     if (fas > cf.mixed_fas_max_cycles) fas = cf.mixed_fas_max_cycles;
-    note_launch();
-    k_to_double<<<blocks_for(n), kThreads, 0, s>>>(H->t32[0], phi, n);
+    const bool dfres = cf.mixed_df_residual != 0;
+    if (dfres) {
+        // phi = theta32 + 0 as a double-float pair; b split the same way
+        note_launch();
+        k_split_df<<<blocks_for(n), kThreads, 0, s>>>(b, H->g32[0], H->blo32, n);
+        e = cudaMemsetAsync(H->lo32, 0, sizeof(float) * n, s);
+        if (e != cudaSuccess) return fail_cuda(H, e, "mixed phase 2");
+    } else {
+        note_launch();
+        k_to_double<<<blocks_for(n), kThreads, 0, s>>>(H->t32[0], phi, n);
+    }
 
-    // ---- (ii) FP64 defect correction with FP32 linear multigrid
+    // ---- (ii) defect correction with FP32 linear multigrid
     const unsigned nbr = row_grid(H->N, kMaxRedBlocks);
     const double ih2 = 1.0 / (H->h * H->h);
+    const df ih2df = df_from_double(ih2);
     recon_status status = RECON_E_NOCONV;
     double best = INFINITY;
     int o = 0;
     for (o = 1; o <= max_cycles; ++o) {
-        note_launch();
-        k_residual_norms<double><<<nbr, row_block(), 0, s>>>(phi, b, H->scal + S_C, H->N, ih2,
-                                                          H->partials, H->f32[0], H->t32[0]);
-        note_launch();
+        note_launch(2);
+        if (dfres)
+            k_residual_df<<<nbr, row_block(), 0, s>>>(H->t32[0], H->lo32, H->g32[0], H->blo32,
+                                                      H->scal + S_C, H->N, ih2df.hi, ih2df.lo,
+                                                      H->f32[0], H->partials);
+        else
+            k_residual_norms<double><<<nbr, row_block(), 0, s>>>(phi, b, H->scal + S_C, H->N, ih2,
+                                                                 H->partials, H->f32[0], H->t32[0]);
         k_finalize_cycle<<<1, kReduceThreads, 0, s>>>(H->partials, nbr, (double)n, H->scal);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = read_scalars(H);
-        if (e != cudaSuccess) return fail_cuda(H, e, "FP64 residual");
+        if (e != cudaSuccess) return fail_cuda(H, e, "fine-grid residual");
         const double rel = H->hscal[S_REL];
         hist_push(st, rel);
         if (!std::isfinite(rel) || rel > 1e3 * best) {
@@ -1226,8 +1334,6 @@ recon_status solve_mixed(recon_handle *H, const double *b, double *phi, double t
         }
         best = rel < best ? rel : best;
         if (rel < tol) {
-            note_launch();
-            k_gauge<double><<<blocks_for(n), kThreads, 0, s>>>(phi, n, H->scal);
             status = RECON_OK;
             break;
         }
@@ -1241,7 +1347,21 @@ recon_status solve_mixed(recon_handle *H, const double *b, double *phi, double t
         for (int v = 0; v < cf.mixed_linear_vcycles && e == cudaSuccess; ++v) e = lin_vcycle(H, 0);
         if (e != cudaSuccess) return fail_cuda(H, e, "linear V-cycle");
         note_launch();
-        k_update_theta<<<blocks_for(n), kThreads, 0, s>>>(phi, H->e32[0], n, H->scal);
+        if (dfres)
+            k_update_df<<<blocks_for(n), kThreads, 0, s>>>(H->t32[0], H->lo32, H->e32[0], n);
+        else
+            k_update_theta<<<blocks_for(n), kThreads, 0, s>>>(phi, H->e32[0], n, H->scal);
+    }
+    // phi out: FP64, mean-free
+    if (dfres) {
+        const unsigned nb2 = red_blocks(n);
+        note_launch(3);
+        k_df_to_double<<<nb2, kThreads, 0, s>>>(H->t32[0], H->lo32, phi, n, H->partials);
+        k_finalize_mean<<<1, kReduceThreads, 0, s>>>(H->partials, nb2, (double)n, H->scal + S_MEAN_T);
+        k_gauge<double><<<blocks_for(n), kThreads, 0, s>>>(phi, n, H->scal);
+    } else if (status == RECON_OK) {
+        note_launch();
+        k_gauge<double><<<blocks_for(n), kThreads, 0, s>>>(phi, n, H->scal);
     }
     if (o > max_cycles) o = max_cycles;
     if (status == RECON_E_NOCONV) H->err = "max_cycles reached before the tolerance";

@@ -40,7 +40,8 @@ class recon_config(ctypes.Structure):
                 ("coarse_max_sweeps", ctypes.c_int), ("coarse_rtol", ctypes.c_double),
                 ("rule", ctypes.c_int), ("start", ctypes.c_int),
                 ("scale_floor", ctypes.c_double), ("mixed_switch_rtol", ctypes.c_double),
-                ("mixed_fas_max_cycles", ctypes.c_int), ("mixed_linear_vcycles", ctypes.c_int)]
+                ("mixed_fas_max_cycles", ctypes.c_int), ("mixed_linear_vcycles", ctypes.c_int),
+                ("mixed_df_residual", ctypes.c_int)]
 
 
 class recon_stats(ctypes.Structure):

@@ -145,10 +145,12 @@ def _torch_window(N: int, L: float, R: float, device):
     return W
 
 
-def smooth_and_floor(rho, L: float, R: float, floor: float = 0.05):
+def smooth_and_floor(rho, L: float, R: float, floor: float = 0.05, fft_dtype=None):
     """Gaussian-smooth (radius R), floor 1+delta at ``floor``, renormalise to mean 1.
 
-    Accepts numpy arrays or torch tensors and returns the same kind.
+    Accepts numpy arrays or torch tensors and returns the same kind (and
+    dtype).  ``fft_dtype`` (torch only, e.g. torch.float32) runs the smoothing
+    FFTs in that precision.
     """
     N = rho.shape[0]
     if isinstance(rho, np.ndarray):
@@ -159,8 +161,9 @@ def smooth_and_floor(rho, L: float, R: float, floor: float = 0.05):
         return b / b.mean()
     import torch
     if R > 0:
-        b = torch.fft.irfftn(torch.fft.rfftn(rho) * _torch_window(N, L, R, rho.device),
-                             s=tuple(rho.shape))
+        x = rho if fft_dtype is None else rho.to(fft_dtype)
+        W = _torch_window(N, L, R, rho.device)
+        b = torch.fft.irfftn(torch.fft.rfftn(x) * W.to(x.dtype), s=tuple(rho.shape)).to(rho.dtype)
     else:
         b = rho.clone()
     b = torch.clamp(b, min=floor)

@@ -207,13 +207,14 @@ def test_solve_f64_parity(R, O, N, L, sig, Rs):
     s.close()
 
 
-@pytest.mark.parametrize("N,L,sig,Rs", [(32, 100.0, 0.5, 5.0), (64, 64.0, 1.0, 2.0),
-                                        (128, 256.0, 0.8, 4.0)])
-def test_solve_mixed_parity(R, O, N, L, sig, Rs):
-    """N = 128 runs the fused FP32 FAS and linear smoothers."""
+@pytest.mark.parametrize("N,L,sig,Rs,dfres", [(32, 100.0, 0.5, 5.0, 1), (64, 64.0, 1.0, 2.0, 1),
+                                              (128, 256.0, 0.8, 4.0, 1), (64, 64.0, 1.0, 2.0, 0)])
+def test_solve_mixed_parity(R, O, N, L, sig, Rs, dfres):
+    """N = 128 runs the fused FP32 FAS and linear smoothers; dfres selects the
+    double-float (1) or FP64 (0) fine-grid residual."""
     b, _, _ = zeldovich_density(O, N, L, sig, Rs, 2000 + N)
     ref, info = O.solve(b, L, tol=1e-10, max_cycles=40)
-    s = R.Solver(N, L, R.RECON_MIXED)
+    s = R.Solver(N, L, R.RECON_MIXED, mixed_df_residual=dfres)
     phi, st = s.solve(dev(b), tol=1e-10, max_cycles=30)
     assert st["rel_residual"] < 1e-10
     assert rel_l2(host(phi), ref) < 1e-6
@@ -261,6 +262,8 @@ def test_displace_parity(R, O):
     s = R.Solver(N, L)
     psi, dl = s.displace(dev(t), dev(b))
     assert np.max(np.abs(host(psi) - psi_ref)) < 1e-13 * np.abs(psi_ref).max()
-    assert np.max(np.abs(host(dl) - dl_ref)) < 1e-10
+    # v = 3 - tr((I+H)^-1) and the (b v, b) accumulation are FP32 on the GPU:
+    # |delta_r| < 3 with ~8 contributions per cell gives ~1e-6 absolute
+    assert np.max(np.abs(host(dl) - dl_ref)) < 1e-5
     assert host(dl).max() < 3.0
     s.close()
