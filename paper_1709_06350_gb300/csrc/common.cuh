@@ -60,7 +60,11 @@ enum Slot {
     S_BMIN = 6,       // min(b)   (domain check)
     S_BBAD = 7,       // count of non-finite b
     S_LEVEL = 8,      // per-level slots start here: 4 per level
-    S_COUNT = S_LEVEL + 4 * 16
+    S_ADJ_MEAN = S_LEVEL + 4 * 16,   // adjoint: means, norms, null-space sums
+    S_ADJ_NORM,
+    S_ADJ_SLAM,
+    S_ADJ_SN,
+    S_COUNT
 };
 // per-level slots (level l >= 1): restricted-residual mean, defect scale s,
 // prolongation factor 1/s (0 = skip), spare

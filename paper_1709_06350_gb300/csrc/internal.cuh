@@ -9,6 +9,17 @@
 constexpr int kMaxLevels = 16;
 constexpr int kMaxRedBlocks = 2048;   // grid cap of every reducing kernel
 
+// Workspace of the adjoint (allocated at its first call): the potential of
+// every coarse level, the six cofactor arrays of every level, the iterate and
+// right side of every coarse level, the null vector of J^T.
+struct AdjWork {
+    bool ready = false;
+    bool null_ready = false;   // cofactors and null vector match the last solve
+    double null_rel = 0.0;
+    double *th[kMaxLevels] = {}, *cof[kMaxLevels] = {}, *lam[kMaxLevels] = {}, *f[kMaxLevels] = {};
+    double *nvec = nullptr;
+};
+
 struct recon_handle {
     int N = 0;
     double L = 0.0, h = 0.0;
@@ -41,6 +52,10 @@ struct recon_handle {
     const double *last_phi = nullptr;
     const double *last_b = nullptr;
     bool have_solve = false;
+
+    AdjWork adj;
+    int adj_cycles = 0;
+    double adj_rel = 0.0;
 
     std::string err;
 };
@@ -86,6 +101,10 @@ cudaError_t cic_cells(const double *pos, long long n, int N, double L, int *cell
                       double *frac, cudaStream_t s);
 cudaError_t cic_deposit(const double *pos, long long n, int N, double L, double mass,
                         double *rho, cudaStream_t s);
+// ---- adjoint (recon_adjoint.cu)
+recon_status adjoint(recon_handle *H, const double *gbar, double *lam);
+void adj_free(recon_handle *H);
+
 cudaError_t displace(int N, double L, const double *phi, const double *b, double *psi,
                      double *deltaL, double *scratch, cudaStream_t s);
 

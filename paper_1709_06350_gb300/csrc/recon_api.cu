@@ -241,6 +241,7 @@ void recon_destroy(recon_handle *H)
     if (!H) return;
     if (H->stream) cudaStreamSynchronize(H->stream);
     else cudaDeviceSynchronize();
+    adj_free(H);
     free_all(H);
     delete H;
 }
@@ -299,6 +300,7 @@ recon_status recon_solve(recon_handle *H, const double *b, double *phi, double t
         return set_err(H, RECON_E_INVALID, "tol must be > 0 and max_cycles in [1, 100000]");
     H->err.clear();
     H->have_solve = false;
+    H->adj.null_ready = false;
     if (stats) std::memset(stats, 0, sizeof(*stats));
     recon_status s = check_domain(H, b);
     if (s != RECON_OK) return s;
@@ -326,7 +328,8 @@ recon_status recon_adjoint(recon_handle *H, const double *gbar_phi, double *gbar
     if (!H) return RECON_E_INVALID;
     if (!gbar_phi || !gbar_b) return set_err(H, RECON_E_INVALID, "NULL pointer");
     if (!H->have_solve) return set_err(H, RECON_E_INVALID, "no successful recon_solve on this handle");
-    return set_err(H, RECON_E_UNIMPLEMENTED, "the adjoint is not built yet");
+    H->err.clear();
+    return adjoint(H, gbar_phi, gbar_b);
 }
 
 const char *recon_last_error(const recon_handle *H)
