@@ -173,6 +173,36 @@ recon_status recon_displace(recon_handle *h, const double *phi, const double *b,
  * RECON_E_CUDA, RECON_E_UNIMPLEMENTED (not available in this build). */
 recon_status recon_adjoint(recon_handle *h, const double *gbar_phi, double *gbar_b);
 
+/* ---------------------------------------------------------------------------
+ * Batches: many independent MIXED solves (uneven N allowed) advanced together.
+ * Each realisation has its own handle and stream; every phase of the solve
+ * for all realisations is one CUDA-graph launch (graphs are captured at the
+ * first solve and reused while the field pointers and options stay the
+ * same).  All realisations run the same number of FP32 FAS cycles (until each
+ * reached mixed_switch_rtol or stalled) and correction iterations (until each
+ * met tol; the ones that met it earlier keep refining). */
+typedef struct recon_batch recon_batch;
+
+/* count realisations of sizes N[i] (rules of recon_create) and boxes L[i]. */
+recon_status recon_batch_create(int count, const int *N, const double *L, recon_batch **out);
+void recon_batch_destroy(recon_batch *batch);
+
+/* The graphs are launched on `stream` (NULL: the batch's own stream). */
+recon_status recon_batch_set_stream(recon_batch *batch, void *stream);
+
+/* Handle of realisation i (for recon_set_config / recon_get_config and
+ * recon_adjoint after a batch solve); owned by the batch. */
+recon_handle *recon_batch_handle(recon_batch *batch, int i);
+
+/* Solve realisation i for b[i] into phi[i] (host arrays of device pointers,
+ * each field as in recon_solve).  stats: host array of count (nullable).
+ * Returns RECON_OK when every realisation met tol, else RECON_E_NOCONV /
+ * RECON_E_DIVERGED / RECON_E_DOMAIN / RECON_E_CUDA (message:
+ * recon_batch_last_error). */
+recon_status recon_batch_solve(recon_batch *batch, const double *const *b, double *const *phi,
+                               double tol, int max_cycles, recon_stats *stats);
+const char *recon_batch_last_error(const recon_batch *batch);
+
 /* Message of the last failing call on this handle ("" if none); a handle
  * of NULL gives the last message of recon_create or
  * recon_step_coarse_solve_noalloc on this thread. */

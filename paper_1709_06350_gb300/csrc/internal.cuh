@@ -65,6 +65,12 @@ namespace recon {
 // Kernels launched by this library in this process (diagnostics).
 void note_launch(unsigned long long n = 1);
 
+void unnote_launch(unsigned long long n);
+unsigned long long launch_count();
+
+// Dynamic shared-memory limits of the fused kernels (set before any capture).
+cudaError_t prepare_kernels();
+
 // Message returned by recon_last_error(NULL) on this thread.
 void set_thread_error(const char *msg);
 
@@ -95,6 +101,15 @@ recon_status solve_f64(recon_handle *H, const double *b, double *phi, double tol
 recon_status solve_mixed(recon_handle *H, const double *b, double *phi, double tol,
                          int max_cycles, recon_stats *st);
 recon_status check_domain(recon_handle *H, const double *b);
+
+// capture-safe phases of the mixed solve (recon_mg.cu): enqueue work on
+// H->stream and never synchronise
+cudaError_t mixed_start(recon_handle *H, const double *b, const double *phi);
+cudaError_t mixed_fas_cycle(recon_handle *H);
+cudaError_t mixed_switch(recon_handle *H, const double *b, double *phi);
+cudaError_t mixed_residual(recon_handle *H, const double *b, const double *phi);
+cudaError_t mixed_correct(recon_handle *H, double *phi);
+cudaError_t mixed_finish(recon_handle *H, double *phi, bool converged);
 
 // ---- CIC and displacement (recon_cic.cu)
 cudaError_t cic_cells(const double *pos, long long n, int N, double L, int *cells,

@@ -39,6 +39,7 @@ const char *check_size(int N, int *Nl, int *nlev)
 recon_config default_config()
 {
     recon_config c;
+    std::memset(&c, 0, sizeof(c));   // padding too: batches compare configs bytewise
     c.nu1 = 2;
     c.nu2 = 2;
     c.coarse_max_sweeps = 200;
@@ -224,7 +225,8 @@ recon_status recon_create(int N, double L, recon_dtype dtype, recon_handle **out
         cudaGetLastError();
         return RECON_E_OOM;
     }
-    cudaError_t e = cudaMemset(H->scal, 0, sizeof(double) * S_COUNT);
+    cudaError_t e = prepare_kernels();
+    if (e == cudaSuccess) e = cudaMemset(H->scal, 0, sizeof(double) * S_COUNT);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         g_create_err = std::string("initialising the workspace: ") + cudaGetErrorString(e);
@@ -437,4 +439,6 @@ recon_status recon_step_jacobian_apply(int N, double h, const double *theta, con
 static std::atomic<unsigned long long> g_launches{0};
 void recon::note_launch(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 void recon::set_thread_error(const char *msg) { g_create_err = msg ? msg : ""; }
+void recon::unnote_launch(unsigned long long n) { g_launches.fetch_sub(n, std::memory_order_relaxed); }
+unsigned long long recon::launch_count() { return g_launches.load(); }
 extern "C" unsigned long long recon_kernel_launches(void) { return g_launches.load(); }

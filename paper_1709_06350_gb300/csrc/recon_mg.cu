@@ -256,15 +256,29 @@ k_sweep_fused(const T *__restrict__ src, T *__restrict__ dst, const T *__restric
 }
 
 template <typename T, bool LIN>
+static cudaError_t fused_attr()
+{
+    return cudaFuncSetAttribute(k_sweep_fused<T, LIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sizeof(FusedSmem<T, LIN>));
+}
+
+cudaError_t prepare_kernels()
+{
+    cudaError_t e = fused_attr<float, false>();
+    if (e == cudaSuccess) e = fused_attr<double, false>();
+    if (e == cudaSuccess) e = fused_attr<float, true>();
+    return e;
+}
+
+template <typename T, bool LIN>
 static cudaError_t fused_sweep_launch(int N, const T *src, T *dst, const T *g, const T *th,
                                       const double *cptr, double cval, T ih2, T h2_6, int rule,
                                       cudaStream_t s)
 {
-    static bool attr_set = false;
+    static bool attr_set = false;   // step entry points may run without a handle
     const size_t smem = sizeof(FusedSmem<T, LIN>);
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_sweep_fused<T, LIN>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = fused_attr<T, LIN>();
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
@@ -1254,33 +1268,114 @@ cudaError_t lin_vcycle(recon_handle *H, int l)
 
 }  // namespace
 
+// ---- capture-safe phases of the mixed solve (no host synchronisation)
+cudaError_t mixed_start(recon_handle *H, const double *b, const double *phi)
+{
+    cudaStream_t s = H->stream;
+    const size_t n = ncell(H->N);
+    const Hier<float> Y = hier32(H);
+    note_launch();
+    k_to_float<<<blocks_for(n), kThreads, 0, s>>>(b, H->g32[0], n);
+    if (H->cfg.start == RECON_START_FMG) return fmg_start<float>(H, Y);
+    note_launch();
+    k_to_float<<<blocks_for(n), kThreads, 0, s>>>(phi, H->t32[0], n);
+    CK(cudaMemsetAsync(H->scal + S_C, 0, sizeof(double), s));
+    return compat_gauge<float>(H, Y, 0);
+}
+
+cudaError_t mixed_fas_cycle(recon_handle *H)
+{
+    const Hier<float> Y = hier32(H);
+    CK(vcycle<float>(H, Y, 0, H->scal + S_C));
+    return compat_gauge<float>(H, Y, 0);
+}
+
+cudaError_t mixed_switch(recon_handle *H, const double *b, double *phi)
+{
+    cudaStream_t s = H->stream;
+    const size_t n = ncell(H->N);
+    note_launch();
+    if (H->cfg.mixed_df_residual) {
+        // phi = theta32 + 0 as a double-float pair; b split the same way
+        k_split_df<<<blocks_for(n), kThreads, 0, s>>>(b, H->g32[0], H->blo32, n);
+        return cudaMemsetAsync(H->lo32, 0, sizeof(float) * n, s);
+    }
+    k_to_double<<<blocks_for(n), kThreads, 0, s>>>(H->t32[0], phi, n);
+    return cudaGetLastError();
+}
+
+// r = b + c - det(I + H phi) (double-float or FP64), c -= mean r, rel
+cudaError_t mixed_residual(recon_handle *H, const double *b, const double *phi)
+{
+    cudaStream_t s = H->stream;
+    const size_t n = ncell(H->N);
+    const unsigned nbr = row_grid(H->N, kMaxRedBlocks);
+    const double ih2 = 1.0 / (H->h * H->h);
+    note_launch(2);
+    if (H->cfg.mixed_df_residual) {
+        const df ih2df = df_from_double(ih2);
+        k_residual_df<<<nbr, row_block(), 0, s>>>(H->t32[0], H->lo32, H->g32[0], H->blo32,
+                                                  H->scal + S_C, H->N, ih2df.hi, ih2df.lo,
+                                                  H->f32[0], H->partials);
+    } else {
+        k_residual_norms<double><<<nbr, row_block(), 0, s>>>(phi, b, H->scal + S_C, H->N, ih2,
+                                                             H->partials, H->f32[0], H->t32[0]);
+    }
+    k_finalize_cycle<<<1, kReduceThreads, 0, s>>>(H->partials, nbr, (double)n, H->scal);
+    return cudaGetLastError();
+}
+
+// J(phi) e = r - mean r by FP32 linear multigrid, then phi += e
+cudaError_t mixed_correct(recon_handle *H, double *phi)
+{
+    cudaStream_t s = H->stream;
+    const size_t n = ncell(H->N);
+    note_launch();
+    k_sub_scalar<<<blocks_for(n), kThreads, 0, s>>>(H->f32[0], n, H->scal + S_MEAN_R);
+    for (int l = 1; l < H->nlev; ++l) CK(restrict_plain<float>(H->Nl[l - 1], H->t32[l - 1], H->t32[l], s));
+    CK(cudaMemsetAsync(H->e32[0], 0, sizeof(float) * n, s));
+    for (int v = 0; v < H->cfg.mixed_linear_vcycles; ++v) CK(lin_vcycle(H, 0));
+    note_launch();
+    if (H->cfg.mixed_df_residual)
+        k_update_df<<<blocks_for(n), kThreads, 0, s>>>(H->t32[0], H->lo32, H->e32[0], n);
+    else
+        k_update_theta<<<blocks_for(n), kThreads, 0, s>>>(phi, H->e32[0], n, H->scal);
+    return cudaGetLastError();
+}
+
+// phi out: FP64, mean-free
+cudaError_t mixed_finish(recon_handle *H, double *phi, bool converged)
+{
+    cudaStream_t s = H->stream;
+    const size_t n = ncell(H->N);
+    if (H->cfg.mixed_df_residual) {
+        const unsigned nb2 = red_blocks(n);
+        note_launch(3);
+        k_df_to_double<<<nb2, kThreads, 0, s>>>(H->t32[0], H->lo32, phi, n, H->partials);
+        k_finalize_mean<<<1, kReduceThreads, 0, s>>>(H->partials, nb2, (double)n, H->scal + S_MEAN_T);
+        k_gauge<double><<<blocks_for(n), kThreads, 0, s>>>(phi, n, H->scal);
+    } else if (converged) {
+        note_launch();
+        k_gauge<double><<<blocks_for(n), kThreads, 0, s>>>(phi, n, H->scal);
+    }
+    return cudaGetLastError();
+}
+
+// (i) FP32 FAS until the FP32 residual reaches mixed_switch_rtol, stalls, or
+// mixed_fas_max_cycles ran; (ii) defect correction: the fine-grid residual in
+// double-float (or FP64), mixed_linear_vcycles FP32 linear V-cycles on
+// J(phi) e = r - mean r, phi += e, until ||r - mean r|| / ||b - 1|| < tol.
 recon_status solve_mixed(recon_handle *H, const double *b, double *phi, double tol,
                          int max_cycles, recon_stats *st)
 {
     const double t0 = now_s();
-    cudaStream_t s = H->stream;
     const recon_config &cf = H->cfg;
-    const size_t n = ncell(H->N);
-    const Hier<float> Y = hier32(H);
-    cudaError_t e = cudaSuccess;
-
-    // ---- (i) FP32 FAS
-    note_launch();
-    k_to_float<<<blocks_for(n), kThreads, 0, s>>>(b, H->g32[0], n);
-    if (cf.start == RECON_START_FMG) {
-        e = fmg_start<float>(H, Y);
-    } else {
-        note_launch();
-        k_to_float<<<blocks_for(n), kThreads, 0, s>>>(phi, H->t32[0], n);
-        e = cudaMemsetAsync(H->scal + S_C, 0, sizeof(double), s);
-        if (e == cudaSuccess) e = compat_gauge<float>(H, Y, 0);
-    }
+    cudaError_t e = mixed_start(H, b, phi);
     if (e != cudaSuccess) return fail_cuda(H, e, "mixed start");
     int fas = 0;
     double prev = INFINITY;
     for (fas = 1; fas <= cf.mixed_fas_max_cycles; ++fas) {
-        e = vcycle<float>(H, Y, 0, H->scal + S_C);
-        if (e == cudaSuccess) e = compat_gauge<float>(H, Y, 0);
+        e = mixed_fas_cycle(H);
         if (e == cudaSuccess) e = read_scalars(H);
         if (e != cudaSuccess) return fail_cuda(H, e, "FP32 V-cycle");
         const double rel = H->hscal[S_REL];
@@ -1293,36 +1388,13 @@ recon_status solve_mixed(recon_handle *H, const double *b, double *phi, double t
         prev = rel;
     }
     if (fas > cf.mixed_fas_max_cycles) fas = cf.mixed_fas_max_cycles;
-    const bool dfres = cf.mixed_df_residual != 0;
-    if (dfres) {
-        // phi = theta32 + 0 as a double-float pair; b split the same way
-        note_launch();
-        k_split_df<<<blocks_for(n), kThreads, 0, s>>>(b, H->g32[0], H->blo32, n);
-        e = cudaMemsetAsync(H->lo32, 0, sizeof(float) * n, s);
-        if (e != cudaSuccess) return fail_cuda(H, e, "mixed phase 2");
-    } else {
-        note_launch();
-        k_to_double<<<blocks_for(n), kThreads, 0, s>>>(H->t32[0], phi, n);
-    }
+    if ((e = mixed_switch(H, b, phi)) != cudaSuccess) return fail_cuda(H, e, "mixed switch");
 
-    // ---- (ii) defect correction with FP32 linear multigrid
-    const unsigned nbr = row_grid(H->N, kMaxRedBlocks);
-    const double ih2 = 1.0 / (H->h * H->h);
-    const df ih2df = df_from_double(ih2);
     recon_status status = RECON_E_NOCONV;
     double best = INFINITY;
     int o = 0;
     for (o = 1; o <= max_cycles; ++o) {
-        note_launch(2);
-        if (dfres)
-            k_residual_df<<<nbr, row_block(), 0, s>>>(H->t32[0], H->lo32, H->g32[0], H->blo32,
-                                                      H->scal + S_C, H->N, ih2df.hi, ih2df.lo,
-                                                      H->f32[0], H->partials);
-        else
-            k_residual_norms<double><<<nbr, row_block(), 0, s>>>(phi, b, H->scal + S_C, H->N, ih2,
-                                                                 H->partials, H->f32[0], H->t32[0]);
-        k_finalize_cycle<<<1, kReduceThreads, 0, s>>>(H->partials, nbr, (double)n, H->scal);
-        e = cudaGetLastError();
+        e = mixed_residual(H, b, phi);
         if (e == cudaSuccess) e = read_scalars(H);
         if (e != cudaSuccess) return fail_cuda(H, e, "fine-grid residual");
         const double rel = H->hscal[S_REL];
@@ -1337,35 +1409,12 @@ recon_status solve_mixed(recon_handle *H, const double *b, double *phi, double t
             status = RECON_OK;
             break;
         }
-        note_launch();
-        k_sub_scalar<<<blocks_for(n), kThreads, 0, s>>>(H->f32[0], n, H->scal + S_MEAN_R);
-        for (int l = 1; l < H->nlev; ++l) {
-            e = restrict_plain<float>(H->Nl[l - 1], H->t32[l - 1], H->t32[l], s);
-            if (e != cudaSuccess) return fail_cuda(H, e, "theta hierarchy");
-        }
-        e = cudaMemsetAsync(H->e32[0], 0, sizeof(float) * n, s);
-        for (int v = 0; v < cf.mixed_linear_vcycles && e == cudaSuccess; ++v) e = lin_vcycle(H, 0);
-        if (e != cudaSuccess) return fail_cuda(H, e, "linear V-cycle");
-        note_launch();
-        if (dfres)
-            k_update_df<<<blocks_for(n), kThreads, 0, s>>>(H->t32[0], H->lo32, H->e32[0], n);
-        else
-            k_update_theta<<<blocks_for(n), kThreads, 0, s>>>(phi, H->e32[0], n, H->scal);
-    }
-    // phi out: FP64, mean-free
-    if (dfres) {
-        const unsigned nb2 = red_blocks(n);
-        note_launch(3);
-        k_df_to_double<<<nb2, kThreads, 0, s>>>(H->t32[0], H->lo32, phi, n, H->partials);
-        k_finalize_mean<<<1, kReduceThreads, 0, s>>>(H->partials, nb2, (double)n, H->scal + S_MEAN_T);
-        k_gauge<double><<<blocks_for(n), kThreads, 0, s>>>(phi, n, H->scal);
-    } else if (status == RECON_OK) {
-        note_launch();
-        k_gauge<double><<<blocks_for(n), kThreads, 0, s>>>(phi, n, H->scal);
+        if ((e = mixed_correct(H, phi)) != cudaSuccess) return fail_cuda(H, e, "linear correction");
     }
     if (o > max_cycles) o = max_cycles;
     if (status == RECON_E_NOCONV) H->err = "max_cycles reached before the tolerance";
-    e = cudaStreamSynchronize(s);
+    e = mixed_finish(H, phi, status == RECON_OK);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(H->stream);
     if (e != cudaSuccess) return fail_cuda(H, e, "mixed solve");
     if (st) {
         st->cycles = fas;

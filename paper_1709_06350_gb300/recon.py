@@ -71,6 +71,12 @@ _SIGS = {
     "recon_last_error": (ctypes.c_char_p, [_P]),
     "recon_status_string": (ctypes.c_char_p, [_I]),
     "recon_kernel_launches": (ctypes.c_ulonglong, []),
+    "recon_batch_create": (_I, [_I, _P, _P, ctypes.POINTER(_P)]),
+    "recon_batch_destroy": (None, [_P]),
+    "recon_batch_set_stream": (_I, [_P, _P]),
+    "recon_batch_handle": (_P, [_P, _I]),
+    "recon_batch_solve": (_I, [_P, _P, _P, _D, _I, _P]),
+    "recon_batch_last_error": (ctypes.c_char_p, [_P]),
     "recon_step_sweep": (_I, [_I, _D, _I, _I, _P, _P, _D, _I, _P, _P]),
     "recon_step_residual": (_I, [_I, _D, _P, _P, _D, _P, _P]),
     "recon_step_det": (_I, [_I, _D, _P, _P, _P]),
@@ -360,6 +366,61 @@ class Solver:
         if self.h is not None:
             recon_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many independent MIXED solves (uneven N) advanced together through
+    CUDA-graph launches (recon_batch_* of include/recon.h)."""
+
+    def __init__(self, sizes, boxes, stream=None):
+        n = len(sizes)
+        Ns = (ctypes.c_int * n)(*[int(v) for v in sizes])
+        Ls = (ctypes.c_double * n)(*[float(v) for v in boxes])
+        self.b = ctypes.c_void_p()
+        st = load().recon_batch_create(n, Ns, Ls, ctypes.byref(self.b))
+        if st != 0:
+            raise ReconError(st, (load().recon_last_error(None) or b"").decode())
+        self.sizes, self.boxes = list(sizes), list(boxes)
+        if stream is not None:
+            load().recon_batch_set_stream(self.b, _stream(stream))
+
+    def handle(self, i):
+        return ctypes.c_void_p(load().recon_batch_handle(self.b, int(i)))
+
+    def configure(self, **kw):
+        for i in range(len(self.sizes)):
+            h = self.handle(i)
+            c = recon_get_config(h)
+            for k, v in kw.items():
+                setattr(c, k, v)
+            recon_set_config(h, c)
+        return self
+
+    def solve(self, bs, phis=None, tol=1e-8, max_cycles=50, raise_on_noconv=True):
+        import torch
+        n = len(self.sizes)
+        if phis is None:
+            phis = [torch.zeros_like(x) for x in bs]
+        for x, N in zip(list(bs) + list(phis), self.sizes + self.sizes):
+            _dev_ptr(x, torch.float64, N ** 3)
+        bp = (ctypes.c_void_p * n)(*[x.data_ptr() for x in bs])
+        pp = (ctypes.c_void_p * n)(*[x.data_ptr() for x in phis])
+        stats = (recon_stats * n)()
+        st = load().recon_batch_solve(self.b, bp, pp, float(tol), int(max_cycles), stats)
+        if st != 0 and not (st == 3 and not raise_on_noconv):
+            raise ReconError(st, (load().recon_batch_last_error(self.b) or b"").decode())
+        return phis, [s.as_dict() for s in stats]
+
+    def close(self):
+        if self.b is not None:
+            load().recon_batch_destroy(self.b)
+            self.b = None
 
     def __del__(self):
         try:
