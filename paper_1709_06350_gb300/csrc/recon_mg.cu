@@ -262,11 +262,14 @@ static cudaError_t fused_attr()
                                 (int)sizeof(FusedSmem<T, LIN>));
 }
 
+static bool g_kernels_ready = false;
+
 cudaError_t prepare_kernels()
 {
     cudaError_t e = fused_attr<float, false>();
     if (e == cudaSuccess) e = fused_attr<double, false>();
     if (e == cudaSuccess) e = fused_attr<float, true>();
+    if (e == cudaSuccess) g_kernels_ready = true;
     return e;
 }
 
@@ -275,12 +278,12 @@ static cudaError_t fused_sweep_launch(int N, const T *src, T *dst, const T *g, c
                                       const double *cptr, double cval, T ih2, T h2_6, int rule,
                                       cudaStream_t s)
 {
-    static bool attr_set = false;   // step entry points may run without a handle
+    // set once per process (recon_create does it before any graph capture;
+    // step entry points may run without a handle)
     const size_t smem = sizeof(FusedSmem<T, LIN>);
-    if (!attr_set) {
-        cudaError_t e = fused_attr<T, LIN>();
+    if (!g_kernels_ready) {
+        const cudaError_t e = prepare_kernels();
         if (e != cudaSuccess) return e;
-        attr_set = true;
     }
     const int CI = N >= 512 ? 64 : (N >= 256 ? 32 : 16);
     const dim3 grid((N + kTK - 1) / kTK, (N + kTJ - 1) / kTJ, (N + CI - 1) / CI);
