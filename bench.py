@@ -43,6 +43,11 @@ def parse():
     p.add_argument("--no-fp64-compare", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-batch", action="store_true")
+    p.add_argument("--no-adjoint", action="store_true")
+    p.add_argument("--batch-count", type=int, default=64)
+    p.add_argument("--adjoint-n", type=int, default=256)
+    p.add_argument("--fd-directions", type=int, default=8)
     p.add_argument("--cpu-sample-n", type=int, default=128)
     p.add_argument("--kernel-only", type=int, default=0, metavar="N",
                    help="only time the roofline kernel at N^3 (small case for profilers)")
@@ -198,8 +203,8 @@ def main():
 
     W = synth.WORKLOADS[args.workload]
     N, L, R, tol = W.N, W.L, W.R, W.tol
-    _, dh = synth.linear_field(N, L, W.sigma_lin, W.seed + 7919 * rank, backend="torch",
-                               device=dev)
+    delta_lin, dh = synth.linear_field(N, L, W.sigma_lin, W.seed + 7919 * rank, backend="torch",
+                                       device=dev)
     pos = synth.zeldovich_positions(dh, N, L).contiguous()
     del dh
     torch.cuda.empty_cache()
@@ -299,6 +304,24 @@ def main():
     kern = kernel_roofline(recon, torch, N, L, dev, stream)
     roof = dict(kern[0])
 
+    # ---- reconstruction quality: r(k) of delta_r against the seeded linear field
+    from paper_1709_06350_gb300 import analysis
+    kk, rr, _ = analysis.correlation(last["dl"].view(N, N, N), delta_lin, L)
+    rk = analysis.r_at(kk, rr, (0.05, 0.1, 0.2, 0.3, 0.5))
+    del delta_lin
+
+    batch = None
+    if not args.no_batch and rank == 0:
+        solver.close()
+        torch.cuda.empty_cache()
+        batch = bench_batch(recon, synth, torch, dev, args.batch_count)
+        solver = recon.Solver(N, L, dtype)
+
+    adj = None
+    if not args.no_adjoint and rank == 0:
+        torch.cuda.empty_cache()
+        adj = bench_adjoint(recon, synth, torch, dev, args.adjoint_n, args.fd_directions)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         n = args.cpu_sample_n
@@ -329,6 +352,11 @@ def main():
                       "rel_residual": st["rel_residual"], "compat_c": st["compat_c"],
                       "history": st["history"]},
             "fp64_path": fp64,
+            "r_k": {"k_h_per_Mpc": list(rk.keys()), "r": list(rk.values()),
+                    "fields": "delta_r (displacement output, Lagrangian grid) vs the seeded "
+                              "linear field"},
+            "batched": batch,
+            "adjoint": adj,
             "gs_cell_updates_per_s": roof.pop("cell_updates_per_s", None),
             "roofline": roof,
             "other_kernels": kern[1:],
@@ -342,6 +370,105 @@ def main():
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def bench_batch(recon, synth, torch, dev, count):
+    """Config 4: `count` realisations, N cycling through 64..256 (h = 2 Mpc/h),
+    solved to 1e-8 by one recon_batch (CUDA graphs), against the same solves
+    run one after another on single handles."""
+    Ws = synth.batched_workloads(count)
+    sizes = [w.N for w in Ws]
+    boxes = [w.L for w in Ws]
+    deposit = {}
+    bs = []
+    for w in Ws:
+        if w.N not in deposit:
+            deposit[w.N] = recon.Solver(w.N, w.L, recon.RECON_F64)
+        _, dh = synth.linear_field(w.N, w.L, w.sigma_lin, w.seed, backend="torch", device=dev)
+        pos = synth.zeldovich_positions(dh, w.N, w.L).contiguous()
+        rho = deposit[w.N].deposit_cic(pos)
+        bs.append(synth.smooth_and_floor(rho, w.L, w.R, fft_dtype=torch.float32))
+        del dh, pos, rho
+    for s in deposit.values():
+        s.close()
+    B = recon.Batch(sizes, boxes)
+    phis = [torch.zeros_like(b) for b in bs]
+    B.solve(bs, phis=phis, tol=1e-8, max_cycles=40)          # captures the graphs
+    torch.cuda.synchronize()
+    reps = 2
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        _, stats = B.solve(bs, phis=phis, tol=1e-8, max_cycles=40)
+    torch.cuda.synchronize()
+    t_batch = (time.perf_counter() - t0) / reps
+    B.close()
+    single = {}
+    for n, L in sorted(set(zip(sizes, boxes))):
+        single[n] = recon.Solver(n, L, recon.RECON_MIXED)
+    for b, n in zip(bs[:5], sizes[:5]):
+        single[n].solve(b, tol=1e-8, max_cycles=40)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for b, n in zip(bs, sizes):
+        single[n].solve(b, tol=1e-8, max_cycles=40)
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    for s in single.values():
+        s.close()
+    cells = sum(n ** 3 for n in sizes)
+    worst = max(s["rel_residual"] for s in stats)
+    del bs, phis
+    return {"workload": f"{count} realisations, N cycling 64/96/128/192/256, L = 2N Mpc/h, "
+                        "sigma_lin = 0.8, R = 4 Mpc/h, mixed solve to 1e-8",
+            "seconds_per_batch": t_batch, "realisations_per_s": count / t_batch,
+            "cells_per_s": cells / t_batch, "sequential_seconds": t_seq,
+            "speedup_vs_sequential": t_seq / t_batch, "worst_rel_residual": worst,
+            "cycles": stats[0]["cycles"],
+            "outer_iterations_max": max(s["outer_iterations"] for s in stats)}
+
+
+def bench_adjoint(recon, synth, torch, dev, n, directions):
+    """Config 5: FP64 solve of a 256^3 field (L = 512 Mpc/h, sigma_lin = 0.8,
+    R = 4 Mpc/h), then the adjoint of loss = <w, phi(b)>; checked against
+    central finite differences along random directions."""
+    L = 2.0 * n
+    w = synth.WORKLOADS.get("adjoint-256")
+    _, dh = synth.linear_field(n, L, 0.8, w.seed if w else 5000, backend="torch", device=dev)
+    pos = synth.zeldovich_positions(dh, n, L).contiguous()
+    s = recon.Solver(n, L, recon.RECON_F64)
+    b = synth.smooth_and_floor(s.deposit_cic(pos), L, 4.0)
+    del dh, pos
+    gen = torch.Generator(device=dev).manual_seed(11)
+    wv = torch.randn((n, n, n), dtype=torch.float64, device=dev, generator=gen)
+    t0 = time.perf_counter()
+    phi, st = s.solve(b, tol=1e-12, max_cycles=60)
+    torch.cuda.synchronize()
+    t_solve = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    g = s.adjoint(wv)
+    torch.cuda.synchronize()
+    t_adj = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    g = s.adjoint(wv)                      # cofactors and null vector reused
+    torch.cuda.synchronize()
+    t_adj2 = time.perf_counter() - t0
+    eps = 1e-4
+    errs = []
+    aux = recon.Solver(n, L, recon.RECON_F64)
+    for _ in range(directions):
+        d = torch.randn((n, n, n), dtype=torch.float64, device=dev, generator=gen)
+        pp, _ = aux.solve(b + eps * d, tol=1e-12, max_cycles=60)
+        lp = float((wv * pp).sum())
+        pm, _ = aux.solve(b - eps * d, tol=1e-12, max_cycles=60)
+        lm = float((wv * pm).sum())
+        fd = (lp - lm) / (2 * eps)
+        errs.append(abs(float((g * d).sum()) - fd) / abs(fd))
+    aux.close()
+    s.close()
+    return {"workload": f"{n}^3, L = {L:g} Mpc/h, sigma_lin = 0.8, R = 4 Mpc/h, FP64",
+            "solve_seconds": t_solve, "adjoint_seconds_first": t_adj,
+            "adjoint_seconds_repeat": t_adj2, "fd_directions": directions,
+            "fd_max_rel_error": max(errs) if errs else None, "fd_step": eps}
 
 
 def _time_launches(torch, stream, fn, reps):
