@@ -472,14 +472,20 @@ def bench_adjoint(recon, synth, torch, dev, n, directions):
 
 
 def _time_launches(torch, stream, fn, reps):
+    """Mean time of one launch: (time of fn(reps) - time of fn(1)) / (reps - 1),
+    so per-call set-up (the linear smoother's cofactor pass) drops out."""
+    def timed(k):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn(k)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1e3
     fn(2)
-    torch.cuda.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    fn(reps)
-    b.record(stream)
-    torch.cuda.synchronize()
-    return a.elapsed_time(b) / 1e3 / reps
+    t1 = min(timed(1) for _ in range(3))
+    tr = timed(reps)
+    return (tr - t1) / (reps - 1)
 
 
 def kernel_roofline(recon, torch, N, L, dev, stream):
@@ -487,7 +493,8 @@ def kernel_roofline(recon, torch, N, L, dev, stream):
     on its stream (one launch = one fused red+black sweep for N >= 128).
 
     Algorithmic bytes per sweep: FAS smoother 12 B/cell (read theta and b,
-    write theta); linear smoother 16 B/cell (read theta, e, f; write e)."""
+    write theta); linear smoother 36 B/cell (read e, f and the six
+    precomputed cofactors of the cell; write e)."""
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -505,12 +512,13 @@ def kernel_roofline(recon, torch, N, L, dev, stream):
     t_fas = _time_launches(torch, stream, lambda k: recon.recon_step_sweep(
         th, g, 0.0, h, sweeps=k, work=work, stream=stream), reps)
     e = torch.zeros_like(th)
+    work7 = torch.empty(7 * N ** 3, dtype=torch.float32, device=dev)
     t_lin = _time_launches(torch, stream, lambda k: recon.recon_step_linear_sweep(
-        e, g, th, h, sweeps=k, work=work, stream=stream), reps)
-    del th, g, work, e
+        e, g, th, h, sweeps=k, work=work7, stream=stream), reps)
+    del th, g, work, e, work7
     out = []
     for name, t, bpc in (("k_sweep_fused<float, FAS> (FP32 red-black Newton smoother, one sweep)", t_fas, 12.0),
-                         ("k_sweep_fused<float, LIN> (FP32 red-black smoother of J e = f, one sweep)", t_lin, 16.0)):
+                         ("k_sweep_fused<float, LIN> (FP32 red-black smoother of J e = f, one sweep)", t_lin, 36.0)):
         alg = bpc * N ** 3
         ach = alg / t / 1e9
         out.append({"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",

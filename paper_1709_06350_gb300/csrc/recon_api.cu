@@ -93,6 +93,7 @@ void plan(recon_handle *H, Planner &P)
             P.take(&H->g32[l], n);
             P.take(&H->e32[l], n);
             P.take(&H->f32[l], n);
+            P.take(&H->cof32[l], 6 * n);
             if (l > 0) {
                 P.take(&H->told32[l], n);
                 P.take(&H->aux32[l], n);
@@ -130,6 +131,7 @@ void free_all(recon_handle *H)
         f(H->aux32[l]);
         f(H->e32[l]);
         f(H->f32[l]);
+        f(H->cof32[l]);
     }
     f(H->scal);
     f(H->partials);

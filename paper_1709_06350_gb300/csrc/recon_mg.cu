@@ -68,8 +68,8 @@ k_rb_pass(const T *__restrict__ src, T *__restrict__ dst, const T *__restrict__ 
 // only OLD values), then the black cells of plane s on the tile (faces from
 // RED, edges and centre from OLD) and write plane s.  DRAM traffic: src and
 // g read once, dst written once.  The linear variant (LIN) relaxes J e = f:
-// the staged unknown is e, a second OLD ring holds theta (cofactors of
-// I + H theta at every cell), and g is f.
+// the staged unknown is e, g is f, and the cofactors of I + H theta at each
+// updated cell come from six precomputed arrays (cof, [6][N^3]).
 // Requires N >= kFusedMinN (so one wrap suffices for every halo index).
 // ----------------------------------------------------------------------
 constexpr int kTJ = 16, kTK = 64;
@@ -85,7 +85,6 @@ template <typename T, bool LIN>
 struct FusedSmem {
     T old_[kOSlots][kOJ][kOK];
     T red_[kRSlots][kRJ][kRK];
-    T th_[LIN ? kOSlots : 1][LIN ? kOJ : 1][LIN ? kOK : 1];
 };
 
 __device__ __forceinline__ int wrap1(int x, int N) { return x < 0 ? x + N : (x >= N ? x - N : x); }
@@ -135,11 +134,17 @@ __device__ __forceinline__ Nb19<T> nb_from(const T (*pm)[K], const T (*pc)[K], c
 
 // The cell update of one colour: nonlinear (eq. update) or linear Gauss-Seidel on J.
 template <typename T, bool LIN>
-__device__ __forceinline__ T cell_update(const Nb19<T> &nb, const Nb19<T> *thn, T rhs, T ih2,
-                                         T h2_6, int rule)
+__device__ __forceinline__ T cell_update(const Nb19<T> &nb, const T *cof, size_t n, unsigned o,
+                                         T rhs, T ih2, T h2_6, int rule)
 {
     if constexpr (LIN) {
-        const Cof<T> a = cofactors(*thn, ih2);
+        Cof<T> a;
+        a.xx = cof[o];
+        a.yy = cof[n + o];
+        a.zz = cof[2 * n + o];
+        a.xy = cof[3 * n + o];
+        a.yz = cof[4 * n + o];
+        a.xz = cof[5 * n + o];
         const T Je = jac_apply(a, nb, ih2);
         const T diag = T(-2) * (a.xx + a.yy + a.zz) * ih2;
         return nb.c + (rhs - Je) / diag;
@@ -153,7 +158,7 @@ __device__ __forceinline__ T cell_update(const Nb19<T> &nb, const Nb19<T> *thn, 
 template <typename T, bool LIN>
 __global__ void __launch_bounds__(kFT)
 k_sweep_fused(const T *__restrict__ src, T *__restrict__ dst, const T *__restrict__ g,
-              const T *__restrict__ th, const double *__restrict__ cptr, double cval, int N,
+              const T *__restrict__ cof, const double *__restrict__ cptr, double cval, int N,
               int CI, T ih2, T h2_6, int rule)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -163,6 +168,7 @@ k_sweep_fused(const T *__restrict__ src, T *__restrict__ dst, const T *__restric
     const int i1 = min(i0 + CI, N);
     const int tid = threadIdx.x;
     const unsigned NN = (unsigned)N * (unsigned)N;
+    const size_t ncell = (size_t)NN * (size_t)N;
 
     // in-plane offsets of this thread's OLD elements (the same for every plane)
     unsigned goff[kLoadsPerThread];
@@ -181,12 +187,6 @@ k_sweep_fused(const T *__restrict__ src, T *__restrict__ dst, const T *__restric
 #pragma unroll
         for (int t = 0; t < kLoadsPerThread; ++t)
             if (soff[t] >= 0) cp_async_elem(so + soff[t], src + pb + goff[t]);
-        if constexpr (LIN) {
-            T *st = &S.th_[slot][0][0];
-#pragma unroll
-            for (int t = 0; t < kLoadsPerThread; ++t)
-                if (soff[t] >= 0) cp_async_elem(st + soff[t], th + pb + goff[t]);
-        }
         cp_async_commit();
     };
     // red cells of plane p on the tile + 1 halo (RED local (r, q) = OLD (r+1, q+1))
@@ -200,10 +200,8 @@ k_sweep_fused(const T *__restrict__ src, T *__restrict__ dst, const T *__restric
             const int q = 2 * m + ((pw + gj + kfirst) & 1);   // the red cell of the pair
             const int gk = k0 - 1 + q;
             const Nb19<T> nb = nb_from<T, kOK>(S.old_[om], S.old_[oc], S.old_[op], r + 1, q + 1);
-            Nb19<T> thn;
-            if constexpr (LIN) thn = nb_from<T, kOK>(S.th_[om], S.th_[oc], S.th_[op], r + 1, q + 1);
-            const T rhs = g[pb + (unsigned)wrap1(gj, N) * (unsigned)N + (unsigned)wrap1(gk, N)] + c;
-            S.red_[rslot][r][q] = cell_update<T, LIN>(nb, &thn, rhs, ih2, h2_6, rule);
+            const unsigned go = pb + (unsigned)wrap1(gj, N) * (unsigned)N + (unsigned)wrap1(gk, N);
+            S.red_[rslot][r][q] = cell_update<T, LIN>(nb, cof, ncell, go, g[go] + c, ih2, h2_6, rule);
         }
     };
 
@@ -243,10 +241,8 @@ k_sweep_fused(const T *__restrict__ src, T *__restrict__ dst, const T *__restric
             nb.ym = S.red_[rc][r][qb + 1];
             nb.zp = S.red_[rc][r + 1][qb + 2];
             nb.zm = S.red_[rc][r + 1][qb];
-            Nb19<T> thn;
-            if constexpr (LIN) thn = nb_from<T, kOK>(S.th_[om], S.th_[oc], S.th_[op], r + 2, qb + 2);
             const unsigned gb = pb + (unsigned)gj * (unsigned)N + (unsigned)k0;
-            const T vb = cell_update<T, LIN>(nb, &thn, g[gb + qb] + c, ih2, h2_6, rule);
+            const T vb = cell_update<T, LIN>(nb, cof, ncell, gb + qb, g[gb + qb] + c, ih2, h2_6, rule);
             const T vr = S.red_[rc][r + 1][qr + 1];
             dst[gb + qb] = vb;
             dst[gb + qr] = vr;
@@ -274,7 +270,7 @@ cudaError_t prepare_kernels()
 }
 
 template <typename T, bool LIN>
-static cudaError_t fused_sweep_launch(int N, const T *src, T *dst, const T *g, const T *th,
+static cudaError_t fused_sweep_launch(int N, const T *src, T *dst, const T *g, const T *cof,
                                       const double *cptr, double cval, T ih2, T h2_6, int rule,
                                       cudaStream_t s)
 {
@@ -288,7 +284,7 @@ static cudaError_t fused_sweep_launch(int N, const T *src, T *dst, const T *g, c
     const int CI = N >= 512 ? 64 : (N >= 256 ? 32 : 16);
     const dim3 grid((N + kTK - 1) / kTK, (N + kTJ - 1) / kTJ, (N + CI - 1) / CI);
     note_launch();
-    k_sweep_fused<T, LIN><<<grid, kFT, smem, s>>>(src, dst, g, th, cptr, cval, N, CI, ih2, h2_6, rule);
+    k_sweep_fused<T, LIN><<<grid, kFT, smem, s>>>(src, dst, g, cof, cptr, cval, N, CI, ih2, h2_6, rule);
     return cudaGetLastError();
 }
 
@@ -874,13 +870,45 @@ k_df_to_double(const float *__restrict__ hi, const float *__restrict__ lo, doubl
     if (ltid() == 0) partials[4 * blockIdx.x + 0] = v;
 }
 
-// ---- linear multigrid for J e = f in FP32 (J from the FP32 theta of the level)
+// ---- linear multigrid for J e = f in FP32.  J = sum adj(I + H theta)_ab D_ab
+// with the FP32 theta of the level; its six cofactor arrays ([6][N^3]) are
+// computed once per correction (k_cof6f) and read by every sweep.
+__global__ void __launch_bounds__(kRowThreads)
+k_cof6f(const float *__restrict__ th, int N, float ih2, float *__restrict__ cof)
+{
+    const size_t n = (size_t)N * N * N;
+    FOR_ROWS(N, i, j)
+    for (int k = threadIdx.x; k < N; k += kRowX) {
+        const Cof<float> a = cofactors(load19<float>(th, N, i, j, k), ih2);
+        const unsigned id = offs(N, i, j, k);
+        cof[id] = a.xx;
+        cof[n + id] = a.yy;
+        cof[2 * n + id] = a.zz;
+        cof[3 * n + id] = a.xy;
+        cof[4 * n + id] = a.yz;
+        cof[5 * n + id] = a.xz;
+    }
+}
+
+__device__ __forceinline__ Cof<float> cof_at(const float *cof, size_t n, unsigned o)
+{
+    Cof<float> a;
+    a.xx = cof[o];
+    a.yy = cof[n + o];
+    a.zz = cof[2 * n + o];
+    a.xy = cof[3 * n + o];
+    a.yz = cof[4 * n + o];
+    a.xz = cof[5 * n + o];
+    return a;
+}
+
 // One colour pass of Gauss-Seidel on J: e_c += (f - J e)_c / J_cc,
 // J_cc = -2 (adj_xx + adj_yy + adj_zz) / h^2.
 __global__ void __launch_bounds__(kRowThreads)
 k_lin_pass(const float *__restrict__ src, float *__restrict__ dst, const float *__restrict__ f,
-           const float *__restrict__ th, int N, float ih2, int colour)
+           const float *__restrict__ cof, int N, float ih2, int colour)
 {
+    const size_t n = (size_t)N * N * N;
     const int half = N >> 1;
     FOR_ROWS(N, i, j)
     {
@@ -888,7 +916,7 @@ k_lin_pass(const float *__restrict__ src, float *__restrict__ dst, const float *
         const unsigned base = offs(N, i, j, 0);
         for (int m = threadIdx.x; m < half; m += kRowX) {
             const int ka = 2 * m + par, kb = 2 * m + 1 - par;
-            const Cof<float> a = cofactors(load19<float>(th, N, i, j, ka), ih2);
+            const Cof<float> a = cof_at(cof, n, base + ka);
             const Nb19<float> ev = load19<float>(src, N, i, j, ka);
             const float Je = jac_apply(a, ev, ih2);
             const float diag = -2.0f * (a.xx + a.yy + a.zz) * ih2;
@@ -898,14 +926,14 @@ k_lin_pass(const float *__restrict__ src, float *__restrict__ dst, const float *
     }
 }
 
-static cudaError_t lin_sweep(int N, double h, float *e, const float *f, const float *th,
+static cudaError_t lin_sweep(int N, double h, float *e, const float *f, const float *cof,
                              int sweeps, float *work, cudaStream_t s)
 {
     const float ih2 = (float)(1.0 / (h * h));
     if (N >= kFusedMinN) {
         float *a = e, *b = work;
         for (int it = 0; it < sweeps; ++it) {
-            const cudaError_t err = fused_sweep_launch<float, true>(N, a, b, f, th, nullptr, 0.0, ih2,
+            const cudaError_t err = fused_sweep_launch<float, true>(N, a, b, f, cof, nullptr, 0.0, ih2,
                                                                    0.0f, 0, s);
             if (err != cudaSuccess) return err;
             float *tmp = a;
@@ -917,8 +945,8 @@ static cudaError_t lin_sweep(int N, double h, float *e, const float *f, const fl
     }
     for (int it = 0; it < sweeps; ++it) {
         note_launch(2);
-        k_lin_pass<<<row_grid(N), row_block(), 0, s>>>(e, work, f, th, N, ih2, 0);
-        k_lin_pass<<<row_grid(N), row_block(), 0, s>>>(work, e, f, th, N, ih2, 1);
+        k_lin_pass<<<row_grid(N), row_block(), 0, s>>>(e, work, f, cof, N, ih2, 0);
+        k_lin_pass<<<row_grid(N), row_block(), 0, s>>>(work, e, f, cof, N, ih2, 1);
     }
     return cudaGetLastError();
 }
@@ -926,16 +954,22 @@ static cudaError_t lin_sweep(int N, double h, float *e, const float *f, const fl
 cudaError_t linear_sweep(int N, double h, float *e, const float *f, const float *th, int sweeps,
                          float *work, cudaStream_t s)
 {
-    return lin_sweep(N, h, e, f, th, sweeps, work, s);
+    // work: N^3 ping-pong followed by the 6 N^3 cofactor arrays
+    const size_t n = (size_t)N * N * N;
+    float *cof = work + n;
+    note_launch();
+    k_cof6f<<<row_grid(N), row_block(), 0, s>>>(th, N, (float)(1.0 / (h * h)), cof);
+    return lin_sweep(N, h, e, f, cof, sweeps, work, s);
 }
 
 // fH = R (f - J e), block partial sums for the mean projection.
 __global__ void __launch_bounds__(kRowThreads)
 k_lin_restrict_residual(const float *__restrict__ e, const float *__restrict__ f,
-                        const float *__restrict__ th, int Nf, float ih2, float *__restrict__ fH,
+                        const float *__restrict__ cof, int Nf, float ih2, float *__restrict__ fH,
                         double *__restrict__ partials)
 {
     __shared__ double sh[32];
+    const size_t nf = (size_t)Nf * Nf * Nf;
     const int Nc = Nf >> 1;
     double sacc = 0.0;
     FOR_ROWS(Nc, I, J)
@@ -945,8 +979,8 @@ k_lin_restrict_residual(const float *__restrict__ e, const float *__restrict__ f
             for (int b = 0; b < 2; ++b)
                 for (int cc = 0; cc < 2; ++cc) {
                     const int i = 2 * I + a, j = 2 * J + b, k = 2 * K + cc;
-                    const Cof<float> co = cofactors(load19<float>(th, Nf, i, j, k), ih2);
-                    acc += f[offs(Nf, i, j, k)] - jac_apply(co, load19<float>(e, Nf, i, j, k), ih2);
+                    const unsigned o = offs(Nf, i, j, k);
+                    acc += f[o] - jac_apply(cof_at(cof, nf, o), load19<float>(e, Nf, i, j, k), ih2);
                 }
         const float v = acc * 0.125f;
         fH[offs(Nc, I, J, K)] = v;
@@ -957,9 +991,10 @@ k_lin_restrict_residual(const float *__restrict__ e, const float *__restrict__ f
 }
 
 __global__ void __launch_bounds__(kCoarseThreads)
-k_lin_coarse(float *e, float *work, const float *f, const float *th, int N, float ih2,
+k_lin_coarse(float *e, float *work, const float *f, const float *cof, int N, float ih2,
              int max_sweeps, double rtol)
 {
+    const size_t ncof = (size_t)N * N * N;
     __shared__ double sh[32];
     __shared__ double sval;
     const int n = N * N * N, half = N >> 1, npairs = N * N * half;
@@ -967,8 +1002,7 @@ k_lin_coarse(float *e, float *work, const float *f, const float *th, int N, floa
         double sr = 0.0;
         for (int id = threadIdx.x; id < n; id += blockDim.x) {
             const int k = id % N, j = (id / N) % N, i = id / (N * N);
-            const Cof<float> co = cofactors(load19<float>(th, N, i, j, k), ih2);
-            const float r = f[id] - jac_apply(co, load19<float>(e, N, i, j, k), ih2);
+            const float r = f[id] - jac_apply(cof_at(cof, ncof, (unsigned)id), load19<float>(e, N, i, j, k), ih2);
             work[id] = r;
             sr += (double)r;
         }
@@ -999,7 +1033,7 @@ k_lin_coarse(float *e, float *work, const float *f, const float *th, int N, floa
                 const int j = r % N, i = r / N;
                 const int par = (colour + i + j) & 1;
                 const int ka = 2 * m + par, kb = 2 * m + 1 - par;
-                const Cof<float> a = cofactors(load19<float>(th, N, i, j, ka), ih2);
+                const Cof<float> a = cof_at(cof, ncof, offs(N, i, j, ka));
                 const Nb19<float> ev = load19<float>(src, N, i, j, ka);
                 const float Je = jac_apply(a, ev, ih2);
                 const float diag = -2.0f * (a.xx + a.yy + a.zz) * ih2;
@@ -1247,16 +1281,16 @@ cudaError_t lin_vcycle(recon_handle *H, int l)
     const float ih2 = (float)(1.0 / (h * h));
     if (l == H->nlev - 1) {
         note_launch();
-        k_lin_coarse<<<1, kCoarseThreads, 0, s>>>(H->e32[l], H->work32, H->f32[l], H->t32[l], N,
+        k_lin_coarse<<<1, kCoarseThreads, 0, s>>>(H->e32[l], H->work32, H->f32[l], H->cof32[l], N,
                                                   ih2, cf.coarse_max_sweeps, cf.coarse_rtol);
         return cudaGetLastError();
     }
-    CK(lin_sweep(N, h, H->e32[l], H->f32[l], H->t32[l], cf.nu1, H->work32, s));
+    CK(lin_sweep(N, h, H->e32[l], H->f32[l], H->cof32[l], cf.nu1, H->work32, s));
     const int Nc = H->Nl[l + 1];
     const size_t nc = ncell(Nc);
     const unsigned nbr = row_grid(Nc, kMaxRedBlocks);
     note_launch();
-    k_lin_restrict_residual<<<nbr, row_block(), 0, s>>>(H->e32[l], H->f32[l], H->t32[l], N, ih2,
+    k_lin_restrict_residual<<<nbr, row_block(), 0, s>>>(H->e32[l], H->f32[l], H->cof32[l], N, ih2,
                                                      H->f32[l + 1], H->partials);
     note_launch();
     k_finalize_mean<<<1, kReduceThreads, 0, s>>>(H->partials, nbr, (double)nc,
@@ -1266,7 +1300,7 @@ cudaError_t lin_vcycle(recon_handle *H, int l)
     CK(cudaMemsetAsync(H->e32[l + 1], 0, sizeof(float) * nc, s));
     CK(lin_vcycle(H, l + 1));
     CK(prolong_add<float>(Nc, H->e32[l + 1], (const float *)nullptr, nullptr, 1.0, H->e32[l], s));
-    return lin_sweep(N, h, H->e32[l], H->f32[l], H->t32[l], cf.nu2, H->work32, s);
+    return lin_sweep(N, h, H->e32[l], H->f32[l], H->cof32[l], cf.nu2, H->work32, s);
 }
 
 }  // namespace
@@ -1336,6 +1370,11 @@ cudaError_t mixed_correct(recon_handle *H, double *phi)
     note_launch();
     k_sub_scalar<<<blocks_for(n), kThreads, 0, s>>>(H->f32[0], n, H->scal + S_MEAN_R);
     for (int l = 1; l < H->nlev; ++l) CK(restrict_plain<float>(H->Nl[l - 1], H->t32[l - 1], H->t32[l], s));
+    for (int l = 0; l < H->nlev; ++l) {
+        note_launch();
+        k_cof6f<<<row_grid(H->Nl[l]), row_block(), 0, s>>>(H->t32[l], H->Nl[l],
+                                                           (float)(1.0 / (H->hl[l] * H->hl[l])), H->cof32[l]);
+    }
     CK(cudaMemsetAsync(H->e32[0], 0, sizeof(float) * n, s));
     for (int v = 0; v < H->cfg.mixed_linear_vcycles; ++v) CK(lin_vcycle(H, 0));
     note_launch();
