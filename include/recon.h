@@ -68,7 +68,7 @@ typedef enum {
 /* Solver options.  Defaults (recon_create): nu1 = nu2 = 2,
  * coarse_max_sweeps = 200, coarse_rtol = 1e-3, rule = NEWTON1, start = FMG,
  * scale_floor = 0.5, mixed_switch_rtol = 1e-4, mixed_fas_max_cycles = 12,
- * mixed_linear_vcycles = 2, mixed_df_residual = 1. */
+ * mixed_linear_vcycles = 2, mixed_df_residual = 1, fused_chunk = 0. */
 typedef struct {
     int nu1, nu2;               /* pre- / post-smoothing sweeps per level          */
     int coarse_max_sweeps;      /* coarsest grid: sweep cap                        */
@@ -88,6 +88,8 @@ typedef struct {
                                    double-float pairs (hi + lo floats, 48-bit
                                    significand, FP32 pipes) while iterating;
                                    0 = plain FP64 arithmetic for both          */
+    int fused_chunk;            /* planes per thread block of the fused smoother
+                                   sweeps (grids >= 128^3): 8..128, 0 = by size  */
 } recon_config;
 
 #define RECON_HISTORY_MAX 64

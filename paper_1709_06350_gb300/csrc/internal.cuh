@@ -71,6 +71,8 @@ unsigned long long launch_count();
 
 // Dynamic shared-memory limits of the fused kernels (set before any capture).
 cudaError_t prepare_kernels();
+// Planes per CTA of the fused sweeps enqueued next on this host thread (0 = auto).
+void set_fused_chunk(int c);
 
 // Message returned by recon_last_error(NULL) on this thread.
 void set_thread_error(const char *msg);

@@ -51,6 +51,7 @@ recon_config default_config()
     c.mixed_fas_max_cycles = 12;
     c.mixed_linear_vcycles = 2;
     c.mixed_df_residual = 1;
+    c.fused_chunk = 0;
     return c;
 }
 
@@ -280,7 +281,8 @@ recon_status recon_set_config(recon_handle *H, const recon_config *c)
     if (!(c->scale_floor < 1.0) || !std::isfinite(c->scale_floor))
         return set_err(H, RECON_E_INVALID, "scale_floor must be < 1");
     if (!(c->mixed_switch_rtol > 0.0) || c->mixed_fas_max_cycles < 0 || c->mixed_linear_vcycles < 1 ||
-        (c->mixed_df_residual != 0 && c->mixed_df_residual != 1))
+        (c->mixed_df_residual != 0 && c->mixed_df_residual != 1) ||
+        (c->fused_chunk != 0 && (c->fused_chunk < 8 || c->fused_chunk > 128)))
         return set_err(H, RECON_E_INVALID, "bad mixed-precision options");
     H->cfg = *c;
     return RECON_OK;
@@ -350,6 +352,7 @@ recon_status recon_step_sweep(int N, double h, int prec, int rule, void *theta, 
     if (!step_size_ok(N) || !(h > 0) || sweeps < 0 || !theta || !g || !work || (rule != 0 && rule != 1))
         return RECON_E_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
+    set_fused_chunk(0);
     cudaError_t e = prec == 0
         ? sweep<double>(N, h, rule, (double *)theta, (const double *)g, nullptr, c, sweeps, (double *)work, s)
         : prec == 1 ? sweep<float>(N, h, rule, (float *)theta, (const float *)g, nullptr, c, sweeps, (float *)work, s)
@@ -422,6 +425,7 @@ recon_status recon_step_linear_sweep(int N, double h, float *e, const float *f, 
 {
     if (!step_size_ok(N) || !(h > 0) || sweeps < 0 || !e || !f || !theta || !work)
         return RECON_E_INVALID;
+    set_fused_chunk(0);
     return linear_sweep(N, h, e, f, theta, sweeps, work, (cudaStream_t)stream) == cudaSuccess
                ? RECON_OK : RECON_E_CUDA;
 }

@@ -259,6 +259,10 @@ static cudaError_t fused_attr()
 }
 
 static bool g_kernels_ready = false;
+// planes per CTA of the fused sweeps for the solve being enqueued on this
+// host thread (recon_config.fused_chunk; 0 = by grid size)
+static thread_local int g_fused_chunk = 0;
+void set_fused_chunk(int c) { g_fused_chunk = c; }
 
 cudaError_t prepare_kernels()
 {
@@ -281,7 +285,7 @@ static cudaError_t fused_sweep_launch(int N, const T *src, T *dst, const T *g, c
         const cudaError_t e = prepare_kernels();
         if (e != cudaSuccess) return e;
     }
-    const int CI = N >= 512 ? 64 : (N >= 256 ? 32 : 16);
+    const int CI = g_fused_chunk > 0 ? g_fused_chunk : (N >= 512 ? 64 : (N >= 256 ? 32 : 16));
     const dim3 grid((N + kTK - 1) / kTK, (N + kTJ - 1) / kTJ, (N + CI - 1) / CI);
     note_launch();
     k_sweep_fused<T, LIN><<<grid, kFT, smem, s>>>(src, dst, g, cof, cptr, cval, N, CI, ih2, h2_6, rule);
@@ -1086,6 +1090,7 @@ cudaError_t vcycle(recon_handle *H, const Hier<T> &Y, int l, const double *cptr)
 {
     cudaStream_t s = H->stream;
     const recon_config &cf = H->cfg;
+    set_fused_chunk(cf.fused_chunk);
     const int N = H->Nl[l];
     const double h = H->hl[l];
     if (l == H->nlev - 1)
@@ -1276,6 +1281,7 @@ cudaError_t lin_vcycle(recon_handle *H, int l)
 {
     cudaStream_t s = H->stream;
     const recon_config &cf = H->cfg;
+    set_fused_chunk(cf.fused_chunk);
     const int N = H->Nl[l];
     const double h = H->hl[l];
     const float ih2 = (float)(1.0 / (h * h));
