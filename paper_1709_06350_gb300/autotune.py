@@ -15,7 +15,8 @@ import time
 
 from . import recon, synth
 
-CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
+# tuned schedules, keyed by GPU name, grid size and dtype (written by tune())
+CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "autotune_cache.json")
 
 # candidate values; the search is a coordinate descent from the defaults
 SPACE = {
