@@ -211,6 +211,8 @@ def main():
 
     dtype = recon.RECON_MIXED if args.dtype == "mixed" else recon.RECON_F64
     solver = recon.Solver(N, L, dtype)
+    from paper_1709_06350_gb300 import autotune
+    tuned = autotune.apply(solver, N, dtype)
     rho = torch.zeros((N, N, N), dtype=torch.float64, device=dev)
     phi = torch.zeros_like(rho)
     stream = torch.cuda.current_stream()
@@ -316,6 +318,7 @@ def main():
         torch.cuda.empty_cache()
         batch = bench_batch(recon, synth, torch, dev, args.batch_count)
         solver = recon.Solver(N, L, dtype)
+        autotune.apply(solver, N, dtype)
 
     adj = None
     if not args.no_adjoint and rank == 0:
@@ -345,7 +348,9 @@ def main():
                                     f"+ solve to ||r||/||b-1|| < {tol:g} + displacement"),
                        "l2": "inputs larger than L2 (particle positions "
                              f"{pos.numel() * 8 / 1e9:.1f} GB, fields {N ** 3 * 8 / 1e9:.2f} GB)",
-                       "solver": solver.config()},
+                       "solver": solver.config(),
+                       "schedule": "autotuned (paper_1709_06350_gb300/autotune_cache.json)"
+                                   if tuned else "defaults"},
             "time_to_tol_s": {"mixed": statistics.median(solve_times) / 1e3,
                               "fp64": fp64["time_to_tol_s"] if fp64 else None},
             "solve": {"fas_cycles": st["cycles"], "outer_iterations": st["outer_iterations"],
@@ -392,6 +397,8 @@ def bench_batch(recon, synth, torch, dev, count):
     for s in deposit.values():
         s.close()
     B = recon.Batch(sizes, boxes)
+    from paper_1709_06350_gb300 import autotune
+    autotune.apply(B)
     phis = [torch.zeros_like(b) for b in bs]
     B.solve(bs, phis=phis, tol=1e-8, max_cycles=40)          # captures the graphs
     torch.cuda.synchronize()
@@ -493,8 +500,8 @@ def kernel_roofline(recon, torch, N, L, dev, stream):
     on its stream (one launch = one fused red+black sweep for N >= 128).
 
     Algorithmic bytes per sweep: FAS smoother 12 B/cell (read theta and b,
-    write theta); linear smoother 36 B/cell (read e, f and the six
-    precomputed cofactors of the cell; write e)."""
+    write theta); linear smoother 44 B/cell (read e, f and the cell's
+    precomputed 32-byte cofactor record; write e)."""
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -512,13 +519,13 @@ def kernel_roofline(recon, torch, N, L, dev, stream):
     t_fas = _time_launches(torch, stream, lambda k: recon.recon_step_sweep(
         th, g, 0.0, h, sweeps=k, work=work, stream=stream), reps)
     e = torch.zeros_like(th)
-    work7 = torch.empty(7 * N ** 3, dtype=torch.float32, device=dev)
+    work7 = torch.empty(9 * N ** 3, dtype=torch.float32, device=dev)
     t_lin = _time_launches(torch, stream, lambda k: recon.recon_step_linear_sweep(
         e, g, th, h, sweeps=k, work=work7, stream=stream), reps)
     del th, g, work, e, work7
     out = []
     for name, t, bpc in (("k_sweep_fused<float, FAS> (FP32 red-black Newton smoother, one sweep)", t_fas, 12.0),
-                         ("k_sweep_fused<float, LIN> (FP32 red-black smoother of J e = f, one sweep)", t_lin, 36.0)):
+                         ("k_sweep_fused<float, LIN> (FP32 red-black smoother of J e = f, one sweep)", t_lin, 44.0)):
         alg = bpc * N ** 3
         ach = alg / t / 1e9
         out.append({"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
