@@ -501,9 +501,9 @@ def kernel_roofline(recon, torch, N, L, dev, stream):
 
     Algorithmic bytes per sweep: FAS smoother 12 B/cell (read theta and b,
     write theta); linear smoother 16 B/cell (read theta, e, f; write e).
-    The linear kernel as built reads a precomputed 32-byte cofactor record
-    per cell instead of theta, so its DRAM traffic exceeds these bytes; the
-    fraction is always against the algorithmic figure."""
+    The linear kernel as built reads six precomputed cofactors per cell
+    instead of theta, so its DRAM traffic exceeds these bytes; the fraction
+    is always against the algorithmic figure."""
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -521,7 +521,7 @@ def kernel_roofline(recon, torch, N, L, dev, stream):
     t_fas = _time_launches(torch, stream, lambda k: recon.recon_step_sweep(
         th, g, 0.0, h, sweeps=k, work=work, stream=stream), reps)
     e = torch.zeros_like(th)
-    work7 = torch.empty(9 * N ** 3, dtype=torch.float32, device=dev)
+    work7 = torch.empty(7 * N ** 3, dtype=torch.float32, device=dev)
     t_lin = _time_launches(torch, stream, lambda k: recon.recon_step_linear_sweep(
         e, g, th, h, sweeps=k, work=work7, stream=stream), reps)
     del th, g, work, e, work7

@@ -88,9 +88,9 @@ recon_status recon_step_cic_cells(const double *pos, long long n, int N, double 
  * (FP32 grids), the smoother of the mixed-precision defect correction:
  * e_c += (f - J e)_c / J_cc with J_cc = -2 (adj_xx + adj_yy + adj_zz) / h^2,
  * red then black, each colour reading the values held at the start of its
- * pass.  theta: the FP32 potential whose cofactors define J.  work: 9 N^3
- * floats of scratch (a ping-pong grid and one 8-float cofactor record per
- * cell, computed once per call).  N even. */
+ * pass.  theta: the FP32 potential whose cofactors define J.  work: 7 N^3
+ * floats of scratch (a ping-pong grid and the six cofactor arrays, computed
+ * once per call).  N even. */
 recon_status recon_step_linear_sweep(int N, double h, float *e, const float *f,
                                      const float *theta, int sweeps, float *work,
                                      void *stream);

@@ -43,7 +43,7 @@ struct recon_handle {
     float *e32[kMaxLevels] = {}, *f32[kMaxLevels] = {};
     float *work32 = nullptr;
     float *lo32 = nullptr, *blo32 = nullptr;   // low halves of phi and b (double-float)
-    float *cof32[kMaxLevels] = {};             // cofactors of I + H theta32, [n_l][8]
+    float *cof32[kMaxLevels] = {};             // cofactors of I + H theta32, [6][n_l]
 
     double *scal = nullptr;      // device scalars (recon::Slot)
     double *partials = nullptr;  // kMaxRedBlocks x 4 doubles

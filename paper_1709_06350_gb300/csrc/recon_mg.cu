@@ -69,8 +69,7 @@ k_rb_pass(const T *__restrict__ src, T *__restrict__ dst, const T *__restrict__ 
 // RED, edges and centre from OLD) and write plane s.  DRAM traffic: src and
 // g read once, dst written once.  The linear variant (LIN) relaxes J e = f:
 // the staged unknown is e, g is f, and the cofactors of I + H theta at each
-// updated cell come from a precomputed 32-byte record per cell (cof,
-// [N^3][8] floats: xx yy zz xy | yz xz - -, two 16-byte loads).
+// updated cell come from six precomputed arrays (cof, [6][N^3]).
 // Requires N >= kFusedMinN (so one wrap suffices for every halo index).
 // ----------------------------------------------------------------------
 constexpr int kTJ = 16, kTK = 64;
@@ -139,16 +138,13 @@ __device__ __forceinline__ T cell_update(const Nb19<T> &nb, const T *cof, size_t
                                          T rhs, T ih2, T h2_6, int rule)
 {
     if constexpr (LIN) {
-        const float4 c0 = reinterpret_cast<const float4 *>(cof)[2 * (size_t)o];
-        const float4 c1 = reinterpret_cast<const float4 *>(cof)[2 * (size_t)o + 1];
         Cof<T> a;
-        a.xx = c0.x;
-        a.yy = c0.y;
-        a.zz = c0.z;
-        a.xy = c0.w;
-        a.yz = c1.x;
-        a.xz = c1.y;
-        (void)n;
+        a.xx = cof[o];
+        a.yy = cof[n + o];
+        a.zz = cof[2 * n + o];
+        a.xy = cof[3 * n + o];
+        a.yz = cof[4 * n + o];
+        a.xz = cof[5 * n + o];
         const T Je = jac_apply(a, nb, ih2);
         const T diag = T(-2) * (a.xx + a.yy + a.zz) * ih2;
         return nb.c + (rhs - Je) / diag;
@@ -879,34 +875,34 @@ k_df_to_double(const float *__restrict__ hi, const float *__restrict__ lo, doubl
 }
 
 // ---- linear multigrid for J e = f in FP32.  J = sum adj(I + H theta)_ab D_ab
-// with the FP32 theta of the level; its cofactors are computed once per
-// correction (k_cof8f) into one 32-byte record per cell, [N^3][8] floats
-// (xx yy zz xy | yz xz 0 0), read by every sweep with two 16-byte loads.
+// with the FP32 theta of the level; its six cofactor arrays ([6][N^3]) are
+// computed once per correction (k_cof6f) and read by every sweep.
 __global__ void __launch_bounds__(kRowThreads)
-k_cof8f(const float *__restrict__ th, int N, float ih2, float *__restrict__ cof)
+k_cof6f(const float *__restrict__ th, int N, float ih2, float *__restrict__ cof)
 {
+    const size_t n = (size_t)N * N * N;
     FOR_ROWS(N, i, j)
     for (int k = threadIdx.x; k < N; k += kRowX) {
         const Cof<float> a = cofactors(load19<float>(th, N, i, j, k), ih2);
-        const size_t id = offs(N, i, j, k);
-        float4 *c = reinterpret_cast<float4 *>(cof) + 2 * id;
-        c[0] = make_float4(a.xx, a.yy, a.zz, a.xy);
-        c[1] = make_float4(a.yz, a.xz, 0.0f, 0.0f);
+        const unsigned id = offs(N, i, j, k);
+        cof[id] = a.xx;
+        cof[n + id] = a.yy;
+        cof[2 * n + id] = a.zz;
+        cof[3 * n + id] = a.xy;
+        cof[4 * n + id] = a.yz;
+        cof[5 * n + id] = a.xz;
     }
 }
 
 __device__ __forceinline__ Cof<float> cof_at(const float *cof, size_t n, unsigned o)
 {
-    (void)n;
-    const float4 c0 = reinterpret_cast<const float4 *>(cof)[2 * (size_t)o];
-    const float4 c1 = reinterpret_cast<const float4 *>(cof)[2 * (size_t)o + 1];
     Cof<float> a;
-    a.xx = c0.x;
-    a.yy = c0.y;
-    a.zz = c0.z;
-    a.xy = c0.w;
-    a.yz = c1.x;
-    a.xz = c1.y;
+    a.xx = cof[o];
+    a.yy = cof[n + o];
+    a.zz = cof[2 * n + o];
+    a.xy = cof[3 * n + o];
+    a.yz = cof[4 * n + o];
+    a.xz = cof[5 * n + o];
     return a;
 }
 
@@ -962,11 +958,11 @@ static cudaError_t lin_sweep(int N, double h, float *e, const float *f, const fl
 cudaError_t linear_sweep(int N, double h, float *e, const float *f, const float *th, int sweeps,
                          float *work, cudaStream_t s)
 {
-    // work: N^3 ping-pong followed by the [N^3][8] cofactor records
+    // work: N^3 ping-pong followed by the 6 N^3 cofactor arrays
     const size_t n = (size_t)N * N * N;
     float *cof = work + n;
     note_launch();
-    k_cof8f<<<row_grid(N), row_block(), 0, s>>>(th, N, (float)(1.0 / (h * h)), cof);
+    k_cof6f<<<row_grid(N), row_block(), 0, s>>>(th, N, (float)(1.0 / (h * h)), cof);
     return lin_sweep(N, h, e, f, cof, sweeps, work, s);
 }
 
@@ -1382,7 +1378,7 @@ cudaError_t mixed_correct(recon_handle *H, double *phi)
     for (int l = 1; l < H->nlev; ++l) CK(restrict_plain<float>(H->Nl[l - 1], H->t32[l - 1], H->t32[l], s));
     for (int l = 0; l < H->nlev; ++l) {
         note_launch();
-        k_cof8f<<<row_grid(H->Nl[l]), row_block(), 0, s>>>(H->t32[l], H->Nl[l],
+        k_cof6f<<<row_grid(H->Nl[l]), row_block(), 0, s>>>(H->t32[l], H->Nl[l],
                                                            (float)(1.0 / (H->hl[l] * H->hl[l])), H->cof32[l]);
     }
     CK(cudaMemsetAsync(H->e32[0], 0, sizeof(float) * n, s));

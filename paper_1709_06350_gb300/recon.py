@@ -291,14 +291,14 @@ def recon_step_cic_cells(pos, N, L, cells, frac, stream=None):
 
 
 def recon_step_linear_sweep(e, f, theta, h, sweeps=1, work=None, stream=None):
-    """work: 9 N^3 floats (ping-pong grid + 8-float cofactor record per cell)."""
+    """work: 7 N^3 floats (ping-pong grid + six cofactor arrays)."""
     import torch
     N = e.shape[0]
-    work = torch.empty(9 * N ** 3, dtype=torch.float32, device=e.device) if work is None else work
+    work = torch.empty(7 * N ** 3, dtype=torch.float32, device=e.device) if work is None else work
     _check(load().recon_step_linear_sweep(N, float(h), _dev_ptr(e, torch.float32),
                                           _dev_ptr(f, torch.float32, N ** 3),
                                           _dev_ptr(theta, torch.float32, N ** 3), int(sweeps),
-                                          _dev_ptr(work, torch.float32, 9 * N ** 3), _stream(stream)))
+                                          _dev_ptr(work, torch.float32, 7 * N ** 3), _stream(stream)))
 
 
 def recon_step_jacobian_apply(theta, v, h, out, stream=None):
