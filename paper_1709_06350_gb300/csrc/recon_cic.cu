@@ -54,14 +54,14 @@ __device__ __forceinline__ void cic_scatter2(const double xyz[3], float v0, floa
     int i0[3];
     double f[3];
     for (int d = 0; d < 3; ++d) cic_axis(xyz[d], N, inv_h, i0[d], f[d]);
+    const float fx = (float)f[0], fy = (float)f[1], fz = (float)f[2];
     for (int a = 0; a < 2; ++a)
         for (int b = 0; b < 2; ++b)
             for (int cc = 0; cc < 2; ++cc) {
                 const int i = a ? (i0[0] + 1 == N ? 0 : i0[0] + 1) : i0[0];
                 const int j = b ? (i0[1] + 1 == N ? 0 : i0[1] + 1) : i0[1];
                 const int k = cc ? (i0[2] + 1 == N ? 0 : i0[2] + 1) : i0[2];
-                const float w = (float)((a ? f[0] : 1.0 - f[0]) * (b ? f[1] : 1.0 - f[1]) *
-                                        (cc ? f[2] : 1.0 - f[2]));
+                const float w = (a ? fx : 1.0f - fx) * (b ? fy : 1.0f - fy) * (cc ? fz : 1.0f - fz);
                 atomicAdd(acc + offs(N, i, j, k), make_float2(v0 * w, v1 * w));
             }
 }
@@ -107,10 +107,9 @@ cudaError_t cic_deposit(const double *pos, long long n, int N, double L, double 
 
 // ---------------------------------------------------------------- displace
 // Per Eulerian cell x_c: psi = -grad phi (central differences, FP64), the
-// mapped Lagrangian position q = x + grad phi (mod L, FP64, explicitly
-// rounded so that its CIC cell matches any IEEE evaluation), and
+// mapped Lagrangian position q = x + grad phi (mod L, FP64), and
 // v = 3 - tr((I + H)^-1) computed in FP32 from the FP64 Hessian; the pair
-// (b v, b) is accumulated at q with CIC weights in FP32 (vector atomics).
+// (b v, b) is accumulated at q with FP32 CIC weights (vector atomics).
 // delta_r = sum(b v) / max(sum(b), 1e-12) then carries FP32 rounding
 // (~1e-6 absolute for |delta_r| < 3).
 __global__ void __launch_bounds__(kRowX * kRowY)
@@ -118,13 +117,14 @@ k_displace_cells(const double *__restrict__ t, const double *__restrict__ b, int
                  double h, double ih2, double *__restrict__ psi, float2 *__restrict__ acc)
 {
     const unsigned n = (unsigned)N * N * N;
-    const double inv_h = (double)N / L;
+    const double inv_h = (double)N / L, inv_2h = 0.5 / h;
     FOR_ROWS(N, i, j)
     for (int k = threadIdx.x; k < N; k += kRowX) {
         const unsigned id = offs(N, i, j, k);
         const Nb19<double> nb = load19<double>(t, N, i, j, k);
-        const double g[3] = {(nb.xp - nb.xm) / (2.0 * h), (nb.yp - nb.ym) / (2.0 * h),
-                             (nb.zp - nb.zm) / (2.0 * h)};
+        // central gradient; a multiply by 1/(2h) (within 1 ulp of the quotient)
+        const double g[3] = {(nb.xp - nb.xm) * inv_2h, (nb.yp - nb.ym) * inv_2h,
+                             (nb.zp - nb.zm) * inv_2h};
         const double x[3] = {__dmul_rn(i + 0.5, h), __dmul_rn(j + 0.5, h), __dmul_rn(k + 0.5, h)};
         double q[3];
         for (int d = 0; d < 3; ++d) {

@@ -89,6 +89,16 @@ struct FusedSmem {
 
 __device__ __forceinline__ int wrap1(int x, int N) { return x < 0 ? x + N : (x >= N ? x - N : x); }
 
+// Colour-split position of cell (i, j, k) in a per-cell operand array of the
+// linear smoother: within each row (i, j) the N/2 cells of colour
+// (i+j+k) % 2 == 0 come first, then the N/2 others, each in k order, so the
+// cells one colour pass updates are contiguous (coalesced loads).
+__host__ __device__ __forceinline__ unsigned cof_slot(int N, int i, int j, int k)
+{
+    return ((unsigned)i * (unsigned)N + (unsigned)j) * (unsigned)N +
+           (((i + j + k) & 1) ? (unsigned)(N >> 1) : 0u) + (unsigned)(k >> 1);
+}
+
 __device__ __forceinline__ void cp_async_elem(float *sdst, const float *gsrc)
 {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
@@ -137,6 +147,7 @@ template <typename T, bool LIN>
 __device__ __forceinline__ T cell_update(const Nb19<T> &nb, const T *cof, size_t n, unsigned o,
                                          T rhs, T ih2, T h2_6, int rule)
 {
+    // o: the cell's colour-split slot in the cofactor arrays (LIN only)
     if constexpr (LIN) {
         Cof<T> a;
         a.xx = cof[o];
@@ -200,8 +211,10 @@ k_sweep_fused(const T *__restrict__ src, T *__restrict__ dst, const T *__restric
             const int q = 2 * m + ((pw + gj + kfirst) & 1);   // the red cell of the pair
             const int gk = k0 - 1 + q;
             const Nb19<T> nb = nb_from<T, kOK>(S.old_[om], S.old_[oc], S.old_[op], r + 1, q + 1);
-            const unsigned go = pb + (unsigned)wrap1(gj, N) * (unsigned)N + (unsigned)wrap1(gk, N);
-            S.red_[rslot][r][q] = cell_update<T, LIN>(nb, cof, ncell, go, g[go] + c, ih2, h2_6, rule);
+            const int wj = wrap1(gj, N), wk = wrap1(gk, N);
+            const unsigned go = pb + (unsigned)wj * (unsigned)N + (unsigned)wk;
+            S.red_[rslot][r][q] = cell_update<T, LIN>(nb, cof, ncell, cof_slot(N, pw, wj, wk),
+                                                      g[go] + c, ih2, h2_6, rule);
         }
     };
 
@@ -242,7 +255,8 @@ k_sweep_fused(const T *__restrict__ src, T *__restrict__ dst, const T *__restric
             nb.zp = S.red_[rc][r + 1][qb + 2];
             nb.zm = S.red_[rc][r + 1][qb];
             const unsigned gb = pb + (unsigned)gj * (unsigned)N + (unsigned)k0;
-            const T vb = cell_update<T, LIN>(nb, cof, ncell, gb + qb, g[gb + qb] + c, ih2, h2_6, rule);
+            const T vb = cell_update<T, LIN>(nb, cof, ncell, cof_slot(N, s, gj, k0 + qb), g[gb + qb] + c,
+                                             ih2, h2_6, rule);
             const T vr = S.red_[rc][r + 1][qr + 1];
             dst[gb + qb] = vb;
             dst[gb + qr] = vr;
@@ -876,7 +890,8 @@ k_df_to_double(const float *__restrict__ hi, const float *__restrict__ lo, doubl
 
 // ---- linear multigrid for J e = f in FP32.  J = sum adj(I + H theta)_ab D_ab
 // with the FP32 theta of the level; its six cofactor arrays ([6][N^3]) are
-// computed once per correction (k_cof6f) and read by every sweep.
+// computed once per correction (k_cof6f) and read by every sweep; they are
+// stored colour-split within each row (cof_slot).
 __global__ void __launch_bounds__(kRowThreads)
 k_cof6f(const float *__restrict__ th, int N, float ih2, float *__restrict__ cof)
 {
@@ -884,7 +899,7 @@ k_cof6f(const float *__restrict__ th, int N, float ih2, float *__restrict__ cof)
     FOR_ROWS(N, i, j)
     for (int k = threadIdx.x; k < N; k += kRowX) {
         const Cof<float> a = cofactors(load19<float>(th, N, i, j, k), ih2);
-        const unsigned id = offs(N, i, j, k);
+        const unsigned id = cof_slot(N, i, j, k);
         cof[id] = a.xx;
         cof[n + id] = a.yy;
         cof[2 * n + id] = a.zz;
@@ -920,7 +935,7 @@ k_lin_pass(const float *__restrict__ src, float *__restrict__ dst, const float *
         const unsigned base = offs(N, i, j, 0);
         for (int m = threadIdx.x; m < half; m += kRowX) {
             const int ka = 2 * m + par, kb = 2 * m + 1 - par;
-            const Cof<float> a = cof_at(cof, n, base + ka);
+            const Cof<float> a = cof_at(cof, n, cof_slot(N, i, j, ka));
             const Nb19<float> ev = load19<float>(src, N, i, j, ka);
             const float Je = jac_apply(a, ev, ih2);
             const float diag = -2.0f * (a.xx + a.yy + a.zz) * ih2;
@@ -983,8 +998,8 @@ k_lin_restrict_residual(const float *__restrict__ e, const float *__restrict__ f
             for (int b = 0; b < 2; ++b)
                 for (int cc = 0; cc < 2; ++cc) {
                     const int i = 2 * I + a, j = 2 * J + b, k = 2 * K + cc;
-                    const unsigned o = offs(Nf, i, j, k);
-                    acc += f[o] - jac_apply(cof_at(cof, nf, o), load19<float>(e, Nf, i, j, k), ih2);
+                    acc += f[offs(Nf, i, j, k)] -
+                           jac_apply(cof_at(cof, nf, cof_slot(Nf, i, j, k)), load19<float>(e, Nf, i, j, k), ih2);
                 }
         const float v = acc * 0.125f;
         fH[offs(Nc, I, J, K)] = v;
@@ -1006,7 +1021,7 @@ k_lin_coarse(float *e, float *work, const float *f, const float *cof, int N, flo
         double sr = 0.0;
         for (int id = threadIdx.x; id < n; id += blockDim.x) {
             const int k = id % N, j = (id / N) % N, i = id / (N * N);
-            const float r = f[id] - jac_apply(cof_at(cof, ncof, (unsigned)id), load19<float>(e, N, i, j, k), ih2);
+            const float r = f[id] - jac_apply(cof_at(cof, ncof, cof_slot(N, i, j, k)), load19<float>(e, N, i, j, k), ih2);
             work[id] = r;
             sr += (double)r;
         }
@@ -1037,7 +1052,7 @@ k_lin_coarse(float *e, float *work, const float *f, const float *cof, int N, flo
                 const int j = r % N, i = r / N;
                 const int par = (colour + i + j) & 1;
                 const int ka = 2 * m + par, kb = 2 * m + 1 - par;
-                const Cof<float> a = cof_at(cof, ncof, offs(N, i, j, ka));
+                const Cof<float> a = cof_at(cof, ncof, cof_slot(N, i, j, ka));
                 const Nb19<float> ev = load19<float>(src, N, i, j, ka);
                 const float Je = jac_apply(a, ev, ih2);
                 const float diag = -2.0f * (a.xx + a.yy + a.zz) * ih2;
