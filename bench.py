@@ -177,9 +177,8 @@ def main():
         print(json.dumps({"kernel_only": n, "kernels": roof}), flush=True)
         return 0
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_1709_06350_gb300 import replicas
+    world, rank, local = replicas.world()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if world > 1:
@@ -191,20 +190,15 @@ def main():
     recon.load()
 
     def barrier():
-        if world > 1:
-            dist.barrier()
+        replicas.barrier(dist if world > 1 else None)
 
     def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return replicas.max_over_ranks(x, dist if world > 1 else None, dev)
 
     W = synth.WORKLOADS[args.workload]
     N, L, R, tol = W.N, W.L, W.R, W.tol
-    delta_lin, dh = synth.linear_field(N, L, W.sigma_lin, W.seed + 7919 * rank, backend="torch",
-                                       device=dev)
+    delta_lin, dh = synth.linear_field(N, L, W.sigma_lin, replicas.replica_seed(W.seed, rank),
+                                       backend="torch", device=dev)
     pos = synth.zeldovich_positions(dh, N, L).contiguous()
     del dh
     torch.cuda.empty_cache()
@@ -338,7 +332,8 @@ def main():
     if rank == 0:
         ms = elapsed_ms / args.steps
         line = {
-            "metric": METRIC, "value": world * args.steps / (elapsed_ms / 1e3), "unit": UNIT,
+            "metric": METRIC, "value": replicas.job_throughput(args.steps, world, elapsed_ms / 1e3),
+            "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32/f64" if dtype == recon.RECON_MIXED else "f64",

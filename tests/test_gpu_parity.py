@@ -267,3 +267,38 @@ def test_displace_parity(R, O):
     assert np.max(np.abs(host(dl) - dl_ref)) < 1e-5
     assert host(dl).max() < 3.0
     s.close()
+
+
+# ------------------------------------------------------------------ edge cases
+@pytest.mark.parametrize("N,L", [(6, 12.0), (4, 8.0), (96, 192.0)])
+def test_solve_single_level_and_odd_hierarchies(R, O, N, L):
+    """N = 4, 6: one level (the coarsest solve is the whole solve); 96: ends at 6^3."""
+    b, _, _ = zeldovich_density(O, N, L, 0.5, 2.0 * L / N, 60 + N)
+    ref, info = O.solve(b, L, tol=1e-10, max_cycles=60)
+    for dt in (R.RECON_F64, R.RECON_MIXED):
+        s = R.Solver(N, L, dt)
+        phi, st = s.solve(dev(b), tol=1e-10, max_cycles=60)
+        assert rel_l2(host(phi), ref) < (1e-10 if dt == R.RECON_F64 else 1e-6)
+        s.close()
+
+
+def test_mixed_resume_and_noconv(R, O):
+    N, L = 32, 64.0
+    b, _, _ = zeldovich_density(O, N, L, 0.8, 4.0, 71)
+    s = R.Solver(N, L, R.RECON_MIXED)
+    phi, st = s.solve(dev(b), tol=1e-10)
+    s.configure(start=R.START_GUESS, mixed_fas_max_cycles=0)
+    phi2, st2 = s.solve(dev(b), phi=phi.clone(), tol=1e-9)
+    assert st2["outer_iterations"] == 1 and st2["rel_residual"] < 1e-9
+    status, st3 = R.recon_solve(s.h, N, dev(b), torch.zeros_like(phi), 1e-15, 1,
+                                raise_on_noconv=False)
+    assert status == 3 and st3["outer_iterations"] == 1
+    s.close()
+
+
+def test_launch_counter_counts_our_kernels(R):
+    before = R.recon_kernel_launches()
+    s = R.Solver(16, 16.0)
+    s.solve(torch.ones((16,) * 3, dtype=torch.float64, device="cuda") * 1.0, tol=1e-8)
+    assert R.recon_kernel_launches() > before
+    s.close()
