@@ -109,7 +109,7 @@ recon_status check_domain(recon_handle *H, const double *b);
 // H->stream and never synchronise
 cudaError_t mixed_start(recon_handle *H, const double *b, const double *phi);
 cudaError_t mixed_fas_cycle(recon_handle *H);
-cudaError_t mixed_switch(recon_handle *H, const double *b, double *phi);
+cudaError_t mixed_switch(recon_handle *H, const double *b, double *phi, bool from_phi);
 cudaError_t mixed_residual(recon_handle *H, const double *b, const double *phi);
 cudaError_t mixed_correct(recon_handle *H, double *phi);
 cudaError_t mixed_finish(recon_handle *H, double *phi, bool converged);

@@ -223,7 +223,7 @@ recon_status recon_batch_solve(recon_batch *B, const double *const *b, double *c
         if (e == cudaSuccess)
             e = capture(B, [&](int i) { return recon::mixed_fas_cycle(B->h[i]); }, G_FAS);
         if (e == cudaSuccess)
-            e = capture(B, [&](int i) { return recon::mixed_switch(B->h[i], b[i], phi[i]); }, G_SWITCH);
+            e = capture(B, [&](int i) { return recon::mixed_switch(B->h[i], b[i], phi[i], false); }, G_SWITCH);
         if (e == cudaSuccess)
             e = capture(B, [&](int i) {
                 cudaError_t r = recon::mixed_residual(B->h[i], b[i], phi[i]);

@@ -1348,16 +1348,24 @@ cudaError_t mixed_fas_cycle(recon_handle *H)
     return compat_gauge<float>(H, Y, 0);
 }
 
-cudaError_t mixed_switch(recon_handle *H, const double *b, double *phi)
+// from_phi: no FP32 cycle ran after a START_GUESS start, so the caller's FP64
+// phi (not its FP32 copy) is the iterate to continue from.
+cudaError_t mixed_switch(recon_handle *H, const double *b, double *phi, bool from_phi)
 {
     cudaStream_t s = H->stream;
     const size_t n = ncell(H->N);
-    note_launch();
     if (H->cfg.mixed_df_residual) {
-        // phi = theta32 + 0 as a double-float pair; b split the same way
+        // phi as a double-float pair (theta32 + 0, or the split of phi); b split too
+        note_launch(from_phi ? 2 : 1);
         k_split_df<<<blocks_for(n), kThreads, 0, s>>>(b, H->g32[0], H->blo32, n);
+        if (from_phi) {
+            k_split_df<<<blocks_for(n), kThreads, 0, s>>>(phi, H->t32[0], H->lo32, n);
+            return cudaGetLastError();
+        }
         return cudaMemsetAsync(H->lo32, 0, sizeof(float) * n, s);
     }
+    if (from_phi) return cudaSuccess;
+    note_launch();
     k_to_double<<<blocks_for(n), kThreads, 0, s>>>(H->t32[0], phi, n);
     return cudaGetLastError();
 }
@@ -1451,7 +1459,8 @@ recon_status solve_mixed(recon_handle *H, const double *b, double *phi, double t
         prev = rel;
     }
     if (fas > cf.mixed_fas_max_cycles) fas = cf.mixed_fas_max_cycles;
-    if ((e = mixed_switch(H, b, phi)) != cudaSuccess) return fail_cuda(H, e, "mixed switch");
+    const bool from_phi = cf.start == RECON_START_GUESS && fas == 0;
+    if ((e = mixed_switch(H, b, phi, from_phi)) != cudaSuccess) return fail_cuda(H, e, "mixed switch");
 
     recon_status status = RECON_E_NOCONV;
     double best = INFINITY;
