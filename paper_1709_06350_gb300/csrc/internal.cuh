@@ -8,6 +8,7 @@
 
 constexpr int kMaxLevels = 16;
 constexpr int kMaxRedBlocks = 2048;   // grid cap of every reducing kernel
+constexpr int kFusedMinN = 128;       // grids of at least this size use the fused sweeps
 
 // Workspace of the adjoint (allocated at its first call): the potential of
 // every coarse level, the six cofactor arrays of every level, the iterate and
@@ -43,7 +44,7 @@ struct recon_handle {
     float *e32[kMaxLevels] = {}, *f32[kMaxLevels] = {};
     float *work32 = nullptr;
     float *lo32 = nullptr, *blo32 = nullptr;   // low halves of phi and b (double-float)
-    float *cof32[kMaxLevels] = {};             // cofactors of I + H theta32, [6][n_l]
+    float *cof32[kMaxLevels] = {};             // cofactors of I + H theta32, [6][n_l] (levels below kFusedMinN)
 
     double *scal = nullptr;      // device scalars (recon::Slot)
     double *partials = nullptr;  // kMaxRedBlocks x 4 doubles

@@ -94,7 +94,8 @@ void plan(recon_handle *H, Planner &P)
             P.take(&H->g32[l], n);
             P.take(&H->e32[l], n);
             P.take(&H->f32[l], n);
-            P.take(&H->cof32[l], 6 * n);
+            // the fused linear sweeps form the cofactors from theta32
+            if (H->Nl[l] < kFusedMinN) P.take(&H->cof32[l], 6 * n);
             if (l > 0) {
                 P.take(&H->told32[l], n);
                 P.take(&H->aux32[l], n);

@@ -60,39 +60,63 @@ k_rb_pass(const T *__restrict__ src, T *__restrict__ dst, const T *__restrict__ 
 // ----------------------------------------------------------------------
 // Fused sweep: both colour passes in one kernel, src -> dst, with the same
 // snapshot semantics as two k_rb_pass launches.  A CTA owns a TJ x TK tile
-// of (j, k) and streams a chunk of planes along i through shared memory:
-//   OLD  ring of 5 planes of src, tile + 2-cell halo (planes s-1 .. s+2 in
-//        use, plane s+3 arriving by cp.async while step s computes)
-//   RED  ring of 3 planes of red-new values, tile + 1-cell halo
-// Step s: update the red cells of plane s+1 on the tile + 1 halo (they read
-// only OLD values), then the black cells of plane s on the tile (faces from
-// RED, edges and centre from OLD) and write plane s.  DRAM traffic: src and
-// g read once, dst written once.  The linear variant (LIN) relaxes J e = f:
-// the staged unknown is e, g is f, and the cofactors of I + H theta at each
-// updated cell come from six precomputed arrays (cof, [6][N^3]).
+// of (j, k) and streams a chunk of planes along i through shared memory.
+//
+//   OLD  ring of 6 planes of src, tile + 2-cell halo.  Each row is stored
+//        colour-split: the cells of even k first, then those of odd k, so
+//        that a warp reading one neighbour of 32 same-colour cells reads 32
+//        consecutive words (no bank conflicts).
+//   RED  ring of 4 planes holding only the new red values, tile + 1 halo.
+//   TH   (linear variant) ring of 6 planes of theta, laid out like OLD.
+//
+// Step s (one barrier): the red cells of plane s+2 (they read only OLD) and
+// the black cells of plane s (faces from RED planes s-1..s+1, edges and
+// centre from OLD); plane s+4 arrives by cp.async meanwhile.  The red cells
+// are computed on the tile + 1 halo, so a CTA needs nothing from another.
+// DRAM traffic: src and g read once, dst written once (linear variant:
+// theta read once more).  The linear variant (LIN) relaxes J e = f: the
+// staged unknown is e, g is f, and the cofactors of I + H theta at each
+// updated cell are formed from the staged theta.
 // Requires N >= kFusedMinN (so one wrap suffices for every halo index).
 // ----------------------------------------------------------------------
 constexpr int kTJ = 16, kTK = 64;
-constexpr int kFusedMinN = 128;
-constexpr int kOJ = kTJ + 4, kOK = kTK + 4;   // OLD plane extent
-constexpr int kRJ = kTJ + 2, kRK = kTK + 2;   // RED plane extent
-constexpr int kFT = 256;                      // threads per CTA
-constexpr int kOElem = kOJ * kOK;             // 1360 elements per OLD plane
+constexpr int kOJ = kTJ + 4;                 // OLD rows
+constexpr int kOH = (kTK + 4) / 2;           // 34 cells of one k parity per OLD row
+constexpr int kRJ = kTJ + 2;                 // RED rows
+constexpr int kRH = (kTK + 2) / 2;           // 33 red cells per RED row
+constexpr int kFT = 256;                     // threads per CTA
+constexpr int kOElem = kOJ * 2 * kOH;        // 1360 elements per OLD plane
 constexpr int kLoadsPerThread = (kOElem + kFT - 1) / kFT;   // 6
-constexpr int kOSlots = 5, kRSlots = 3;
+constexpr int kOSlots = 6, kRSlots = 4;
+constexpr int kRowItems = kTK / 2;           // 32: one warp per row
+constexpr int kRedMain = kRJ * kRowItems;    // 576 red cells with index < 32
+constexpr int kRedItems = kRJ * kRH;         // 594 (+ the 18 cells of index 32)
+constexpr int kBlackItems = kTJ * kRowItems; // 512
+static_assert(kRowItems == 32 && kRH == kRowItems + 1, "one warp per tile row");
+
+template <typename T>
+using OldPlane = T[kOJ][2][kOH];
 
 template <typename T, bool LIN>
-struct FusedSmem {
-    T old_[kOSlots][kOJ][kOK];
-    T red_[kRSlots][kRJ][kRK];
+struct FusedSmem;
+template <typename T>
+struct FusedSmem<T, false> {
+    OldPlane<T> old_[kOSlots];
+    T red_[kRSlots][kRJ][kRH];
+};
+template <typename T>
+struct FusedSmem<T, true> {
+    OldPlane<T> old_[kOSlots];
+    T red_[kRSlots][kRJ][kRH];
+    OldPlane<T> th_[kOSlots];
 };
 
 __device__ __forceinline__ int wrap1(int x, int N) { return x < 0 ? x + N : (x >= N ? x - N : x); }
 
 // Colour-split position of cell (i, j, k) in a per-cell operand array of the
-// linear smoother: within each row (i, j) the N/2 cells of colour
-// (i+j+k) % 2 == 0 come first, then the N/2 others, each in k order, so the
-// cells one colour pass updates are contiguous (coalesced loads).
+// linear smoother on the coarse (unfused) levels: within each row (i, j) the
+// N/2 cells of colour (i+j+k) % 2 == 0 come first, then the N/2 others, each
+// in k order, so the cells one colour pass updates are contiguous.
 __host__ __device__ __forceinline__ unsigned cof_slot(int N, int i, int j, int k)
 {
     return ((unsigned)i * (unsigned)N + (unsigned)j) * (unsigned)N +
@@ -113,63 +137,66 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int K>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(K)); }
 
-// 19-point neighbourhood from a shared plane triple (planes m, c, p) at
-// local (r, q) of arrays with row length K.
-template <typename T, int K>
-__device__ __forceinline__ Nb19<T> nb_from(const T (*pm)[K], const T (*pc)[K], const T (*pp)[K],
-                                           int r, int q)
+// 19-point neighbourhood from three colour-split planes (m, c, p) for the cell
+// in row r whose k parity is po: a is its index within its parity half, bp and
+// bm the indices of its k+1 and k-1 neighbours within the other half.
+template <typename T>
+__device__ __forceinline__ Nb19<T> nb_split(const OldPlane<T> &pm, const OldPlane<T> &pc,
+                                            const OldPlane<T> &pp, int r, int po, int a, int bp,
+                                            int bm)
 {
+    const int qo = po ^ 1;
     Nb19<T> v;
-    v.c = pc[r][q];
-    v.xp = pp[r][q];
-    v.xm = pm[r][q];
-    v.yp = pc[r + 1][q];
-    v.ym = pc[r - 1][q];
-    v.zp = pc[r][q + 1];
-    v.zm = pc[r][q - 1];
-    v.xpyp = pp[r + 1][q];
-    v.xmym = pm[r - 1][q];
-    v.xmyp = pm[r + 1][q];
-    v.xpym = pp[r - 1][q];
-    v.ypzp = pc[r + 1][q + 1];
-    v.ymzm = pc[r - 1][q - 1];
-    v.ymzp = pc[r - 1][q + 1];
-    v.ypzm = pc[r + 1][q - 1];
-    v.xpzp = pp[r][q + 1];
-    v.xmzm = pm[r][q - 1];
-    v.xmzp = pm[r][q + 1];
-    v.xpzm = pp[r][q - 1];
+    v.c = pc[r][po][a];
+    v.xp = pp[r][po][a];
+    v.xm = pm[r][po][a];
+    v.yp = pc[r + 1][po][a];
+    v.ym = pc[r - 1][po][a];
+    v.zp = pc[r][qo][bp];
+    v.zm = pc[r][qo][bm];
+    v.xpyp = pp[r + 1][po][a];
+    v.xmym = pm[r - 1][po][a];
+    v.xmyp = pm[r + 1][po][a];
+    v.xpym = pp[r - 1][po][a];
+    v.ypzp = pc[r + 1][qo][bp];
+    v.ymzm = pc[r - 1][qo][bm];
+    v.ymzp = pc[r - 1][qo][bp];
+    v.ypzm = pc[r + 1][qo][bm];
+    v.xpzp = pp[r][qo][bp];
+    v.xmzm = pm[r][qo][bm];
+    v.xmzp = pm[r][qo][bp];
+    v.xpzm = pp[r][qo][bm];
     return v;
 }
 
-// The cell update of one colour: nonlinear (eq. update) or linear Gauss-Seidel on J.
-template <typename T, bool LIN>
-__device__ __forceinline__ T cell_update(const Nb19<T> &nb, const T *cof, size_t n, unsigned o,
-                                         T rhs, T ih2, T h2_6, int rule)
+// The nonlinear cell update (eq. update).
+template <typename T>
+__device__ __forceinline__ T fas_update(const Nb19<T> &nb, T rhs, T ih2, T h2_6, int rule)
 {
-    // o: the cell's colour-split slot in the cofactor arrays (LIN only)
-    if constexpr (LIN) {
-        Cof<T> a;
-        a.xx = cof[o];
-        a.yy = cof[n + o];
-        a.zz = cof[2 * n + o];
-        a.xy = cof[3 * n + o];
-        a.yz = cof[4 * n + o];
-        a.xz = cof[5 * n + o];
-        const T Je = jac_apply(a, nb, ih2);
-        const T diag = T(-2) * (a.xx + a.yy + a.zz) * ih2;
-        return nb.c + (rhs - Je) / diag;
-    } else {
-        T s, p, q;
-        cubic_coeffs(nb, ih2, rhs, s, p, q);
-        return point_update(nb.c, h2_6, s, p, q, rule);
-    }
+    T s, p, q;
+    cubic_coeffs(nb, ih2, rhs, s, p, q);
+    return point_update(nb.c, h2_6, s, p, q, rule);
 }
 
+// Gauss-Seidel on J e = f at a cell: J = sum_ab adj(I + H theta)_ab D_ab,
+// J_cc = -2 (adj_xx + adj_yy + adj_zz) / h^2.
+template <typename T>
+__device__ __forceinline__ T lin_update(const Nb19<T> &nt, const Nb19<T> &ne, T rhs, T ih2)
+{
+    const Cof<T> a = cofactors(nt, ih2);
+    const T Je = jac_apply(a, ne, ih2);
+    const T diag = T(-2) * (a.xx + a.yy + a.zz) * ih2;
+    return ne.c + (rhs - Je) / diag;
+}
+
+template <typename T> struct Pair;
+template <> struct Pair<float> { using type = float2; };
+template <> struct Pair<double> { using type = double2; };
+
 template <typename T, bool LIN>
-__global__ void __launch_bounds__(kFT)
+__global__ void __launch_bounds__(kFT, sizeof(T) == 8 ? 2 : (LIN ? 3 : 5))
 k_sweep_fused(const T *__restrict__ src, T *__restrict__ dst, const T *__restrict__ g,
-              const T *__restrict__ cof, const double *__restrict__ cptr, double cval, int N,
+              const T *__restrict__ th, const double *__restrict__ cptr, double cval, int N,
               int CI, T ih2, T h2_6, int rule)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -179,90 +206,118 @@ k_sweep_fused(const T *__restrict__ src, T *__restrict__ dst, const T *__restric
     const int i1 = min(i0 + CI, N);
     const int tid = threadIdx.x;
     const unsigned NN = (unsigned)N * (unsigned)N;
-    const size_t ncell = (size_t)NN * (size_t)N;
 
-    // in-plane offsets of this thread's OLD elements (the same for every plane)
+    // this thread's OLD elements: in-plane global offset and colour-split
+    // position within a plane (the same for every plane)
     unsigned goff[kLoadsPerThread];
     int soff[kLoadsPerThread];
 #pragma unroll
     for (int t = 0; t < kLoadsPerThread; ++t) {
         const int e = tid + t * kFT;
-        const int r = e / kOK, q = e - r * kOK;
-        soff[t] = e < kOElem ? e : -1;
+        const int r = e / (2 * kOH), q = e - r * (2 * kOH);
+        soff[t] = e < kOElem ? (2 * r + (q & 1)) * kOH + (q >> 1) : -1;
         goff[t] = (unsigned)wrap1(j0 - 2 + (r < kOJ ? r : 0), N) * (unsigned)N +
                   (unsigned)wrap1(k0 - 2 + q, N);
     }
-    auto issue_plane = [&](int slot, int plane) {
-        const unsigned pb = (unsigned)wrap1(plane, N) * NN;
-        T *so = &S.old_[slot][0][0];
+    // plane p lives in OLD/TH slot (p - i0 + 2) % 6 and RED slot (p - i0 + 1) % 4
+    auto oslot = [&](int p) { return (p - i0 + 2) % kOSlots; };
+    auto rslot = [&](int p) { return (p - i0 + 1) % kRSlots; };
+    auto issue_plane = [&](int p) {
+        const unsigned pb = (unsigned)wrap1(p, N) * NN;
+        T *so = &S.old_[oslot(p)][0][0][0];
 #pragma unroll
         for (int t = 0; t < kLoadsPerThread; ++t)
             if (soff[t] >= 0) cp_async_elem(so + soff[t], src + pb + goff[t]);
+        if constexpr (LIN) {
+            T *st = &S.th_[oslot(p)][0][0][0];
+#pragma unroll
+            for (int t = 0; t < kLoadsPerThread; ++t)
+                if (soff[t] >= 0) cp_async_elem(st + soff[t], th + pb + goff[t]);
+        }
         cp_async_commit();
     };
-    // red cells of plane p on the tile + 1 halo (RED local (r, q) = OLD (r+1, q+1))
-    auto red_plane = [&](int rslot, int om, int oc, int op, int p) {
+    // red cells of plane p on the tile + 1 halo.  Item -> (RED row r, red
+    // index h): one warp per row for h < 32, then h = 32 of every row.  The
+    // red cell sits at RED column 2h + pr, i.e. OLD row r+1, parity pr ^ 1,
+    // same-parity index h + pr, k-neighbours at other-parity indices h, h+1.
+    auto red_plane = [&](int p) {
         const int pw = wrap1(p, N);
         const unsigned pb = (unsigned)pw * NN;
-        for (int e = tid; e < kRJ * (kRK / 2); e += kFT) {
-            const int r = e / (kRK / 2), m = e - r * (kRK / 2);
-            const int gj = j0 - 1 + r;
-            const int kfirst = k0 - 1 + 2 * m;
-            const int q = 2 * m + ((pw + gj + kfirst) & 1);   // the red cell of the pair
-            const int gk = k0 - 1 + q;
-            const Nb19<T> nb = nb_from<T, kOK>(S.old_[om], S.old_[oc], S.old_[op], r + 1, q + 1);
-            const int wj = wrap1(gj, N), wk = wrap1(gk, N);
-            const unsigned go = pb + (unsigned)wj * (unsigned)N + (unsigned)wk;
-            S.red_[rslot][r][q] = cell_update<T, LIN>(nb, cof, ncell, cof_slot(N, pw, wj, wk),
-                                                      g[go] + c, ih2, h2_6, rule);
+        const OldPlane<T> &om = S.old_[oslot(p - 1)], &oc = S.old_[oslot(p)], &op = S.old_[oslot(p + 1)];
+        T(*R)[kRH] = S.red_[rslot(p)];
+        for (int e = tid; e < kRedItems; e += kFT) {
+            const int r = e < kRedMain ? e / kRowItems : e - kRedMain;
+            const int h = e < kRedMain ? e % kRowItems : kRowItems;
+            const int pr = (p + j0 + r) & 1;
+            const Nb19<T> nb = nb_split<T>(om, oc, op, r + 1, pr ^ 1, h + pr, h + 1, h);
+            const unsigned go = pb + (unsigned)wrap1(j0 - 1 + r, N) * (unsigned)N +
+                                (unsigned)wrap1(k0 - 1 + 2 * h + pr, N);
+            if constexpr (LIN) {
+                const Nb19<T> nt = nb_split<T>(S.th_[oslot(p - 1)], S.th_[oslot(p)], S.th_[oslot(p + 1)],
+                                               r + 1, pr ^ 1, h + pr, h + 1, h);
+                R[r][h] = lin_update<T>(nt, nb, g[go], ih2);
+            } else {
+                R[r][h] = fas_update<T>(nb, g[go] + c, ih2, h2_6, rule);
+            }
+        }
+    };
+    // black cells of plane s on the tile, written with their red partners as
+    // (even k, odd k) pairs.  Item -> (tile row r, pair m); the black cell is
+    // at tile column 2m + pb: OLD row r+2, parity pb, index m+1; its red
+    // faces at RED row r+1, index m + pb (x, y) and m, m+1 (z).
+    auto black_plane = [&](int s) {
+        const OldPlane<T> &om = S.old_[oslot(s - 1)], &oc = S.old_[oslot(s)], &op = S.old_[oslot(s + 1)];
+        const T(*Rm)[kRH] = S.red_[rslot(s - 1)];
+        const T(*Rc)[kRH] = S.red_[rslot(s)];
+        const T(*Rp)[kRH] = S.red_[rslot(s + 1)];
+        const unsigned pb0 = (unsigned)s * NN;
+        for (int e = tid; e < kBlackItems; e += kFT) {
+            const int r = e / kRowItems, m = e % kRowItems;
+            const int gj = j0 + r, gk0 = k0 + 2 * m;
+            if (gj >= N || gk0 >= N) continue;
+            const int pb = (s + j0 + r + 1) & 1;
+            Nb19<T> nb = nb_split<T>(om, oc, op, r + 2, pb, m + 1, m + 1 + pb, m + pb);
+            nb.xp = Rp[r + 1][m + pb];
+            nb.xm = Rm[r + 1][m + pb];
+            nb.yp = Rc[r + 2][m + pb];
+            nb.ym = Rc[r][m + pb];
+            nb.zp = Rc[r + 1][m + 1];
+            nb.zm = Rc[r + 1][m];
+            const unsigned gb = pb0 + (unsigned)gj * (unsigned)N + (unsigned)gk0;
+            T vb;
+            if constexpr (LIN) {
+                const Nb19<T> nt = nb_split<T>(S.th_[oslot(s - 1)], S.th_[oslot(s)], S.th_[oslot(s + 1)],
+                                               r + 2, pb, m + 1, m + 1 + pb, m + pb);
+                vb = lin_update<T>(nt, nb, g[gb + pb], ih2);
+            } else {
+                vb = fas_update<T>(nb, g[gb + pb] + c, ih2, h2_6, rule);
+            }
+            const T vr = Rc[r + 1][m + 1 - pb];
+            typename Pair<T>::type v;
+            v.x = pb ? vr : vb;
+            v.y = pb ? vb : vr;
+            *reinterpret_cast<typename Pair<T>::type *>(dst + gb) = v;
         }
     };
 
-    // prologue: OLD planes i0-2 .. i0+2 (plane p in slot (p - i0 + 2) % 5),
-    // RED planes i0-1, i0 (plane p in slot (p - i0 + 1) % 3)
-    for (int d = 0; d < 4; ++d) issue_plane(d, i0 - 2 + d);
+    // prologue: OLD planes i0-2 .. i0+2, then RED planes i0-1 .. i0+1 while
+    // plane i0+3 arrives.  RED planes i0-1 .. i1 and OLD planes i0-2 .. i1+1
+    // are the ones the chunk needs.
+    for (int p = i0 - 2; p <= i0 + 2; ++p) issue_plane(p);
     cp_async_wait<0>();
     __syncthreads();
-    issue_plane(4, i0 + 2);
-    red_plane(0, 0, 1, 2, i0 - 1);
-    red_plane(1, 1, 2, 3, i0);
-
+    if (i0 + 3 <= i1 + 1) issue_plane(i0 + 3);
+    red_plane(i0 - 1);
+    red_plane(i0);
+    red_plane(i0 + 1);
     for (int s = i0; s < i1; ++s) {
-        const int u = s - i0;
-        __syncthreads();                                  // slot of plane s-2 is free
-        issue_plane((u + 5) % kOSlots, s + 3);            // prefetch for the next step
-        cp_async_wait<1>();                               // plane s+2 has landed
-        __syncthreads();
-        red_plane((u + 2) % 3, (u + 2) % kOSlots, (u + 3) % kOSlots, (u + 4) % kOSlots, s + 1);
-        __syncthreads();
-        // black cells of plane s on the tile; write the plane
-        const int om = (u + 1) % kOSlots, oc = (u + 2) % kOSlots, op = (u + 3) % kOSlots;
-        const int rm = u % 3, rc = (u + 1) % 3, rp = (u + 2) % 3;
-        const unsigned pb = (unsigned)s * NN;
-        for (int e = tid; e < kTJ * (kTK / 2); e += kFT) {
-            const int r = e / (kTK / 2), m = e - r * (kTK / 2);
-            const int gj = j0 + r, gk0 = k0 + 2 * m;
-            if (gj >= N || gk0 >= N) continue;
-            const int par = (s + gj + gk0) & 1;       // 0: first cell red, second black
-            const int qb = 2 * m + 1 - par;           // black cell, tile-local k
-            const int qr = 2 * m + par;               // red cell
-            // OLD local = tile + 2, RED local = tile + 1
-            Nb19<T> nb = nb_from<T, kOK>(S.old_[om], S.old_[oc], S.old_[op], r + 2, qb + 2);
-            nb.xp = S.red_[rp][r + 1][qb + 1];
-            nb.xm = S.red_[rm][r + 1][qb + 1];
-            nb.yp = S.red_[rc][r + 2][qb + 1];
-            nb.ym = S.red_[rc][r][qb + 1];
-            nb.zp = S.red_[rc][r + 1][qb + 2];
-            nb.zm = S.red_[rc][r + 1][qb];
-            const unsigned gb = pb + (unsigned)gj * (unsigned)N + (unsigned)k0;
-            const T vb = cell_update<T, LIN>(nb, cof, ncell, cof_slot(N, s, gj, k0 + qb), g[gb + qb] + c,
-                                             ih2, h2_6, rule);
-            const T vr = S.red_[rc][r + 1][qr + 1];
-            dst[gb + qb] = vb;
-            dst[gb + qr] = vr;
-        }
+        cp_async_wait<0>();   // this thread's copies of plane s+3 have landed
+        __syncthreads();      // everyone's; RED s+1 written; slots of plane s-2 free
+        if (s + 4 <= i1 + 1) issue_plane(s + 4);
+        if (s + 2 <= i1) red_plane(s + 2);
+        black_plane(s);
     }
-    cp_async_wait<0>();   // drain the last prefetch before the CTA exits
+    cp_async_wait<0>();
 }
 
 template <typename T, bool LIN>
@@ -287,8 +342,18 @@ cudaError_t prepare_kernels()
     return e;
 }
 
+// The fused sweeps store (even k, odd k) pairs as one vector: the arrays they
+// write must be aligned to two elements (true of every allocation; a caller's
+// offset view may not be, and then the two-pass kernels run instead).
+template <typename T>
+static inline bool pair_aligned(const T *p)
+{
+    return ((uintptr_t)p % (2 * sizeof(T))) == 0;
+}
+
+// th: the theta of the linear variant (nullptr for the nonlinear one)
 template <typename T, bool LIN>
-static cudaError_t fused_sweep_launch(int N, const T *src, T *dst, const T *g, const T *cof,
+static cudaError_t fused_sweep_launch(int N, const T *src, T *dst, const T *g, const T *th,
                                       const double *cptr, double cval, T ih2, T h2_6, int rule,
                                       cudaStream_t s)
 {
@@ -302,7 +367,7 @@ static cudaError_t fused_sweep_launch(int N, const T *src, T *dst, const T *g, c
     const int CI = g_fused_chunk > 0 ? g_fused_chunk : (N >= 512 ? 64 : (N >= 256 ? 32 : 16));
     const dim3 grid((N + kTK - 1) / kTK, (N + kTJ - 1) / kTJ, (N + CI - 1) / CI);
     note_launch();
-    k_sweep_fused<T, LIN><<<grid, kFT, smem, s>>>(src, dst, g, cof, cptr, cval, N, CI, ih2, h2_6, rule);
+    k_sweep_fused<T, LIN><<<grid, kFT, smem, s>>>(src, dst, g, th, cptr, cval, N, CI, ih2, h2_6, rule);
     return cudaGetLastError();
 }
 
@@ -311,7 +376,7 @@ cudaError_t sweep(int N, double h, int rule, T *t, const T *g, const double *cpt
                   double cval, int sweeps, T *work, cudaStream_t s)
 {
     const T ih2 = (T)(1.0 / (h * h)), h2_6 = (T)(h * h / 6.0);
-    if (N >= kFusedMinN) {
+    if (N >= kFusedMinN && pair_aligned(t) && pair_aligned(work)) {
         T *a = t, *b = work;
         for (int it = 0; it < sweeps; ++it) {
             const cudaError_t e = fused_sweep_launch<T, false>(N, a, b, g, (const T *)nullptr, cptr, cval, ih2, h2_6, rule, s);
@@ -889,9 +954,10 @@ k_df_to_double(const float *__restrict__ hi, const float *__restrict__ lo, doubl
 }
 
 // ---- linear multigrid for J e = f in FP32.  J = sum adj(I + H theta)_ab D_ab
-// with the FP32 theta of the level; its six cofactor arrays ([6][N^3]) are
-// computed once per correction (k_cof6f) and read by every sweep; they are
-// stored colour-split within each row (cof_slot).
+// with the FP32 theta of the level.  Grids of at least kFusedMinN form the
+// cofactors from theta inside each kernel; the coarser grids read six
+// cofactor arrays ([6][N^3]) computed once per correction (k_cof6f), stored
+// colour-split within each row (cof_slot).
 __global__ void __launch_bounds__(kRowThreads)
 k_cof6f(const float *__restrict__ th, int N, float ih2, float *__restrict__ cof)
 {
@@ -945,14 +1011,21 @@ k_lin_pass(const float *__restrict__ src, float *__restrict__ dst, const float *
     }
 }
 
+static inline bool lin_fused(int N, const float *e, const float *work)
+{
+    return N >= kFusedMinN && pair_aligned(e) && pair_aligned(work);
+}
+
+// cof: the level's cofactor arrays (read by the two-pass kernels); th: its
+// theta (read by the fused kernel)
 static cudaError_t lin_sweep(int N, double h, float *e, const float *f, const float *cof,
-                             int sweeps, float *work, cudaStream_t s)
+                             const float *th, int sweeps, float *work, cudaStream_t s)
 {
     const float ih2 = (float)(1.0 / (h * h));
-    if (N >= kFusedMinN) {
+    if (lin_fused(N, e, work)) {
         float *a = e, *b = work;
         for (int it = 0; it < sweeps; ++it) {
-            const cudaError_t err = fused_sweep_launch<float, true>(N, a, b, f, cof, nullptr, 0.0, ih2,
+            const cudaError_t err = fused_sweep_launch<float, true>(N, a, b, f, th, nullptr, 0.0, ih2,
                                                                    0.0f, 0, s);
             if (err != cudaSuccess) return err;
             float *tmp = a;
@@ -973,19 +1046,23 @@ static cudaError_t lin_sweep(int N, double h, float *e, const float *f, const fl
 cudaError_t linear_sweep(int N, double h, float *e, const float *f, const float *th, int sweeps,
                          float *work, cudaStream_t s)
 {
-    // work: N^3 ping-pong followed by the 6 N^3 cofactor arrays
+    // work: N^3 ping-pong followed by room for the 6 N^3 cofactor arrays
+    // (used by the two-pass kernels only)
     const size_t n = (size_t)N * N * N;
     float *cof = work + n;
-    note_launch();
-    k_cof6f<<<row_grid(N), row_block(), 0, s>>>(th, N, (float)(1.0 / (h * h)), cof);
-    return lin_sweep(N, h, e, f, cof, sweeps, work, s);
+    if (!lin_fused(N, e, work)) {
+        note_launch();
+        k_cof6f<<<row_grid(N), row_block(), 0, s>>>(th, N, (float)(1.0 / (h * h)), cof);
+    }
+    return lin_sweep(N, h, e, f, cof, th, sweeps, work, s);
 }
 
-// fH = R (f - J e), block partial sums for the mean projection.
+// fH = R (f - J e), block partial sums for the mean projection.  The
+// cofactors come from cof (colour-split arrays) or, when cof is null, from th.
 __global__ void __launch_bounds__(kRowThreads)
 k_lin_restrict_residual(const float *__restrict__ e, const float *__restrict__ f,
-                        const float *__restrict__ cof, int Nf, float ih2, float *__restrict__ fH,
-                        double *__restrict__ partials)
+                        const float *__restrict__ cof, const float *__restrict__ th, int Nf,
+                        float ih2, float *__restrict__ fH, double *__restrict__ partials)
 {
     __shared__ double sh[32];
     const size_t nf = (size_t)Nf * Nf * Nf;
@@ -998,8 +1075,9 @@ k_lin_restrict_residual(const float *__restrict__ e, const float *__restrict__ f
             for (int b = 0; b < 2; ++b)
                 for (int cc = 0; cc < 2; ++cc) {
                     const int i = 2 * I + a, j = 2 * J + b, k = 2 * K + cc;
-                    acc += f[offs(Nf, i, j, k)] -
-                           jac_apply(cof_at(cof, nf, cof_slot(Nf, i, j, k)), load19<float>(e, Nf, i, j, k), ih2);
+                    const Cof<float> A = cof ? cof_at(cof, nf, cof_slot(Nf, i, j, k))
+                                             : cofactors(load19<float>(th, Nf, i, j, k), ih2);
+                    acc += f[offs(Nf, i, j, k)] - jac_apply(A, load19<float>(e, Nf, i, j, k), ih2);
                 }
         const float v = acc * 0.125f;
         fH[offs(Nc, I, J, K)] = v;
@@ -1306,13 +1384,13 @@ cudaError_t lin_vcycle(recon_handle *H, int l)
                                                   ih2, cf.coarse_max_sweeps, cf.coarse_rtol);
         return cudaGetLastError();
     }
-    CK(lin_sweep(N, h, H->e32[l], H->f32[l], H->cof32[l], cf.nu1, H->work32, s));
+    CK(lin_sweep(N, h, H->e32[l], H->f32[l], H->cof32[l], H->t32[l], cf.nu1, H->work32, s));
     const int Nc = H->Nl[l + 1];
     const size_t nc = ncell(Nc);
     const unsigned nbr = row_grid(Nc, kMaxRedBlocks);
     note_launch();
-    k_lin_restrict_residual<<<nbr, row_block(), 0, s>>>(H->e32[l], H->f32[l], H->cof32[l], N, ih2,
-                                                     H->f32[l + 1], H->partials);
+    k_lin_restrict_residual<<<nbr, row_block(), 0, s>>>(H->e32[l], H->f32[l], H->cof32[l], H->t32[l],
+                                                     N, ih2, H->f32[l + 1], H->partials);
     note_launch();
     k_finalize_mean<<<1, kReduceThreads, 0, s>>>(H->partials, nbr, (double)nc,
                                                  H->scal + slot_rmean(l + 1));
@@ -1321,7 +1399,7 @@ cudaError_t lin_vcycle(recon_handle *H, int l)
     CK(cudaMemsetAsync(H->e32[l + 1], 0, sizeof(float) * nc, s));
     CK(lin_vcycle(H, l + 1));
     CK(prolong_add<float>(Nc, H->e32[l + 1], (const float *)nullptr, nullptr, 1.0, H->e32[l], s));
-    return lin_sweep(N, h, H->e32[l], H->f32[l], H->cof32[l], cf.nu2, H->work32, s);
+    return lin_sweep(N, h, H->e32[l], H->f32[l], H->cof32[l], H->t32[l], cf.nu2, H->work32, s);
 }
 
 }  // namespace
@@ -1400,6 +1478,7 @@ cudaError_t mixed_correct(recon_handle *H, double *phi)
     k_sub_scalar<<<blocks_for(n), kThreads, 0, s>>>(H->f32[0], n, H->scal + S_MEAN_R);
     for (int l = 1; l < H->nlev; ++l) CK(restrict_plain<float>(H->Nl[l - 1], H->t32[l - 1], H->t32[l], s));
     for (int l = 0; l < H->nlev; ++l) {
+        if (H->Nl[l] >= kFusedMinN) continue;   // formed from theta32 in the kernels
         note_launch();
         k_cof6f<<<row_grid(H->Nl[l]), row_block(), 0, s>>>(H->t32[l], H->Nl[l],
                                                            (float)(1.0 / (H->hl[l] * H->hl[l])), H->cof32[l]);

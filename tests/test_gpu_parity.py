@@ -72,10 +72,11 @@ def test_sweep_fp32_tracks_fp64(R, O, N):
     assert rel_max(host(th), ref) < 1e-4
 
 
-@pytest.mark.parametrize("N", [6, 48, 128])
+@pytest.mark.parametrize("N", [6, 48, 128, 144])
 def test_linear_sweep_vs_oracle_jacobian(R, O, N):
     """Red-black Gauss-Seidel on J e = f against the same sweep written with
-    the oracle's sparse Jacobian (N = 128 runs the fused kernel)."""
+    the oracle's sparse Jacobian (N >= 128 runs the fused kernel, which forms
+    the cofactors from theta; 144: a ragged k-tile)."""
     L = 2.0 * N
     h = L / N
     from paper_1709_06350_gb300 import synth
@@ -95,6 +96,41 @@ def test_linear_sweep_vs_oracle_jacobian(R, O, N):
     ev = dev(e0, torch.float32)
     R.recon_step_linear_sweep(ev, dev(f, torch.float32), dev(t, torch.float32), h, sweeps=2)
     assert rel_max(host(ev).ravel(), e) < 2e-5
+
+
+def _offset_view(x):
+    """the same values in a contiguous tensor whose storage starts one element
+    past an allocation boundary (not aligned to an element pair)"""
+    buf = torch.empty(x.numel() + 1, dtype=x.dtype, device=x.device)
+    v = buf[1:].view(x.shape)
+    v.copy_(x)
+    return v
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_fused_and_two_pass_sweeps_agree(R, dtype):
+    """An unaligned theta runs the two-pass kernels; an aligned one the fused
+    kernel: same sweeps, same results up to rounding order."""
+    N, h = 128, 1.0
+    from paper_1709_06350_gb300 import synth
+    t0 = dev(synth.smooth_field(N, 31, 0.3, kmax=3), dtype)
+    g = dev(smooth_density(N, 32, 0.8), dtype)
+    a = t0.clone()
+    R.recon_step_sweep(a, g, 0.01, h, sweeps=2)
+    b = _offset_view(t0)
+    assert b.data_ptr() % (2 * b.element_size()) != 0
+    R.recon_step_sweep(b, g, 0.01, h, sweeps=2)
+    tol = 1e-5 if dtype == torch.float32 else 1e-13
+    assert rel_max(host(b), host(a)) < tol
+    # linear smoother
+    th = dev(synth.smooth_field(N, 33, 0.3, kmax=3), torch.float32)
+    f = dev(np.random.default_rng(34).standard_normal((N,) * 3), torch.float32)
+    e0 = torch.zeros_like(f)
+    ea = e0.clone()
+    R.recon_step_linear_sweep(ea, f, th, h, sweeps=2)
+    eb = _offset_view(e0)
+    R.recon_step_linear_sweep(eb, f, th, h, sweeps=2)
+    assert rel_max(host(eb), host(ea)) < 1e-5
 
 
 @pytest.mark.parametrize("N", [4, 12, 48])
