@@ -30,6 +30,40 @@ inline unsigned blocks_for(size_t work, int threads = kThreads)
     return (unsigned)((work + threads - 1) / threads);
 }
 
+// Grid of the grid-stride elementwise kernels: enough blocks to fill the
+// GPU, few enough that per-thread set-up (an FP64 scalar read and converted
+// once) is amortised over many elements.
+constexpr unsigned kMaxStrideBlocks = 4096;
+inline unsigned stride_blocks(size_t work)
+{
+    const unsigned b = blocks_for(work);
+    return b == 0 ? 1u : (b < kMaxStrideBlocks ? b : kMaxStrideBlocks);
+}
+
+// Per-thread sum of values of type T, returned as double.  For float the
+// sum is compensated (Kahan): GB300 runs FP64 at 1/64 of the FP32 rate, so
+// FP32 kernels accumulate in FP32 and widen once per thread.
+template <typename T>
+struct ThreadSum;
+template <>
+struct ThreadSum<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ double get() const { return s; }
+};
+template <>
+struct ThreadSum<float> {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float x)
+    {
+        const float y = x - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double get() const { return (double)s - (double)c; }
+};
+
 // Row-based launch shape of the grid kernels: 32 threads along k (or along
 // k-pairs), 8 rows (i, j) per block, a grid-stride loop over the N^2 rows.
 // Index arithmetic is a single 32-bit division per row.

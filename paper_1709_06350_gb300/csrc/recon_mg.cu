@@ -13,6 +13,7 @@
 // Launch shape of the grid kernels: blocks of 32 x 8 threads, 32 along k
 // (coalesced), 8 rows (i, j), grid-stride over the N^2 rows (FOR_ROWS).
 #include <chrono>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 
@@ -60,7 +61,7 @@ k_rb_pass(const T *__restrict__ src, T *__restrict__ dst, const T *__restrict__ 
 // ----------------------------------------------------------------------
 // Fused sweep: both colour passes in one kernel, src -> dst, with the same
 // snapshot semantics as two k_rb_pass launches.  A CTA owns a TJ x TK tile
-// of (j, k) and streams a chunk of planes along i through shared memory.
+// of (j, k) and streams a chunk of planes along i through shared memory:
 //
 //   OLD  ring of 6 planes of src, tile + 2-cell halo.  Each row is stored
 //        colour-split: the cells of even k first, then those of odd k, so
@@ -77,44 +78,43 @@ k_rb_pass(const T *__restrict__ src, T *__restrict__ dst, const T *__restrict__ 
 // theta read once more).  The linear variant (LIN) relaxes J e = f: the
 // staged unknown is e, g is f, and the cofactors of I + H theta at each
 // updated cell are formed from the staged theta.
-// Requires N >= kFusedMinN (so one wrap suffices for every halo index).
+//
+// Work split: warp w relaxes tile rows w and w+8 (black) and RED rows w,
+// w+8 (and w+16 for w < 2) at red index = lane; the last red cell of each
+// of the 18 RED rows goes to lanes 0..17 of warp 7.  Rows 8 apart share
+// their colour, so one set of shared-memory offsets serves all of a
+// thread's rows (the others are immediates), and the ring slots rotate in
+// registers.  Requires N >= kFusedMinN (one wrap suffices for every halo
+// index).
 // ----------------------------------------------------------------------
 constexpr int kTJ = 16, kTK = 64;
 constexpr int kOJ = kTJ + 4;                 // OLD rows
 constexpr int kOH = (kTK + 4) / 2;           // 34 cells of one k parity per OLD row
+constexpr int kOR = 2 * kOH;                 // OLD row stride
 constexpr int kRJ = kTJ + 2;                 // RED rows
 constexpr int kRH = (kTK + 2) / 2;           // 33 red cells per RED row
 constexpr int kFT = 256;                     // threads per CTA
-constexpr int kOElem = kOJ * 2 * kOH;        // 1360 elements per OLD plane
-constexpr int kLoadsPerThread = (kOElem + kFT - 1) / kFT;   // 6
+constexpr int kWarps = kFT / 32;
+constexpr int kOPlane = kOJ * kOR;           // 1360 elements per OLD / TH plane
+constexpr int kRPlane = kRJ * kRH;           // 594 elements per RED plane
+constexpr int kLoadsPerThread = (kOPlane + kFT - 1) / kFT;   // 6
 constexpr int kOSlots = 6, kRSlots = 4;
-constexpr int kRowItems = kTK / 2;           // 32: one warp per row
-constexpr int kRedMain = kRJ * kRowItems;    // 576 red cells with index < 32
-constexpr int kRedItems = kRJ * kRH;         // 594 (+ the 18 cells of index 32)
-constexpr int kBlackItems = kTJ * kRowItems; // 512
-static_assert(kRowItems == 32 && kRH == kRowItems + 1, "one warp per tile row");
-
-template <typename T>
-using OldPlane = T[kOJ][2][kOH];
+constexpr int kRedBase = kOSlots * kOPlane;  // RED ring after the OLD ring
+constexpr int kThBase = kRedBase + kRSlots * kRPlane;        // TH ring after RED
+static_assert(kTK / 2 == 32 && kRH == 33 && kWarps == 8 && kTJ == 2 * kWarps,
+              "warp w owns tile rows w and w + 8 and red index = lane");
+static_assert(kRJ - 2 * kWarps == 2, "RED rows 16 and 17 go to warps 0 and 1");
 
 template <typename T, bool LIN>
-struct FusedSmem;
-template <typename T>
-struct FusedSmem<T, false> {
-    OldPlane<T> old_[kOSlots];
-    T red_[kRSlots][kRJ][kRH];
-};
-template <typename T>
-struct FusedSmem<T, true> {
-    OldPlane<T> old_[kOSlots];
-    T red_[kRSlots][kRJ][kRH];
-    OldPlane<T> th_[kOSlots];
-};
+constexpr size_t fused_smem_bytes()
+{
+    return sizeof(T) * (size_t)(kThBase + (LIN ? kOSlots * kOPlane : 0));
+}
 
 __device__ __forceinline__ int wrap1(int x, int N) { return x < 0 ? x + N : (x >= N ? x - N : x); }
 
 // Colour-split position of cell (i, j, k) in a per-cell operand array of the
-// linear smoother on the coarse (unfused) levels: within each row (i, j) the
+// linear smoother on the two-pass (unfused) path: within each row (i, j) the
 // N/2 cells of colour (i+j+k) % 2 == 0 come first, then the N/2 others, each
 // in k order, so the cells one colour pass updates are contiguous.
 __host__ __device__ __forceinline__ unsigned cof_slot(int N, int i, int j, int k)
@@ -137,35 +137,33 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int K>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(K)); }
 
-// 19-point neighbourhood from three colour-split planes (m, c, p) for the cell
-// in row r whose k parity is po: a is its index within its parity half, bp and
-// bm the indices of its k+1 and k-1 neighbours within the other half.
+// 19-point neighbourhood of a cell from three colour-split planes at
+// element offsets pm, pc, pp of the shared buffer sm.  S: the cell's offset
+// within a plane (its own parity half); O: the offset of its k-1 neighbour
+// (other half), k+1 being O + 1.
 template <typename T>
-__device__ __forceinline__ Nb19<T> nb_split(const OldPlane<T> &pm, const OldPlane<T> &pc,
-                                            const OldPlane<T> &pp, int r, int po, int a, int bp,
-                                            int bm)
+__device__ __forceinline__ Nb19<T> gather19(const T *sm, int pm, int pc, int pp, int S, int O)
 {
-    const int qo = po ^ 1;
     Nb19<T> v;
-    v.c = pc[r][po][a];
-    v.xp = pp[r][po][a];
-    v.xm = pm[r][po][a];
-    v.yp = pc[r + 1][po][a];
-    v.ym = pc[r - 1][po][a];
-    v.zp = pc[r][qo][bp];
-    v.zm = pc[r][qo][bm];
-    v.xpyp = pp[r + 1][po][a];
-    v.xmym = pm[r - 1][po][a];
-    v.xmyp = pm[r + 1][po][a];
-    v.xpym = pp[r - 1][po][a];
-    v.ypzp = pc[r + 1][qo][bp];
-    v.ymzm = pc[r - 1][qo][bm];
-    v.ymzp = pc[r - 1][qo][bp];
-    v.ypzm = pc[r + 1][qo][bm];
-    v.xpzp = pp[r][qo][bp];
-    v.xmzm = pm[r][qo][bm];
-    v.xmzp = pm[r][qo][bp];
-    v.xpzm = pp[r][qo][bm];
+    v.c = sm[pc + S];
+    v.xp = sm[pp + S];
+    v.xm = sm[pm + S];
+    v.yp = sm[pc + S + kOR];
+    v.ym = sm[pc + S - kOR];
+    v.zp = sm[pc + O + 1];
+    v.zm = sm[pc + O];
+    v.xpyp = sm[pp + S + kOR];
+    v.xmym = sm[pm + S - kOR];
+    v.xmyp = sm[pm + S + kOR];
+    v.xpym = sm[pp + S - kOR];
+    v.ypzp = sm[pc + O + kOR + 1];
+    v.ymzm = sm[pc + O - kOR];
+    v.ymzp = sm[pc + O - kOR + 1];
+    v.ypzm = sm[pc + O + kOR];
+    v.xpzp = sm[pp + O + 1];
+    v.xmzm = sm[pm + O];
+    v.xmzp = sm[pm + O + 1];
+    v.xpzm = sm[pp + O];
     return v;
 }
 
@@ -200,99 +198,121 @@ k_sweep_fused(const T *__restrict__ src, T *__restrict__ dst, const T *__restric
               int CI, T ih2, T h2_6, int rule)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    FusedSmem<T, LIN> &S = *reinterpret_cast<FusedSmem<T, LIN> *>(smem_raw);
+    T *sm = reinterpret_cast<T *>(smem_raw);
     const T c = LIN ? T(0) : (T)(cptr ? *cptr : cval);
     const int k0 = blockIdx.x * kTK, j0 = blockIdx.y * kTJ, i0 = blockIdx.z * CI;
     const int i1 = min(i0 + CI, N);
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const unsigned NN = (unsigned)N * (unsigned)N;
 
-    // this thread's OLD elements: in-plane global offset and colour-split
-    // position within a plane (the same for every plane)
+    // this thread's share of a plane copy: in-plane global offset and
+    // colour-split offset within the plane (the same for every plane)
     unsigned goff[kLoadsPerThread];
     int soff[kLoadsPerThread];
 #pragma unroll
     for (int t = 0; t < kLoadsPerThread; ++t) {
         const int e = tid + t * kFT;
-        const int r = e / (2 * kOH), q = e - r * (2 * kOH);
-        soff[t] = e < kOElem ? (2 * r + (q & 1)) * kOH + (q >> 1) : -1;
+        const int r = e / kOR, q = e - r * kOR;
+        soff[t] = e < kOPlane ? r * kOR + (q & 1) * kOH + (q >> 1) : -1;
         goff[t] = (unsigned)wrap1(j0 - 2 + (r < kOJ ? r : 0), N) * (unsigned)N +
                   (unsigned)wrap1(k0 - 2 + q, N);
     }
-    // plane p lives in OLD/TH slot (p - i0 + 2) % 6 and RED slot (p - i0 + 1) % 4
-    auto oslot = [&](int p) { return (p - i0 + 2) % kOSlots; };
-    auto rslot = [&](int p) { return (p - i0 + 1) % kRSlots; };
-    auto issue_plane = [&](int p) {
+    auto issue_plane = [&](int slot, int p) {   // slot: element offset of an OLD plane
         const unsigned pb = (unsigned)wrap1(p, N) * NN;
-        T *so = &S.old_[oslot(p)][0][0][0];
 #pragma unroll
         for (int t = 0; t < kLoadsPerThread; ++t)
-            if (soff[t] >= 0) cp_async_elem(so + soff[t], src + pb + goff[t]);
+            if (soff[t] >= 0) cp_async_elem(sm + slot + soff[t], src + pb + goff[t]);
         if constexpr (LIN) {
-            T *st = &S.th_[oslot(p)][0][0][0];
 #pragma unroll
             for (int t = 0; t < kLoadsPerThread; ++t)
-                if (soff[t] >= 0) cp_async_elem(st + soff[t], th + pb + goff[t]);
+                if (soff[t] >= 0) cp_async_elem(sm + kThBase + slot + soff[t], th + pb + goff[t]);
         }
         cp_async_commit();
     };
-    // red cells of plane p on the tile + 1 halo.  Item -> (RED row r, red
-    // index h): one warp per row for h < 32, then h = 32 of every row.  The
-    // red cell sits at RED column 2h + pr, i.e. OLD row r+1, parity pr ^ 1,
-    // same-parity index h + pr, k-neighbours at other-parity indices h, h+1.
-    auto red_plane = [&](int p) {
-        const int pw = wrap1(p, N);
-        const unsigned pb = (unsigned)pw * NN;
-        const OldPlane<T> &om = S.old_[oslot(p - 1)], &oc = S.old_[oslot(p)], &op = S.old_[oslot(p + 1)];
-        T(*R)[kRH] = S.red_[rslot(p)];
-        for (int e = tid; e < kRedItems; e += kFT) {
-            const int r = e < kRedMain ? e / kRowItems : e - kRedMain;
-            const int h = e < kRedMain ? e % kRowItems : kRowItems;
-            const int pr = (p + j0 + r) & 1;
-            const Nb19<T> nb = nb_split<T>(om, oc, op, r + 1, pr ^ 1, h + pr, h + 1, h);
-            const unsigned go = pb + (unsigned)wrap1(j0 - 1 + r, N) * (unsigned)N +
-                                (unsigned)wrap1(k0 - 1 + 2 * h + pr, N);
+
+    // global offsets of this thread's red cells within a plane: RED rows
+    // w + 8i (row j0 - 1 + w + 8i), red index lane (column k0 - 1 + 2 lane + pr)
+    unsigned grow[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) grow[i] = (unsigned)wrap1(j0 - 1 + w + 8 * i, N) * (unsigned)N;
+    const unsigned gcol0 = (unsigned)wrap1(k0 - 1 + 2 * lane, N);
+    const unsigned gcol1 = (unsigned)wrap1(k0 + 2 * lane, N);
+    // the last red cell (index 32) of RED row `lane`, for lanes 0..17 of warp 7
+    const bool colw = w == kWarps - 1 && lane < kRJ;
+    const unsigned crow = (unsigned)wrap1(j0 - 1 + (colw ? lane : 0), N) * (unsigned)N;
+    const unsigned ccol0 = (unsigned)wrap1(k0 + kTK - 1, N), ccol1 = (unsigned)wrap1(k0 + kTK, N);
+
+    // red cells of plane p on the tile + 1 halo into the RED plane at rs;
+    // om, oc, op: OLD planes p-1, p, p+1.  A red cell at RED row r, index h
+    // sits at RED column 2h + pr: OLD row r+1, parity pr ^ 1, same-parity
+    // index h + pr, k-1 neighbour at other-parity index h.
+    auto red_plane = [&](int p, int om, int oc, int op, int rs) {
+        const unsigned pb = (unsigned)wrap1(p, N) * NN;
+        const int pr = (p + j0 + w) & 1;   // rows w + 8i share it
+        const int S0 = (w + 1) * kOR + (pr ^ 1) * kOH + lane + pr;
+        const int O0 = (w + 1) * kOR + pr * kOH + lane;
+        const unsigned gc = pb + (pr ? gcol1 : gcol0);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            if (i == 2 && w >= kRJ - 2 * kWarps) break;
+            const int S = S0 + 8 * i * kOR, O = O0 + 8 * i * kOR;
+            const Nb19<T> nb = gather19<T>(sm, om, oc, op, S, O);
+            const T rhs = g[gc + grow[i]];
+            T v;
             if constexpr (LIN) {
-                const Nb19<T> nt = nb_split<T>(S.th_[oslot(p - 1)], S.th_[oslot(p)], S.th_[oslot(p + 1)],
-                                               r + 1, pr ^ 1, h + pr, h + 1, h);
-                R[r][h] = lin_update<T>(nt, nb, g[go], ih2);
+                v = lin_update<T>(gather19<T>(sm + kThBase, om, oc, op, S, O), nb, rhs, ih2);
             } else {
-                R[r][h] = fas_update<T>(nb, g[go] + c, ih2, h2_6, rule);
+                v = fas_update<T>(nb, rhs + c, ih2, h2_6, rule);
             }
+            sm[rs + (w + 8 * i) * kRH + lane] = v;
+        }
+        if (colw) {
+            const int r = lane, prc = (p + j0 + r) & 1, h = kRH - 1;
+            const int S = (r + 1) * kOR + (prc ^ 1) * kOH + h + prc;
+            const int O = (r + 1) * kOR + prc * kOH + h;
+            const Nb19<T> nb = gather19<T>(sm, om, oc, op, S, O);
+            const T rhs = g[pb + crow + (prc ? ccol1 : ccol0)];
+            T v;
+            if constexpr (LIN) {
+                v = lin_update<T>(gather19<T>(sm + kThBase, om, oc, op, S, O), nb, rhs, ih2);
+            } else {
+                v = fas_update<T>(nb, rhs + c, ih2, h2_6, rule);
+            }
+            sm[rs + r * kRH + h] = v;
         }
     };
-    // black cells of plane s on the tile, written with their red partners as
-    // (even k, odd k) pairs.  Item -> (tile row r, pair m); the black cell is
-    // at tile column 2m + pb: OLD row r+2, parity pb, index m+1; its red
-    // faces at RED row r+1, index m + pb (x, y) and m, m+1 (z).
-    auto black_plane = [&](int s) {
-        const OldPlane<T> &om = S.old_[oslot(s - 1)], &oc = S.old_[oslot(s)], &op = S.old_[oslot(s + 1)];
-        const T(*Rm)[kRH] = S.red_[rslot(s - 1)];
-        const T(*Rc)[kRH] = S.red_[rslot(s)];
-        const T(*Rp)[kRH] = S.red_[rslot(s + 1)];
-        const unsigned pb0 = (unsigned)s * NN;
-        for (int e = tid; e < kBlackItems; e += kFT) {
-            const int r = e / kRowItems, m = e % kRowItems;
-            const int gj = j0 + r, gk0 = k0 + 2 * m;
+    // black cells of plane s on the tile rows w, w + 8, written with their red
+    // partners as (even k, odd k) pairs; pair m = lane.  The black cell is at
+    // tile column 2m + pb: OLD row r+2, parity pb, index m+1, k-1 neighbour at
+    // other-parity index m + pb; its red faces at RED row r+1, index m + pb
+    // (x, y) and m, m+1 (z).  rm, rc, rp: RED planes s-1, s, s+1.
+    auto black_plane = [&](int s, int om, int oc, int op, int rm, int rc, int rp) {
+        const int pb = (s + j0 + w + 1) & 1;
+        const int S0 = (w + 2) * kOR + pb * kOH + lane + 1;
+        const int O0 = (w + 2) * kOR + (pb ^ 1) * kOH + lane + pb;
+        const int Q0 = (w + 1) * kRH + lane;
+        const unsigned sb = (unsigned)s * NN;
+        const int gk0 = k0 + 2 * lane;
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int gj = j0 + w + 8 * i;
             if (gj >= N || gk0 >= N) continue;
-            const int pb = (s + j0 + r + 1) & 1;
-            Nb19<T> nb = nb_split<T>(om, oc, op, r + 2, pb, m + 1, m + 1 + pb, m + pb);
-            nb.xp = Rp[r + 1][m + pb];
-            nb.xm = Rm[r + 1][m + pb];
-            nb.yp = Rc[r + 2][m + pb];
-            nb.ym = Rc[r][m + pb];
-            nb.zp = Rc[r + 1][m + 1];
-            nb.zm = Rc[r + 1][m];
-            const unsigned gb = pb0 + (unsigned)gj * (unsigned)N + (unsigned)gk0;
+            const int S = S0 + 8 * i * kOR, O = O0 + 8 * i * kOR, Q = Q0 + 8 * i * kRH;
+            Nb19<T> nb = gather19<T>(sm, om, oc, op, S, O);
+            nb.xp = sm[rp + Q + pb];
+            nb.xm = sm[rm + Q + pb];
+            nb.yp = sm[rc + Q + kRH + pb];
+            nb.ym = sm[rc + Q - kRH + pb];
+            nb.zp = sm[rc + Q + 1];
+            nb.zm = sm[rc + Q];
+            const unsigned gb = sb + (unsigned)gj * (unsigned)N + (unsigned)gk0;
             T vb;
             if constexpr (LIN) {
-                const Nb19<T> nt = nb_split<T>(S.th_[oslot(s - 1)], S.th_[oslot(s)], S.th_[oslot(s + 1)],
-                                               r + 2, pb, m + 1, m + 1 + pb, m + pb);
-                vb = lin_update<T>(nt, nb, g[gb + pb], ih2);
+                vb = lin_update<T>(gather19<T>(sm + kThBase, om, oc, op, S, O), nb, g[gb + pb], ih2);
             } else {
                 vb = fas_update<T>(nb, g[gb + pb] + c, ih2, h2_6, rule);
             }
-            const T vr = Rc[r + 1][m + 1 - pb];
+            const T vr = sm[rc + Q + 1 - pb];
             typename Pair<T>::type v;
             v.x = pb ? vr : vb;
             v.y = pb ? vb : vr;
@@ -300,22 +320,37 @@ k_sweep_fused(const T *__restrict__ src, T *__restrict__ dst, const T *__restric
         }
     };
 
-    // prologue: OLD planes i0-2 .. i0+2, then RED planes i0-1 .. i0+1 while
-    // plane i0+3 arrives.  RED planes i0-1 .. i1 and OLD planes i0-2 .. i1+1
-    // are the ones the chunk needs.
-    for (int p = i0 - 2; p <= i0 + 2; ++p) issue_plane(p);
+    // prologue: OLD planes i0-2 .. i0+2 into slots 0..4, then RED planes
+    // i0-1 .. i0+1 into RED slots 0..2 while plane i0+3 arrives in slot 5.
+    // The chunk needs OLD planes i0-2 .. i1+1 and RED planes i0-1 .. i1.
+    for (int d = 0; d < 5; ++d) issue_plane(d * kOPlane, i0 - 2 + d);
     cp_async_wait<0>();
     __syncthreads();
-    if (i0 + 3 <= i1 + 1) issue_plane(i0 + 3);
-    red_plane(i0 - 1);
-    red_plane(i0);
-    red_plane(i0 + 1);
+    if (i0 + 3 <= i1 + 1) issue_plane(5 * kOPlane, i0 + 3);
+    red_plane(i0 - 1, 0 * kOPlane, 1 * kOPlane, 2 * kOPlane, kRedBase + 0 * kRPlane);
+    red_plane(i0, 1 * kOPlane, 2 * kOPlane, 3 * kOPlane, kRedBase + 1 * kRPlane);
+    red_plane(i0 + 1, 2 * kOPlane, 3 * kOPlane, 4 * kOPlane, kRedBase + 2 * kRPlane);
+    // ring slots of OLD planes s-1 .. s+4 and RED planes s-1 .. s+2
+    int o0 = 1 * kOPlane, o1 = 2 * kOPlane, o2 = 3 * kOPlane, o3 = 4 * kOPlane, o4 = 5 * kOPlane, o5 = 0;
+    int q0 = kRedBase, q1 = kRedBase + kRPlane, q2 = kRedBase + 2 * kRPlane, q3 = kRedBase + 3 * kRPlane;
     for (int s = i0; s < i1; ++s) {
         cp_async_wait<0>();   // this thread's copies of plane s+3 have landed
-        __syncthreads();      // everyone's; RED s+1 written; slots of plane s-2 free
-        if (s + 4 <= i1 + 1) issue_plane(s + 4);
-        if (s + 2 <= i1) red_plane(s + 2);
-        black_plane(s);
+        __syncthreads();      // everyone's; RED s+1 written; slots of planes s-2 free
+        if (s + 4 <= i1 + 1) issue_plane(o5, s + 4);
+        if (s + 2 <= i1) red_plane(s + 2, o2, o3, o4, q3);
+        black_plane(s, o0, o1, o2, q0, q1, q2);
+        const int to = o0;
+        o0 = o1;
+        o1 = o2;
+        o2 = o3;
+        o3 = o4;
+        o4 = o5;
+        o5 = to;
+        const int tq = q0;
+        q0 = q1;
+        q1 = q2;
+        q2 = q3;
+        q3 = tq;
     }
     cp_async_wait<0>();
 }
@@ -324,7 +359,7 @@ template <typename T, bool LIN>
 static cudaError_t fused_attr()
 {
     return cudaFuncSetAttribute(k_sweep_fused<T, LIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sizeof(FusedSmem<T, LIN>));
+                                (int)fused_smem_bytes<T, LIN>());
 }
 
 static bool g_kernels_ready = false;
@@ -359,7 +394,7 @@ static cudaError_t fused_sweep_launch(int N, const T *src, T *dst, const T *g, c
 {
     // set once per process (recon_create does it before any graph capture;
     // step entry points may run without a handle)
-    const size_t smem = sizeof(FusedSmem<T, LIN>);
+    const size_t smem = fused_smem_bytes<T, LIN>();
     if (!g_kernels_ready) {
         const cudaError_t e = prepare_kernels();
         if (e != cudaSuccess) return e;
@@ -433,25 +468,25 @@ k_residual_norms(const T *__restrict__ t, const T *__restrict__ g,
 {
     __shared__ double sh[32];
     const T c = (T)(*cptr);
-    double sr = 0.0, sr2 = 0.0, st = 0.0;
+    ThreadSum<T> sr, sr2, st;
     FOR_ROWS(N, i, j)
     for (int k = threadIdx.x; k < N; k += kRowX) {
         const unsigned id = offs(N, i, j, k);
         const Nb19<T> nb = load19<T>(t, N, i, j, k);
         const T res = (g[id] + c) - det_IH(nb, ih2);
-        sr += (double)res;
-        sr2 += (double)res * (double)res;
-        st += (double)nb.c;
+        sr.add(res);
+        sr2.add(res * res);
+        st.add(nb.c);
         if (f32out) {
             f32out[id] = (float)res;
             t32out[id] = (float)nb.c;
         }
     }
-    double v = block_sum<kRowThreads>(sr, sh);
+    double v = block_sum<kRowThreads>(sr.get(), sh);
     if (ltid() == 0) partials[4 * blockIdx.x + 0] = v;
-    v = block_sum<kRowThreads>(sr2, sh);
+    v = block_sum<kRowThreads>(sr2.get(), sh);
     if (ltid() == 0) partials[4 * blockIdx.x + 1] = v;
-    v = block_sum<kRowThreads>(st, sh);
+    v = block_sum<kRowThreads>(st.get(), sh);
     if (ltid() == 0) partials[4 * blockIdx.x + 2] = v;
 }
 
@@ -486,8 +521,10 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_gauge(T *__restrict__ t, size_t n, const double *__restrict__ scal)
 {
-    const size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (id < n) t[id] -= (T)scal[S_MEAN_T];
+    const T m = (T)scal[S_MEAN_T];
+    for (size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x; id < n;
+         id += (size_t)gridDim.x * blockDim.x)
+        t[id] -= m;
 }
 
 // ======================================================================
@@ -496,8 +533,129 @@ k_gauge(T *__restrict__ t, size_t n, const double *__restrict__ scal)
 // Fused residual + restriction: per coarse cell, the 8 sons' residuals
 // r = g + c - det(I + H theta) and values are averaged (Sec. II.A.3: coarse
 // value = mean of the 8 son cells); the fine residual is never stored.
+// Fine windows of the restrictions.  Every 19-point stencil of the eight
+// children (2I+a, 2J+b, 2K+c) of coarse cell (I, J, K) lies in the fine block
+// i, j, k in 2I-1 .. 2I+2 (etc.) without the corners of its two outer
+// planes: 56 loads instead of 8 x 19.  Window index 1 + a is child a.
+struct Win {
+    unsigned pl[4], row[4], col[4];
+    __device__ __forceinline__ Win(int Nf, int I, int J, int K)
+    {
+        const unsigned nn = (unsigned)Nf * (unsigned)Nf;
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+            pl[d] = (unsigned)wrap1(2 * I - 1 + d, Nf) * nn;
+            row[d] = (unsigned)wrap1(2 * J - 1 + d, Nf) * (unsigned)Nf;
+            col[d] = (unsigned)wrap1(2 * K - 1 + d, Nf);
+        }
+    }
+    __device__ __forceinline__ unsigned at(int d, int b, int c) const { return pl[d] + row[b] + col[c]; }
+};
+
+// window plane d of array a; the corners are loaded only for inner planes
+template <typename T, bool INNER>
+__device__ __forceinline__ void win_plane(const T *__restrict__ a, const Win &w, int d, T (&P)[4][4])
+{
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            P[b][c] = (!INNER && (b == 0 || b == 3) && (c == 0 || c == 3)) ? T(0) : a[w.at(d, b, c)];
+}
+
+// 19-point neighbourhood of the child at window (b, c) of the middle plane
 template <typename T>
-__global__ void __launch_bounds__(kRowThreads)
+__device__ __forceinline__ Nb19<T> win_nb(const T (&Pm)[4][4], const T (&Pc)[4][4], const T (&Pp)[4][4],
+                                          int b, int c)
+{
+    Nb19<T> v;
+    v.c = Pc[b][c];
+    v.xp = Pp[b][c];
+    v.xm = Pm[b][c];
+    v.yp = Pc[b + 1][c];
+    v.ym = Pc[b - 1][c];
+    v.zp = Pc[b][c + 1];
+    v.zm = Pc[b][c - 1];
+    v.xpyp = Pp[b + 1][c];
+    v.xmym = Pm[b - 1][c];
+    v.xmyp = Pm[b + 1][c];
+    v.xpym = Pp[b - 1][c];
+    v.ypzp = Pc[b + 1][c + 1];
+    v.ymzm = Pc[b - 1][c - 1];
+    v.ymzp = Pc[b - 1][c + 1];
+    v.ypzm = Pc[b + 1][c - 1];
+    v.xpzp = Pp[b][c + 1];
+    v.xmzm = Pm[b][c - 1];
+    v.xmzp = Pm[b][c + 1];
+    v.xpzm = Pp[b][c - 1];
+    return v;
+}
+
+// Residual norms of an even grid from the fine windows of its 2 x 2 x 2
+// blocks (7 loads per cell instead of 19); same outputs as k_residual_norms.
+template <typename T>
+__global__ void __launch_bounds__(kRowThreads, 2)
+k_residual_norms_win(const T *__restrict__ t, const T *__restrict__ g,
+                     const double *__restrict__ cptr, int N, T ih2, double *__restrict__ partials,
+                     float *__restrict__ f32out, float *__restrict__ t32out)
+{
+    __shared__ double sh[32];
+    const T c = (T)(*cptr);
+    const int Nc = N >> 1;
+    ThreadSum<T> sr, sr2, st;
+    FOR_ROWS(Nc, I, J)
+    for (int K = threadIdx.x; K < Nc; K += kRowX) {
+        const Win w(N, I, J, K);
+        T P0[4][4], P1[4][4], P2[4][4];
+        win_plane<T, false>(t, w, 0, P0);
+        win_plane<T, true>(t, w, 1, P1);
+        win_plane<T, true>(t, w, 2, P2);
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            if (a == 1) win_plane<T, false>(t, w, 3, P0);
+#pragma unroll
+            for (int b = 1; b <= 2; ++b)
+#pragma unroll
+                for (int cc = 1; cc <= 2; ++cc) {
+                    const Nb19<T> nb = a == 0 ? win_nb<T>(P0, P1, P2, b, cc) : win_nb<T>(P1, P2, P0, b, cc);
+                    const unsigned id = w.at(1 + a, b, cc);
+                    const T res = (g[id] + c) - det_IH(nb, ih2);
+                    sr.add(res);
+                    sr2.add(res * res);
+                    st.add(nb.c);
+                    if (f32out) {
+                        f32out[id] = (float)res;
+                        t32out[id] = (float)nb.c;
+                    }
+                }
+        }
+    }
+    double v = block_sum<kRowThreads>(sr.get(), sh);
+    if (ltid() == 0) partials[4 * blockIdx.x + 0] = v;
+    v = block_sum<kRowThreads>(sr2.get(), sh);
+    if (ltid() == 0) partials[4 * blockIdx.x + 1] = v;
+    v = block_sum<kRowThreads>(st.get(), sh);
+    if (ltid() == 0) partials[4 * blockIdx.x + 2] = v;
+}
+
+// Residual norms on any grid: the windowed kernel for even N >= 32
+template <typename T>
+static unsigned launch_residual_norms(const T *t, const T *g, const double *cptr, int N, T ih2,
+                                      double *partials, float *f32out, float *t32out, cudaStream_t s)
+{
+    note_launch();
+    if (N % 2 == 0 && N >= 32) {
+        const unsigned nbr = row_grid(N / 2, kMaxRedBlocks);
+        k_residual_norms_win<T><<<nbr, row_block(), 0, s>>>(t, g, cptr, N, ih2, partials, f32out, t32out);
+        return nbr;
+    }
+    const unsigned nbr = row_grid(N, kMaxRedBlocks);
+    k_residual_norms<T><<<nbr, row_block(), 0, s>>>(t, g, cptr, N, ih2, partials, f32out, t32out);
+    return nbr;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kRowThreads, 2)
 k_restrict_residual(const T *__restrict__ t, const T *__restrict__ g,
                     const double *__restrict__ cptr, int Nf, T ih2, T *__restrict__ tH,
                     T *__restrict__ toldH, T *__restrict__ rrH, double *__restrict__ partials)
@@ -505,26 +663,40 @@ k_restrict_residual(const T *__restrict__ t, const T *__restrict__ g,
     __shared__ double sh[32];
     const int Nc = Nf >> 1;
     const T c = (T)(*cptr);
-    double srr = 0.0;
+    ThreadSum<T> srr;
     FOR_ROWS(Nc, I, J)
     for (int K = threadIdx.x; K < Nc; K += kRowX) {
+        const Win w(Nf, I, J, K);
+        T P0[4][4], P1[4][4], P2[4][4];
+        win_plane<T, false>(t, w, 0, P0);
+        win_plane<T, true>(t, w, 1, P1);
+        win_plane<T, true>(t, w, 2, P2);
         T at = T(0), ar = T(0);
-        for (int a = 0; a < 2; ++a)
-            for (int b = 0; b < 2; ++b)
-                for (int cc = 0; cc < 2; ++cc) {
-                    const int i = 2 * I + a, j = 2 * J + b, k = 2 * K + cc;
-                    const Nb19<T> nb = load19<T>(t, Nf, i, j, k);
-                    at += nb.c;
-                    ar += (g[offs(Nf, i, j, k)] + c) - det_IH(nb, ih2);
-                }
+#pragma unroll
+        for (int b = 1; b <= 2; ++b)
+#pragma unroll
+            for (int cc = 1; cc <= 2; ++cc) {   // children in fine plane 2I: window planes 0..2
+                const Nb19<T> nb = win_nb<T>(P0, P1, P2, b, cc);
+                at += nb.c;
+                ar += (g[w.at(1, b, cc)] + c) - det_IH(nb, ih2);
+            }
+        win_plane<T, false>(t, w, 3, P0);   // children in fine plane 2I+1: planes 1..3
+#pragma unroll
+        for (int b = 1; b <= 2; ++b)
+#pragma unroll
+            for (int cc = 1; cc <= 2; ++cc) {
+                const Nb19<T> nb = win_nb<T>(P1, P2, P0, b, cc);
+                at += nb.c;
+                ar += (g[w.at(2, b, cc)] + c) - det_IH(nb, ih2);
+            }
         const T vt = at * T(0.125), vr = ar * T(0.125);
         const unsigned id = offs(Nc, I, J, K);
         tH[id] = vt;
         toldH[id] = vt;
         rrH[id] = vr;
-        srr += (double)vr;
+        srr.add(vr);
     }
-    const double v = block_sum<kRowThreads>(srr, sh);
+    const double v = block_sum<kRowThreads>(srr.get(), sh);
     if (ltid() == 0) partials[4 * blockIdx.x + 0] = v;
 }
 
@@ -572,7 +744,8 @@ k_coarse_rhs(const T *__restrict__ tH, T *__restrict__ gH, T *__restrict__ dH,
 {
     __shared__ double sh[32];
     const T m = (T)(*mean_ptr);
-    double mn = INFINITY;
+    const T fl = (T)floor_;
+    T mn = T(INFINITY);
     FOR_ROWS(Nc, I, J)
     for (int K = threadIdx.x; K < Nc; K += kRowX) {
         const unsigned id = offs(Nc, I, J, K);
@@ -581,11 +754,11 @@ k_coarse_rhs(const T *__restrict__ tH, T *__restrict__ gH, T *__restrict__ dH,
         gH[id] = rr;
         dH[id] = d;
         if (rr < T(0)) {
-            const double cand = floor_ * (double)(d > T(0) ? d : T(0)) / (double)(-rr);
-            mn = fmin(mn, cand);
+            const T cand = fl * (d > T(0) ? d : T(0)) / (-rr);
+            mn = cand < mn ? cand : mn;
         }
     }
-    const double v = block_min<kRowThreads>(mn, sh);
+    const double v = block_min<kRowThreads>((double)mn, sh);
     if (ltid() == 0) partials[4 * blockIdx.x + 3] = v;
 }
 
@@ -611,8 +784,10 @@ __global__ void __launch_bounds__(kThreads)
 k_form_rhs(T *__restrict__ gH, const T *__restrict__ dH, size_t nc,
            const double *__restrict__ sslot)
 {
-    const size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (id < nc) gH[id] = dH[id] + (T)(*sslot) * gH[id];
+    const T sc = (T)(*sslot);
+    for (size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x; id < nc;
+         id += (size_t)gridDim.x * blockDim.x)
+        gH[id] = dH[id] + sc * gH[id];
 }
 
 // fine += scale * P(cnew - cold), P cell-centred trilinear: per axis the
@@ -792,21 +967,31 @@ cudaError_t det_write(int N, double h, const double *t, double *out, cudaStream_
 __global__ void __launch_bounds__(kThreads)
 k_b_stats(const double *__restrict__ b, size_t n, double *__restrict__ partials)
 {
+    // finiteness and the minimum on the bit patterns (integer pipes); the
+    // norm from the FP64 difference b - 1 widened once per thread.
     __shared__ double sh[32];
-    double s2 = 0.0, mn = INFINITY, bad = 0.0;
+    ThreadSum<float> s2;
+    long long kmin = LLONG_MAX;   // order-preserving key of the smallest finite b
+    unsigned bad = 0;
     for (size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x; id < n;
          id += (size_t)gridDim.x * blockDim.x) {
         const double v = b[id];
-        if (!isfinite(v)) bad += 1.0;
-        else {
-            s2 += (v - 1.0) * (v - 1.0);
-            mn = fmin(mn, v);
+        const long long bits = __double_as_longlong(v);
+        if (((bits >> 52) & 0x7ff) == 0x7ff) {
+            ++bad;
+        } else {
+            const long long key = bits < 0 ? (bits ^ LLONG_MAX) : bits;
+            kmin = key < kmin ? key : kmin;
+            const float d = (float)(v - 1.0);
+            s2.add(d * d);
         }
     }
-    double v = block_sum<kThreads>(s2, sh);
+    double v = block_sum<kThreads>(s2.get(), sh);
     if (ltid() == 0) partials[4 * blockIdx.x + 0] = v;
-    v = block_sum<kThreads>(bad, sh);
+    v = block_sum<kThreads>((double)bad, sh);
     if (ltid() == 0) partials[4 * blockIdx.x + 1] = v;
+    const double mn = kmin == LLONG_MAX ? INFINITY
+                                        : __longlong_as_double(kmin < 0 ? (kmin ^ LLONG_MAX) : kmin);
     v = block_min<kThreads>(mn, sh);
     if (ltid() == 0) partials[4 * blockIdx.x + 3] = v;
 }
@@ -856,8 +1041,10 @@ k_update_theta(double *__restrict__ t, const float *__restrict__ e, size_t n,
 __global__ void __launch_bounds__(kThreads)
 k_sub_scalar(float *__restrict__ a, size_t n, const double *__restrict__ v)
 {
-    const size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (id < n) a[id] -= (float)(*v);
+    const float m = (float)(*v);
+    for (size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x; id < n;
+         id += (size_t)gridDim.x * blockDim.x)
+        a[id] -= m;
 }
 
 // ---- double-float fine-grid residual of the mixed path
@@ -1057,9 +1244,11 @@ cudaError_t linear_sweep(int N, double h, float *e, const float *f, const float 
     return lin_sweep(N, h, e, f, cof, th, sweeps, work, s);
 }
 
-// fH = R (f - J e), block partial sums for the mean projection.  The
-// cofactors come from cof (colour-split arrays) or, when cof is null, from th.
-__global__ void __launch_bounds__(kRowThreads)
+// fH = R (f - J e), block partial sums for the mean projection, from the
+// fine windows of e and (FROM_TH) theta; otherwise the cofactors come from
+// the colour-split arrays cof.
+template <bool FROM_TH>
+__global__ void __launch_bounds__(kRowThreads, 2)
 k_lin_restrict_residual(const float *__restrict__ e, const float *__restrict__ f,
                         const float *__restrict__ cof, const float *__restrict__ th, int Nf,
                         float ih2, float *__restrict__ fH, double *__restrict__ partials)
@@ -1067,23 +1256,45 @@ k_lin_restrict_residual(const float *__restrict__ e, const float *__restrict__ f
     __shared__ double sh[32];
     const size_t nf = (size_t)Nf * Nf * Nf;
     const int Nc = Nf >> 1;
-    double sacc = 0.0;
+    ThreadSum<float> sacc;
     FOR_ROWS(Nc, I, J)
     for (int K = threadIdx.x; K < Nc; K += kRowX) {
+        const Win w(Nf, I, J, K);
+        float E0[4][4], E1[4][4], E2[4][4], T0[4][4], T1[4][4], T2[4][4];
+        win_plane<float, false>(e, w, 0, E0);
+        win_plane<float, true>(e, w, 1, E1);
+        win_plane<float, true>(e, w, 2, E2);
+        if constexpr (FROM_TH) {
+            win_plane<float, false>(th, w, 0, T0);
+            win_plane<float, true>(th, w, 1, T1);
+            win_plane<float, true>(th, w, 2, T2);
+        }
         float acc = 0.0f;
-        for (int a = 0; a < 2; ++a)
-            for (int b = 0; b < 2; ++b)
-                for (int cc = 0; cc < 2; ++cc) {
-                    const int i = 2 * I + a, j = 2 * J + b, k = 2 * K + cc;
-                    const Cof<float> A = cof ? cof_at(cof, nf, cof_slot(Nf, i, j, k))
-                                             : cofactors(load19<float>(th, Nf, i, j, k), ih2);
-                    acc += f[offs(Nf, i, j, k)] - jac_apply(A, load19<float>(e, Nf, i, j, k), ih2);
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            if (a == 1) {   // slide the window: fine plane 2I+1 needs window planes 1..3
+                win_plane<float, false>(e, w, 3, E0);
+                if constexpr (FROM_TH) win_plane<float, false>(th, w, 3, T0);
+            }
+#pragma unroll
+            for (int b = 1; b <= 2; ++b)
+#pragma unroll
+                for (int cc = 1; cc <= 2; ++cc) {
+                    const Nb19<float> ne = a == 0 ? win_nb<float>(E0, E1, E2, b, cc) : win_nb<float>(E1, E2, E0, b, cc);
+                    Cof<float> A;
+                    if constexpr (FROM_TH) {
+                        A = cofactors(a == 0 ? win_nb<float>(T0, T1, T2, b, cc) : win_nb<float>(T1, T2, T0, b, cc), ih2);
+                    } else {
+                        A = cof_at(cof, nf, cof_slot(Nf, 2 * I + a, 2 * J + b - 1, 2 * K + cc - 1));
+                    }
+                    acc += f[w.at(1 + a, b, cc)] - jac_apply(A, ne, ih2);
                 }
+        }
         const float v = acc * 0.125f;
         fH[offs(Nc, I, J, K)] = v;
-        sacc += (double)v;
+        sacc.add(v);
     }
-    const double v = block_sum<kRowThreads>(sacc, sh);
+    const double v = block_sum<kRowThreads>(sacc.get(), sh);
     if (ltid() == 0) partials[4 * blockIdx.x + 0] = v;
 }
 
@@ -1211,7 +1422,7 @@ cudaError_t vcycle(recon_handle *H, const Hier<T> &Y, int l, const double *cptr)
                                                   H->scal + slot_scale(l + 1),
                                                   H->scal + slot_pscale(l + 1));
     note_launch();
-    k_form_rhs<T><<<blocks_for(nc), kThreads, 0, s>>>(Y.g[l + 1], Y.aux[l + 1], nc,
+    k_form_rhs<T><<<stride_blocks(nc), kThreads, 0, s>>>(Y.g[l + 1], Y.aux[l + 1], nc,
                                                       H->scal + slot_scale(l + 1));
     CK(cudaGetLastError());
     CK(vcycle<T>(H, Y, l + 1, H->scal + S_ZERO));
@@ -1227,16 +1438,13 @@ cudaError_t compat_gauge(recon_handle *H, const Hier<T> &Y, int l)
     cudaStream_t s = H->stream;
     const int N = H->Nl[l];
     const size_t n = ncell(N);
-    const unsigned nbr = row_grid(N, kMaxRedBlocks);
     const double h = H->hl[l];
-    note_launch();
-    k_residual_norms<T><<<nbr, row_block(), 0, s>>>(Y.t[l], Y.g[l], H->scal + S_C, N,
-                                                 (T)(1.0 / (h * h)), H->partials, nullptr,
-                                                 nullptr);
+    const unsigned nbr = launch_residual_norms<T>(Y.t[l], Y.g[l], H->scal + S_C, N, (T)(1.0 / (h * h)),
+                                                  H->partials, nullptr, nullptr, s);
     note_launch();
     k_finalize_cycle<<<1, kReduceThreads, 0, s>>>(H->partials, nbr, (double)n, H->scal);
     note_launch();
-    k_gauge<T><<<blocks_for(n), kThreads, 0, s>>>(Y.t[l], n, H->scal);
+    k_gauge<T><<<stride_blocks(n), kThreads, 0, s>>>(Y.t[l], n, H->scal);
     return cudaGetLastError();
 }
 
@@ -1389,13 +1597,17 @@ cudaError_t lin_vcycle(recon_handle *H, int l)
     const size_t nc = ncell(Nc);
     const unsigned nbr = row_grid(Nc, kMaxRedBlocks);
     note_launch();
-    k_lin_restrict_residual<<<nbr, row_block(), 0, s>>>(H->e32[l], H->f32[l], H->cof32[l], H->t32[l],
-                                                     N, ih2, H->f32[l + 1], H->partials);
+    if (H->cof32[l])
+        k_lin_restrict_residual<false><<<nbr, row_block(), 0, s>>>(H->e32[l], H->f32[l], H->cof32[l], nullptr,
+                                                                    N, ih2, H->f32[l + 1], H->partials);
+    else
+        k_lin_restrict_residual<true><<<nbr, row_block(), 0, s>>>(H->e32[l], H->f32[l], nullptr, H->t32[l],
+                                                                   N, ih2, H->f32[l + 1], H->partials);
     note_launch();
     k_finalize_mean<<<1, kReduceThreads, 0, s>>>(H->partials, nbr, (double)nc,
                                                  H->scal + slot_rmean(l + 1));
     note_launch();
-    k_sub_scalar<<<blocks_for(nc), kThreads, 0, s>>>(H->f32[l + 1], nc, H->scal + slot_rmean(l + 1));
+    k_sub_scalar<<<stride_blocks(nc), kThreads, 0, s>>>(H->f32[l + 1], nc, H->scal + slot_rmean(l + 1));
     CK(cudaMemsetAsync(H->e32[l + 1], 0, sizeof(float) * nc, s));
     CK(lin_vcycle(H, l + 1));
     CK(prolong_add<float>(Nc, H->e32[l + 1], (const float *)nullptr, nullptr, 1.0, H->e32[l], s));
@@ -1453,18 +1665,19 @@ cudaError_t mixed_residual(recon_handle *H, const double *b, const double *phi)
 {
     cudaStream_t s = H->stream;
     const size_t n = ncell(H->N);
-    const unsigned nbr = row_grid(H->N, kMaxRedBlocks);
+    unsigned nbr = row_grid(H->N, kMaxRedBlocks);
     const double ih2 = 1.0 / (H->h * H->h);
-    note_launch(2);
     if (H->cfg.mixed_df_residual) {
         const df ih2df = df_from_double(ih2);
+        note_launch();
         k_residual_df<<<nbr, row_block(), 0, s>>>(H->t32[0], H->lo32, H->g32[0], H->blo32,
                                                   H->scal + S_C, H->N, ih2df.hi, ih2df.lo,
                                                   H->f32[0], H->partials);
     } else {
-        k_residual_norms<double><<<nbr, row_block(), 0, s>>>(phi, b, H->scal + S_C, H->N, ih2,
-                                                             H->partials, H->f32[0], H->t32[0]);
+        nbr = launch_residual_norms<double>(phi, b, H->scal + S_C, H->N, ih2, H->partials, H->f32[0],
+                                            H->t32[0], s);
     }
+    note_launch();
     k_finalize_cycle<<<1, kReduceThreads, 0, s>>>(H->partials, nbr, (double)n, H->scal);
     return cudaGetLastError();
 }
@@ -1475,7 +1688,7 @@ cudaError_t mixed_correct(recon_handle *H, double *phi)
     cudaStream_t s = H->stream;
     const size_t n = ncell(H->N);
     note_launch();
-    k_sub_scalar<<<blocks_for(n), kThreads, 0, s>>>(H->f32[0], n, H->scal + S_MEAN_R);
+    k_sub_scalar<<<stride_blocks(n), kThreads, 0, s>>>(H->f32[0], n, H->scal + S_MEAN_R);
     for (int l = 1; l < H->nlev; ++l) CK(restrict_plain<float>(H->Nl[l - 1], H->t32[l - 1], H->t32[l], s));
     for (int l = 0; l < H->nlev; ++l) {
         if (H->Nl[l] >= kFusedMinN) continue;   // formed from theta32 in the kernels
@@ -1503,10 +1716,10 @@ cudaError_t mixed_finish(recon_handle *H, double *phi, bool converged)
         note_launch(3);
         k_df_to_double<<<nb2, kThreads, 0, s>>>(H->t32[0], H->lo32, phi, n, H->partials);
         k_finalize_mean<<<1, kReduceThreads, 0, s>>>(H->partials, nb2, (double)n, H->scal + S_MEAN_T);
-        k_gauge<double><<<blocks_for(n), kThreads, 0, s>>>(phi, n, H->scal);
+        k_gauge<double><<<stride_blocks(n), kThreads, 0, s>>>(phi, n, H->scal);
     } else if (converged) {
         note_launch();
-        k_gauge<double><<<blocks_for(n), kThreads, 0, s>>>(phi, n, H->scal);
+        k_gauge<double><<<stride_blocks(n), kThreads, 0, s>>>(phi, n, H->scal);
     }
     return cudaGetLastError();
 }
