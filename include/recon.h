@@ -130,13 +130,17 @@ recon_status recon_set_stream(recon_handle *h, void *stream);
 recon_status recon_get_config(const recon_handle *h, recon_config *cfg);
 recon_status recon_set_config(recon_handle *h, const recon_config *cfg);
 
-/* Cloud-in-cell density assignment (Sec. I footnote; spec step a1).
- * pos: device, n_part x 3 doubles (x, y, z) in [0, L) (wrapped if not).
+/* Cloud-in-cell density assignment (Sec. I footnote).
+ * pos: n_part x 3 doubles (x, y, z) in [0, L) (wrapped if not), in device
+ *      memory or in page-locked host memory (cudaHostAlloc / cudaHostRegister,
+ *      or a pinned framework tensor): the kernel then reads the positions
+ *      over the host link itself, with no staging copy.
  * rho: device N^3, ACCUMULATED into (zero it first for a fresh density);
  * each particle adds mass * prod_axis w, w = (1 - f, f) on cells
  * (i0, i0 + 1), u = x * (N / L) - 1/2, i0 = floor(u) mod N, f = u - floor(u).
  * Use mass = N^3 / n_part for a density normalised to mean 1.
- * Errors: RECON_E_INVALID (n_part < 0, null pointers), RECON_E_CUDA. */
+ * Errors: RECON_E_INVALID (n_part < 0, null pointers, pos in pageable host
+ * memory), RECON_E_CUDA. */
 recon_status recon_deposit_cic(recon_handle *h, const double *pos, long long n_part,
                                double mass, double *rho);
 
@@ -157,13 +161,17 @@ recon_status recon_solve(recon_handle *h, const double *b, double *phi, double t
 
 /* Reconstruction output (Sec. II.B steps B2-B3, eq. reconstructed_density,
  * and x - q = -grad theta of Sec. III.B), restated on the grid:
- *   psi  (device 3 x N^3, component-major) = -(central gradient of phi);
+ *   psi  (3 x N^3, component-major) = -(central gradient of phi);
  *   q_c = x_c + grad phi (mod L) for every Eulerian cell centre x_c;
  *   v_c = 3 - tr((I + H phi)^-1)   (div_q chi, chi = q - x);
- *   deltaL (device N^3, on the Lagrangian grid) =
+ *   deltaL (N^3, on the Lagrangian grid) =
  *       CIC(q_c, b_c v_c) / max(CIC(q_c, b_c), 1e-12).
- * Uses 2 N^3 doubles of handle workspace.  Errors: RECON_E_INVALID,
- * RECON_E_CUDA. */
+ * phi, b: device N^3.  psi and deltaL: device memory or page-locked host
+ * memory (written by the kernels over the host link).  psi is FP64
+ * differencing; v, the CIC weights and the two sums are FP32 (deltaL to
+ * ~1e-6 absolute).  Uses 2 N^3 doubles of handle workspace.
+ * Errors: RECON_E_INVALID (null pointers, an output in pageable host
+ * memory), RECON_E_CUDA. */
 recon_status recon_displace(recon_handle *h, const double *phi, const double *b,
                             double *psi, double *deltaL);
 

@@ -124,7 +124,10 @@ cudaError_t cic_deposit(const double *pos, long long n, int N, double L, double 
 recon_status adjoint(recon_handle *H, const double *gbar, double *lam);
 void adj_free(recon_handle *H);
 
+// phi -> (hi, lo) FP32 parts (recon_mg.cu)
+__global__ void k_split_df(const double *__restrict__ a, float *__restrict__ hi, float *__restrict__ lo,
+                           size_t n);
 cudaError_t displace(int N, double L, const double *phi, const double *b, double *psi,
-                     double *deltaL, double *scratch, cudaStream_t s);
+                     double *deltaL, double *scratch, double *split, cudaStream_t s);
 
 }  // namespace recon

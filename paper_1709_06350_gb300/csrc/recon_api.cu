@@ -289,12 +289,27 @@ recon_status recon_set_config(recon_handle *H, const recon_config *c)
     return RECON_OK;
 }
 
+// Device memory, managed memory or page-locked host memory (which kernels
+// reach directly); anything else (pageable host memory) is refused.
+static bool gpu_reachable(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged ||
+           (a.type == cudaMemoryTypeHost && a.devicePointer == p);
+}
+
 recon_status recon_deposit_cic(recon_handle *H, const double *pos, long long n_part, double mass,
                                double *rho)
 {
     if (!H) return RECON_E_INVALID;
     if (n_part < 0 || (n_part > 0 && !pos) || !rho)
         return set_err(H, RECON_E_INVALID, "bad particle count or NULL pointer");
+    if (n_part > 0 && !gpu_reachable(pos))
+        return set_err(H, RECON_E_INVALID, "pos must be device or page-locked host memory");
     return cuda_status(H, cic_deposit(pos, n_part, H->N, H->L, mass, rho, H->stream), "cic");
 }
 
@@ -326,7 +341,9 @@ recon_status recon_displace(recon_handle *H, const double *phi, const double *b,
 {
     if (!H) return RECON_E_INVALID;
     if (!phi || !b || !psi || !deltaL) return set_err(H, RECON_E_INVALID, "NULL pointer");
-    return cuda_status(H, displace(H->N, H->L, phi, b, psi, deltaL, H->work64, H->stream),
+    if (!gpu_reachable(psi) || !gpu_reachable(deltaL))
+        return set_err(H, RECON_E_INVALID, "psi and deltaL must be device or page-locked host memory");
+    return cuda_status(H, displace(H->N, H->L, phi, b, psi, deltaL, H->work64, H->work64b, H->stream),
                        "displace");
 }
 

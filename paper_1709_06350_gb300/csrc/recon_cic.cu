@@ -6,10 +6,13 @@
 // multiply-add), so cell indices and fractions are bit-identical to a plain
 // IEEE evaluation of the same formula on any host.
 //
-// Atomics: plain FP64 atomicAdd for the density.  Warp aggregation of lanes
-// that hit the same cell (__match_any_sync + shuffles) was measured slower on
-// GB300 (512^3 deposit 17.5 ms aggregated vs 9.9 ms plain).  The displacement
-// step accumulates its (b v, b) pair with one float2 vector atomic per corner.
+// GB300 runs FP64 at 1/64 of the FP32 rate, so both kernels keep FP64
+// arithmetic to what an FP64 result needs: the deposit forms u in FP64 and
+// does the rest (floor, fraction, corner weights) in 64-bit fixed point on
+// the integer pipes; the displacement forms psi in FP64 and the rest from
+// FP32 parts of phi.  Atomics: FP64 for the density, one float2 vector
+// atomic per corner for the displacement's (b v, b) pair; lanes that hold
+// consecutive particles (cells) merge shared z corners first.
 #include <cmath>
 
 #include "cellmath.cuh"
@@ -27,43 +30,123 @@ __device__ __forceinline__ void cic_axis(double x, int N, double inv_h, int &i0,
     i0 = (int)ii;
 }
 
-// Deposit `val` (per thread) with CIC weights at position (x, y, z).
+// Cell and fraction of u = x N/L - 1/2 in 64-bit fixed point, from the bits
+// of u (integer pipes only): i0 = floor(u) (mod N), f = (u - floor(u)) 2^64.
+// Exact for u in (-1, 2^31); returns false outside (the caller then uses
+// the FP64 form).
+__device__ __forceinline__ bool cic_fixed(double u, int N, int &i0, unsigned long long &f)
+{
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(u);
+    const int e = (int)((bits >> 52) & 0x7ff);
+    const unsigned long long m = (bits & 0xfffffffffffffull) | (e ? (1ull << 52) : 0ull);
+    const int sh = 1075 - e;   // fractional bits of the 53-bit integer m
+    if (e == 0) {              // +-0 or subnormal: cell 0, fraction ~0
+        i0 = 0;
+        f = 0;
+        return true;
+    }
+    if (sh <= 22) return false;   // |u| >= 2^31
+    unsigned long long ip, fr;
+    if (sh < 64) {
+        ip = m >> sh;
+        fr = (m & ((1ull << sh) - 1)) << (64 - sh);
+    } else {
+        ip = 0;
+        fr = sh - 64 < 64 ? m >> (sh - 64) : 0;
+    }
+    if (bits >> 63) {   // u < 0: floor = -1 and fraction 1 - |u| for |u| < 1
+        if (ip != 0 || fr == 0) return false;
+        i0 = N - 1;
+        f = 0ull - fr;
+        return true;
+    }
+    i0 = (int)(ip < (unsigned long long)N ? ip : ip % (unsigned long long)N);
+    f = fr;
+    return true;
+}
+
+// (a b) / 2^63 for 63-bit fixed-point weights a, b in [0, 2^63]
+__device__ __forceinline__ unsigned long long mul63(unsigned long long a, unsigned long long b)
+{
+    return (__umul64hi(a, b) << 1) | ((a * b) >> 63);
+}
+
+// a 63-bit fixed-point weight w (w / 2^63 in [0, 1]) as a double (truncated
+// to 53 bits), assembled on the integer pipes
+__device__ __forceinline__ double fixed63_to_double(unsigned long long w)
+{
+    if (w == 0) return 0.0;
+    const int lz = __clzll((long long)w);
+    const unsigned long long mant = (w << lz) >> 11;   // 53 bits, leading one at bit 52
+    return __longlong_as_double((long long)(((unsigned long long)(1023 - lz) << 52) |
+                                            (mant & 0xfffffffffffffull)));
+}
+
+// Warp-neighbour merge of a CIC z pair.  Lanes hold consecutive particles
+// (or cells) whose z targets are usually consecutive too: when lane L's
+// upper target t1 is lane L+1's lower target t0 (same (x, y) corner row),
+// lane L+1 adds lane L's value to its own and one atomic serves both.  All
+// 32 lanes must call this (inactive lanes pass the kNoCell targets).
+constexpr unsigned kNoCell = 0xffffffffu, kNoCell0 = 0xfffffffeu;
+__device__ __forceinline__ double shfl_up_v(double v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ float2 shfl_up_v(float2 v)
+{
+    return make_float2(__shfl_up_sync(0xffffffffu, v.x, 1), __shfl_up_sync(0xffffffffu, v.y, 1));
+}
+__device__ __forceinline__ double add_v(double a, double b) { return a + b; }
+__device__ __forceinline__ float2 add_v(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+
+template <typename V>
+__device__ __forceinline__ void zpair_add(V *__restrict__ acc, unsigned t0, unsigned t1, V v0, V v1,
+                                          bool active)
+{
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned up_t1 = __shfl_up_sync(0xffffffffu, t1, 1);
+    const unsigned dn_t0 = __shfl_down_sync(0xffffffffu, t0, 1);
+    const V up_v1 = shfl_up_v(v1);
+    const bool take = lane > 0 && up_t1 == t0;
+    const bool give = lane < 31 && dn_t0 == t1;
+    if (active) {
+        atomicAdd(acc + t0, take ? add_v(v0, up_v1) : v0);
+        if (!give) atomicAdd(acc + t1, v1);
+    }
+}
+
+// Deposit `val` with CIC weights at position (x, y, z) (inactive lanes take
+// part in the merge with no targets).  u is formed in FP64 with the two
+// roundings of the definition; the fraction, the corner weights
+// (w_x w_y) w_z and their conversion to double are 64-bit fixed point,
+// within ~1e-16 of the FP64 products.  val == 1 needs no multiply.
 __device__ __forceinline__ void cic_scatter(bool active, const double xyz[3], double val, int N,
                                             double inv_h, double *__restrict__ rho)
 {
-    if (!active) return;
-    int i0[3];
-    double f[3];
-    for (int d = 0; d < 3; ++d) cic_axis(xyz[d], N, inv_h, i0[d], f[d]);
-    for (int a = 0; a < 2; ++a)
-        for (int b = 0; b < 2; ++b)
-            for (int cc = 0; cc < 2; ++cc) {
-                const int i = a ? (i0[0] + 1 == N ? 0 : i0[0] + 1) : i0[0];
-                const int j = b ? (i0[1] + 1 == N ? 0 : i0[1] + 1) : i0[1];
-                const int k = cc ? (i0[2] + 1 == N ? 0 : i0[2] + 1) : i0[2];
-                const double w = __dmul_rn(__dmul_rn(a ? f[0] : 1.0 - f[0], b ? f[1] : 1.0 - f[1]),
-                                           cc ? f[2] : 1.0 - f[2]);
-                atomicAdd(rho + offs(N, i, j, k), __dmul_rn(val, w));
+    int i0[3] = {0, 0, 0}, i1[3] = {0, 0, 0};
+    unsigned long long w[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+    if (active)
+        for (int d = 0; d < 3; ++d) {
+            const double u = __dsub_rn(__dmul_rn(xyz[d], inv_h), 0.5);
+            unsigned long long f;
+            if (!cic_fixed(u, N, i0[d], f)) {   // far outside [0, L): the FP64 form
+                double ff;
+                cic_axis(xyz[d], N, inv_h, i0[d], ff);
+                f = ff >= 1.0 ? ~0ull : (unsigned long long)ldexp(ff, 64);
             }
-}
-
-// CIC of a value pair (vector atomic): acc[cell] += (v0, v1) * w.
-__device__ __forceinline__ void cic_scatter2(const double xyz[3], float v0, float v1, int N,
-                                             double inv_h, float2 *__restrict__ acc)
-{
-    int i0[3];
-    double f[3];
-    for (int d = 0; d < 3; ++d) cic_axis(xyz[d], N, inv_h, i0[d], f[d]);
-    const float fx = (float)f[0], fy = (float)f[1], fz = (float)f[2];
+            i1[d] = i0[d] + 1 == N ? 0 : i0[d] + 1;
+            w[d][1] = f >> 1;
+            w[d][0] = (1ull << 63) - w[d][1];
+        }
+    const bool unit = val == 1.0;
+#pragma unroll
     for (int a = 0; a < 2; ++a)
-        for (int b = 0; b < 2; ++b)
-            for (int cc = 0; cc < 2; ++cc) {
-                const int i = a ? (i0[0] + 1 == N ? 0 : i0[0] + 1) : i0[0];
-                const int j = b ? (i0[1] + 1 == N ? 0 : i0[1] + 1) : i0[1];
-                const int k = cc ? (i0[2] + 1 == N ? 0 : i0[2] + 1) : i0[2];
-                const float w = (a ? fx : 1.0f - fx) * (b ? fy : 1.0f - fy) * (cc ? fz : 1.0f - fz);
-                atomicAdd(acc + offs(N, i, j, k), make_float2(v0 * w, v1 * w));
-            }
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const unsigned long long wab = mul63(w[0][a], w[1][b]);
+            const unsigned row = offs(N, a ? i1[0] : i0[0], b ? i1[1] : i0[1], 0);
+            const double c0 = fixed63_to_double(mul63(wab, w[2][0]));
+            const double c1 = fixed63_to_double(mul63(wab, w[2][1]));
+            zpair_add<double>(rho, active ? row + i0[2] : kNoCell0, active ? row + i1[2] : kNoCell,
+                              unit ? c0 : __dmul_rn(val, c0), unit ? c1 : __dmul_rn(val, c1), active);
+        }
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -75,7 +158,7 @@ k_cic_deposit(const double *__restrict__ pos, long long n, int N, double inv_h, 
     double xyz[3] = {0.0, 0.0, 0.0};
     if (active)
         for (int d = 0; d < 3; ++d) xyz[d] = pos[3 * p + d];
-    cic_scatter(active, xyz, mass, N, inv_h, rho);   // inactive lanes return at once
+    cic_scatter(active, xyz, mass, N, inv_h, rho);
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -107,72 +190,120 @@ cudaError_t cic_deposit(const double *pos, long long n, int N, double L, double 
 
 // ---------------------------------------------------------------- displace
 // Per Eulerian cell x_c: psi = -grad phi (central differences, FP64), the
-// mapped Lagrangian position q = x + grad phi (mod L, FP64), and
-// v = 3 - tr((I + H)^-1) computed in FP32 from the FP64 Hessian; the pair
-// (b v, b) is accumulated at q with FP32 CIC weights (vector atomics).
-// delta_r = sum(b v) / max(sum(b), 1e-12) then carries FP32 rounding
-// (~1e-6 absolute for |delta_r| < 3).
+// mapped Lagrangian position q = x + grad phi (mod L), and
+// v = 3 - tr((I + H)^-1); the pair (b v, b) is accumulated at q with CIC
+// weights (FP32 vector atomics) and delta_r = sum(b v) / max(sum(b), 1e-12).
+//
+// Only psi (an FP64 output) is formed in FP64.  Everything else comes from
+// phi split into FP32 parts, phi = hi + lo (|lo| <= ulp(hi)/2): the
+// differences hi_n - hi_c of neighbouring values are exact in FP32
+// (Sterbenz) wherever they matter, so the second differences of H and the
+// CIC coordinate u = i + g/h carry one FP32 rounding of the result, not of
+// phi.  The CIC cell is floor(u) = i + floor(g/h) (mod N) with fraction
+// g/h - floor(g/h), the same numbers as x + g mapped through u = q/h - 1/2.
+// delta_r carries FP32 rounding (~1e-6 absolute for |delta_r| < 3).
 __global__ void __launch_bounds__(kRowX * kRowY)
-k_displace_cells(const double *__restrict__ t, const double *__restrict__ b, int N, double L,
-                 double h, double ih2, double *__restrict__ psi, float2 *__restrict__ acc)
+k_displace_cells(const double *__restrict__ t, const float *__restrict__ hi,
+                 const float *__restrict__ lo, const double *__restrict__ b, int N, double h,
+                 float ih2, double *__restrict__ psi, float2 *__restrict__ acc)
 {
     const unsigned n = (unsigned)N * N * N;
-    const double inv_h = (double)N / L, inv_2h = 0.5 / h;
+    const double inv_2h = 0.5 / h;
     FOR_ROWS(N, i, j)
-    for (int k = threadIdx.x; k < N; k += kRowX) {
-        const unsigned id = offs(N, i, j, k);
-        const Nb19<double> nb = load19<double>(t, N, i, j, k);
-        // central gradient; a multiply by 1/(2h) (within 1 ulp of the quotient)
-        const double g[3] = {(nb.xp - nb.xm) * inv_2h, (nb.yp - nb.ym) * inv_2h,
-                             (nb.zp - nb.zm) * inv_2h};
-        const double x[3] = {__dmul_rn(i + 0.5, h), __dmul_rn(j + 0.5, h), __dmul_rn(k + 0.5, h)};
-        double q[3];
-        for (int d = 0; d < 3; ++d) {
-            psi[(size_t)d * n + id] = -g[d];
-            // q mod L: for q in (-L, 2L) the conditional form gives exactly
-            // fmod's result (q - L is exact there); fmod handles the rest
-            double qq = __dadd_rn(x[d], g[d]);
-            if (qq >= L) qq = qq < 2.0 * L ? __dsub_rn(qq, L) : fmod(qq, L);
-            else if (qq <= -L) qq = fmod(qq, L);
-            if (qq < 0.0) qq = __dadd_rn(qq, L);
-            q[d] = qq;
+    for (int kb = 0; kb < N; kb += kRowX) {   // uniform trip count: the warp merges z pairs
+        const int k = kb + (int)threadIdx.x;
+        const bool active = k < N;
+        unsigned t0[4] = {kNoCell0, kNoCell0, kNoCell0, kNoCell0};
+        unsigned t1[4] = {kNoCell, kNoCell, kNoCell, kNoCell};
+        float2 v0[4], v1[4];
+        if (active) {
+            const unsigned id = offs(N, i, j, k);
+            // psi in FP64 from the face neighbours of phi (multiply by
+            // 1/(2h): within 1 ulp of the quotient)
+            psi[id] = (t[offs(N, wm(i, N), j, k)] - t[offs(N, wp(i, N), j, k)]) * inv_2h;
+            psi[(size_t)n + id] = (t[offs(N, i, wm(j, N), k)] - t[offs(N, i, wp(j, N), k)]) * inv_2h;
+            psi[2 * (size_t)n + id] = (t[offs(N, i, j, wm(k, N))] - t[offs(N, i, j, wp(k, N))]) * inv_2h;
+            // differences to the centre: exact for hi, tiny for lo
+            const Nb19<float> H = load19<float>(hi, N, i, j, k);
+            const Nb19<float> Lo = load19<float>(lo, N, i, j, k);
+            auto d = [&](float hn, float ln) { return (hn - H.c) + (ln - Lo.c); };
+            auto dd = [&](float h1, float l1, float h2, float l2) {
+                return ((h1 - H.c) + (h2 - H.c)) + ((l1 + l2) - 2.0f * Lo.c);
+            };
+            const float q4 = 0.25f * ih2;
+            const float axx = 1.0f + dd(H.xp, Lo.xp, H.xm, Lo.xm) * ih2;
+            const float ayy = 1.0f + dd(H.yp, Lo.yp, H.ym, Lo.ym) * ih2;
+            const float azz = 1.0f + dd(H.zp, Lo.zp, H.zm, Lo.zm) * ih2;
+            const float hxy = (dd(H.xpyp, Lo.xpyp, H.xmym, Lo.xmym) - dd(H.xmyp, Lo.xmyp, H.xpym, Lo.xpym)) * q4;
+            const float hyz = (dd(H.ypzp, Lo.ypzp, H.ymzm, Lo.ymzm) - dd(H.ymzp, Lo.ymzp, H.ypzm, Lo.ypzm)) * q4;
+            const float hxz = (dd(H.xpzp, Lo.xpzp, H.xmzm, Lo.xmzm) - dd(H.xmzp, Lo.xmzp, H.xpzm, Lo.xpzm)) * q4;
+            const float cxx = ayy * azz - hyz * hyz, cyy = axx * azz - hxz * hxz, czz = axx * ayy - hxy * hxy;
+            const float D = axx * cxx - hxy * (hxy * azz - hyz * hxz) + hxz * (hxy * hyz - ayy * hxz);
+            const float v = 3.0f - (cxx + cyy + czz) / D;
+            // CIC coordinate along each axis: u = i + g/h, g/h = (phi_+ - phi_-) / (2 h^2)
+            const float half_ih2 = 0.5f * ih2;
+            const float u[3] = {(d(H.xp, Lo.xp) - d(H.xm, Lo.xm)) * half_ih2,
+                                (d(H.yp, Lo.yp) - d(H.ym, Lo.ym)) * half_ih2,
+                                (d(H.zp, Lo.zp) - d(H.zm, Lo.zm)) * half_ih2};
+            const int own[3] = {i, j, k};
+            int c0[3], c1[3];
+            float f[3];
+            for (int a = 0; a < 3; ++a) {
+                const float fl = floorf(u[a]);
+                f[a] = u[a] - fl;
+                int c = own[a] + (int)fl;
+                if (c < 0 || c >= N) c = ((c % N) + N) % N;
+                c0[a] = c;
+                c1[a] = c + 1 == N ? 0 : c + 1;
+            }
+            const float bb = (float)b[id];
+            const float w0 = bb * v, w1 = bb;
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                for (int bq = 0; bq < 2; ++bq) {
+                    const float wab = (a ? f[0] : 1.0f - f[0]) * (bq ? f[1] : 1.0f - f[1]);
+                    const float wz0 = wab * (1.0f - f[2]), wz1 = wab * f[2];
+                    const unsigned row = offs(N, a ? c1[0] : c0[0], bq ? c1[1] : c0[1], 0);
+                    t0[2 * a + bq] = row + c0[2];
+                    t1[2 * a + bq] = row + c1[2];
+                    v0[2 * a + bq] = make_float2(w0 * wz0, w1 * wz0);
+                    v1[2 * a + bq] = make_float2(w0 * wz1, w1 * wz1);
+                }
+        } else {
+            for (int q = 0; q < 4; ++q) v0[q] = v1[q] = make_float2(0.0f, 0.0f);
         }
-        // Hessian in FP64 (differences of phi), the rest in FP32
-        const float axx = (float)(1.0 + ((nb.xp + nb.xm) - 2.0 * nb.c) * ih2);
-        const float ayy = (float)(1.0 + ((nb.yp + nb.ym) - 2.0 * nb.c) * ih2);
-        const float azz = (float)(1.0 + ((nb.zp + nb.zm) - 2.0 * nb.c) * ih2);
-        const float hxy = (float)(((nb.xpyp + nb.xmym) - (nb.xmyp + nb.xpym)) * (0.25 * ih2));
-        const float hyz = (float)(((nb.ypzp + nb.ymzm) - (nb.ymzp + nb.ypzm)) * (0.25 * ih2));
-        const float hxz = (float)(((nb.xpzp + nb.xmzm) - (nb.xmzp + nb.xpzm)) * (0.25 * ih2));
-        const float cxx = ayy * azz - hyz * hyz, cyy = axx * azz - hxz * hxz, czz = axx * ayy - hxy * hxy;
-        const float D = axx * cxx - hxy * (hxy * azz - hyz * hxz) + hxz * (hxy * hyz - ayy * hxz);
-        const float v = 3.0f - (cxx + cyy + czz) / D;
-        const float bb = (float)b[id];
-        cic_scatter2(q, bb * v, bb, N, inv_h, acc);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) zpair_add<float2>(acc, t0[q], t1[q], v0[q], v1[q], active);
     }
 }
 
+// delta_r = sum(b v) / max(sum(b), 1e-12): FP32 quotient (the sums are FP32)
 __global__ void __launch_bounds__(kThreads)
 k_displace_finish(const float2 *__restrict__ acc, size_t n, double *__restrict__ out)
 {
     const size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (id < n) {
         const float2 a = acc[id];
-        const double den = (double)a.y;
-        out[id] = (double)a.x / (den > 1e-12 ? den : 1e-12);
+        out[id] = (double)(a.x / fmaxf(a.y, 1e-12f));
     }
 }
 
+// scratch: N^3 doubles of room (the float2 sums); split: N^3 doubles of
+// room for the FP32 parts of phi
 cudaError_t displace(int N, double L, const double *phi, const double *b, double *psi,
-                     double *deltaL, double *scratch, cudaStream_t s)
+                     double *deltaL, double *scratch, double *split, cudaStream_t s)
 {
     const size_t n = (size_t)N * N * N;
     const double h = L / N;
-    float2 *acc = reinterpret_cast<float2 *>(scratch);   // N^3 float2 = N^3 doubles of room
+    float2 *acc = reinterpret_cast<float2 *>(scratch);
+    float *hi = reinterpret_cast<float *>(split), *lo = hi + n;
     cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(float2) * n, s);
     if (e != cudaSuccess) return e;
-    note_launch(2);
-    k_displace_cells<<<row_grid(N), row_block(), 0, s>>>(phi, b, N, L, h, 1.0 / (h * h), psi, acc);
+    note_launch(3);
+    k_split_df<<<blocks_for(n), kThreads, 0, s>>>(phi, hi, lo, n);
+    k_displace_cells<<<row_grid(N), row_block(), 0, s>>>(phi, hi, lo, b, N, h, (float)(1.0 / (h * h)),
+                                                        psi, acc);
     k_displace_finish<<<blocks_for(n), kThreads, 0, s>>>(acc, n, deltaL);
     return cudaGetLastError();
 }

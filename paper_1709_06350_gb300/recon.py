@@ -123,6 +123,23 @@ def _dev_ptr(t, dtype=None, numel=None):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _reachable_ptr(t, dtype=None, numel=None):
+    """A CUDA tensor, or a CPU tensor in page-locked memory (kernels read or
+    write it over the host link); pageable CPU tensors are refused."""
+    import torch
+    if isinstance(t, torch.Tensor) and not t.is_cuda:
+        if not t.is_pinned():
+            raise TypeError("expected a CUDA tensor or a pinned (page-locked) CPU tensor")
+        if not t.is_contiguous():
+            raise ValueError("expected a contiguous tensor")
+        if dtype is not None and t.dtype != dtype:
+            raise TypeError(f"expected dtype {dtype}, got {t.dtype}")
+        if numel is not None and t.numel() != numel:
+            raise ValueError(f"expected {numel} elements, got {t.numel()}")
+        return ctypes.c_void_p(t.data_ptr())
+    return _dev_ptr(t, dtype, numel)
+
+
 def _stream(stream=None):
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
@@ -167,7 +184,7 @@ def recon_set_config(h, cfg: recon_config) -> None:
 def recon_deposit_cic(h, N: int, pos, mass: float, rho) -> None:
     import torch
     n = pos.numel() // 3
-    _check(load().recon_deposit_cic(h, _dev_ptr(pos, torch.float64) if n else None, n,
+    _check(load().recon_deposit_cic(h, _reachable_ptr(pos, torch.float64) if n else None, n,
                                     float(mass), _dev_ptr(rho, torch.float64, N ** 3)), h)
 
 
@@ -187,8 +204,8 @@ def recon_displace(h, N: int, phi, b, psi, deltaL) -> None:
     import torch
     _check(load().recon_displace(h, _dev_ptr(phi, torch.float64, N ** 3),
                                  _dev_ptr(b, torch.float64, N ** 3),
-                                 _dev_ptr(psi, torch.float64, 3 * N ** 3),
-                                 _dev_ptr(deltaL, torch.float64, N ** 3)), h)
+                                 _reachable_ptr(psi, torch.float64, 3 * N ** 3),
+                                 _reachable_ptr(deltaL, torch.float64, N ** 3)), h)
 
 
 def recon_adjoint(h, N: int, gbar_phi, gbar_b) -> None:
@@ -335,10 +352,13 @@ class Solver:
         return {name: getattr(c, name) for name, _ in c._fields_}
 
     def deposit_cic(self, pos, mass=None, rho=None):
+        """pos: CUDA tensor or pinned CPU tensor (read by the kernel over the
+        host link); rho: CUDA tensor, accumulated into."""
         import torch
         n = pos.numel() // 3
         if rho is None:
-            rho = torch.zeros((self.N,) * 3, dtype=torch.float64, device=pos.device)
+            rho = torch.zeros((self.N,) * 3, dtype=torch.float64,
+                              device=pos.device if pos.is_cuda else torch.device("cuda"))
         m = float(self.N) ** 3 / max(n, 1) if mass is None else float(mass)
         recon_deposit_cic(self.h, self.N, pos, m, rho)
         return rho
@@ -350,10 +370,13 @@ class Solver:
         _, stats = recon_solve(self.h, self.N, b, phi, tol, max_cycles, raise_on_noconv)
         return phi, stats
 
-    def displace(self, phi, b):
+    def displace(self, phi, b, psi=None, dl=None):
+        """psi, dl: optional outputs (CUDA tensors or pinned CPU tensors)."""
         import torch
-        psi = torch.empty((3,) + tuple(phi.shape), dtype=torch.float64, device=phi.device)
-        dl = torch.empty_like(phi)
+        if psi is None:
+            psi = torch.empty((3,) + tuple(phi.shape), dtype=torch.float64, device=phi.device)
+        if dl is None:
+            dl = torch.empty_like(phi)
         recon_displace(self.h, self.N, phi, b, psi, dl)
         return psi, dl
 

@@ -290,10 +290,12 @@ def test_solve_domain_and_limits(R):
 
 
 # ------------------------------------------------------------------ output
-def test_displace_parity(R, O):
-    N, L = 32, 64.0
-    b, _, _ = zeldovich_density(O, N, L, 0.8, 4.0, 41)
-    t, _ = O.solve(b, L, tol=1e-11)
+@pytest.mark.parametrize("N,L,sig,Rs,seed", [(32, 64.0, 0.8, 4.0, 41), (64, 64.0, 1.0, 2.0, 3000)])
+def test_displace_parity(R, O, N, L, sig, Rs, seed):
+    """64^3 at sigma 1, R = 2 h^-1 Mpc: the bench recipe's resolution, with
+    cells down to b ~ 0.14 where v = 3 - tr((I+H)^-1) is most sensitive."""
+    b, _, _ = zeldovich_density(O, N, L, sig, Rs, seed)
+    t, _ = O.solve(b, L, tol=1e-11, max_cycles=40)
     psi_ref, dl_ref = O.displace(t, b, L)
     s = R.Solver(N, L)
     psi, dl = s.displace(dev(t), dev(b))
@@ -337,4 +339,36 @@ def test_launch_counter_counts_our_kernels(R):
     s = R.Solver(16, 16.0)
     s.solve(torch.ones((16,) * 3, dtype=torch.float64, device="cuda") * 1.0, tol=1e-8)
     assert R.recon_kernel_launches() > before
+    s.close()
+
+
+def test_page_locked_host_buffers(R, O):
+    """Positions read from page-locked host memory and delta_r written into it
+    give the device results; pageable host memory is refused, not read."""
+    import ctypes
+    from paper_1709_06350_gb300 import synth
+    N, L = 32, 64.0
+    _, dh = synth.linear_field(N, L, 0.8, 91)
+    pos = synth.zeldovich_positions(dh, N, L)
+    s = R.Solver(N, L)
+    rho_dev = s.deposit_cic(dev(pos))
+    pos_pinned = torch.from_numpy(pos).pin_memory()
+    rho_host_read = s.deposit_cic(pos_pinned)
+    assert np.max(np.abs(host(rho_host_read) - host(rho_dev))) < 1e-12 * host(rho_dev).max()
+    with pytest.raises(TypeError):
+        s.deposit_cic(torch.from_numpy(pos))            # pageable: refused by the binding
+    rho = torch.zeros((N,) * 3, dtype=torch.float64, device="cuda")
+    st = R.load().recon_deposit_cic(s.h, ctypes.c_void_p(pos.ctypes.data), pos.shape[0], 1.0,
+                                    ctypes.c_void_p(rho.data_ptr()))
+    assert st == 1                                        # RECON_E_INVALID from the C ABI
+    assert host(rho).sum() == 0.0
+    b, _, _ = zeldovich_density(O, N, L, 0.8, 4.0, 92)
+    t, _ = O.solve(b, L, tol=1e-10)
+    psi_d, dl_d = s.displace(dev(t), dev(b))
+    dl_h = torch.empty((N,) * 3, dtype=torch.float64).pin_memory()
+    psi_h = torch.empty((3,) + (N,) * 3, dtype=torch.float64).pin_memory()
+    s.displace(dev(t), dev(b), psi=psi_h, dl=dl_h)
+    torch.cuda.synchronize()
+    assert np.max(np.abs(psi_h.numpy() - host(psi_d))) == 0.0
+    assert np.max(np.abs(dl_h.numpy() - host(dl_d))) < 1e-6
     s.close()
