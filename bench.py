@@ -370,7 +370,8 @@ def main():
                               "linear field"},
             "batched": batch,
             "adjoint": adj,
-            "gs_cell_updates_per_s": roof.pop("cell_updates_per_s", None),
+            "gs_cell_updates_per_s": {"fas_newton": kern[1]["cell_updates_per_s"],
+                                      "linear": roof.pop("cell_updates_per_s", None)},
             "roofline": roof,
             "other_kernels": kern[1:],
             "gpu_launches": launches,
@@ -503,15 +504,21 @@ def _time_launches(torch, stream, fn, reps):
     return (tr - t1) / (reps - 1)
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# each fused smoother, from an ncu --set full capture of the 384^3 case
+# (python bench.py --kernel-only 384); a launch at N^3 moves (N/384)^3 times
+# as much.  Valid for the kernels as they were captured: re-measure after a
+# change to either kernel.
+NCU_TRAFFIC_384 = {"LIN": 751.469312e6 + 208.285440e6, "FAS": 498.721280e6 + 201.100032e6}
+
+
 def kernel_roofline(recon, torch, N, L, dev, stream):
     """The two FP32 smoothers at N^3, each timed in isolation with CUDA events
     on its stream (one launch = one fused red+black sweep for N >= 128).
+    The linear smoother comes first: it is the larger share of the step.
 
-    Algorithmic bytes per sweep: FAS smoother 12 B/cell (read theta and b,
-    write theta); linear smoother 16 B/cell (read theta, e, f; write e).
-    The linear kernel as built reads six precomputed cofactors per cell
-    instead of theta, so its DRAM traffic exceeds these bytes; the fraction
-    is always against the algorithmic figure."""
+    Algorithmic bytes per sweep: linear smoother 16 B/cell (read theta, e,
+    f; write e); FAS smoother 12 B/cell (read theta and b, write theta)."""
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -534,14 +541,16 @@ def kernel_roofline(recon, torch, N, L, dev, stream):
         e, g, th, h, sweeps=k, work=work7, stream=stream), reps)
     del th, g, work, e, work7
     out = []
-    for name, t, bpc in (("k_sweep_fused<float, FAS> (FP32 red-black Newton smoother, one sweep)", t_fas, 12.0),
-                         ("k_sweep_fused<float, LIN> (FP32 red-black smoother of J e = f, one sweep)", t_lin, 16.0)):
+    for key, name, t, bpc in (
+            ("LIN", "k_sweep_fused<float, LIN> (FP32 red-black smoother of J e = f, one sweep)", t_lin, 16.0),
+            ("FAS", "k_sweep_fused<float, FAS> (FP32 red-black Newton smoother, one sweep)", t_fas, 12.0)):
         alg = bpc * N ** 3
         ach = alg / t / 1e9
         out.append({"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                    "frac": ach / hbm, "traffic": None, "peak_source": src,
-                    "algorithmic_bytes_per_launch": alg, "avg_launch_ms": t * 1e3,
-                    "cell_updates_per_s": N ** 3 / t})
+                    "frac": ach / hbm, "traffic": NCU_TRAFFIC_384[key] * (N / 384.0) ** 3,
+                    "traffic_source": "ncu dram bytes of one 384^3 launch, scaled by cells",
+                    "peak_source": src, "algorithmic_bytes_per_launch": alg,
+                    "avg_launch_ms": t * 1e3, "cell_updates_per_s": N ** 3 / t})
     return out
 
 
