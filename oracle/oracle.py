@@ -75,6 +75,7 @@ def _load():
             "or_solve": (_I, [_P, _I, _D, _P, _P, _D, _I, _P, _I, _P]),
             "or_vcycle": (None, [_P, _I, _D, _P, _D, _P]),
             "or_cic_deposit": (None, [_P, _L, _I, _D, _D, _P]),
+            "or_assign_deposit": (None, [_P, _L, _I, _D, _D, _I, _P]),
             "or_cic_cells": (None, [_P, _L, _I, _D, _P, _P]),
             "or_displace": (None, [_P, _P, _I, _D, _P, _P]),
             "or_cofactors": (None, [_P, _I, _D, _P]),
@@ -277,6 +278,19 @@ def cic_deposit(pos, N, L, mass=None) -> np.ndarray:
     m = (float(N) ** 3 / n) if mass is None else float(mass)
     rho = np.zeros((N, N, N))
     _load().or_cic_deposit(_ptr(p), n, int(N), float(L), m, _ptr(rho))
+    return rho
+
+
+ASSIGN = {"ngp": 0, "cic": 1, "tsc": 2}
+
+
+def assign_deposit(pos, N, L, scheme="cic", mass=None) -> np.ndarray:
+    """NGP / CIC / TSC density (Sec. I footnote); default mass N^3 / n."""
+    p = _f64(pos).reshape(-1, 3)
+    n = p.shape[0]
+    m = (float(N) ** 3 / n) if mass is None else float(mass)
+    rho = np.zeros((N, N, N))
+    _load().or_assign_deposit(_ptr(p), n, int(N), float(L), m, ASSIGN[scheme], _ptr(rho))
     return rho
 
 

@@ -660,6 +660,58 @@ void or_cic_deposit(const double *pos, long npart, int N, double L,
     }
 }
 
+/* ------------------------------------------------------------------ */
+/* Nearest-grid-point and triangular-shaped-cloud assignment (Sec. I,    */
+/* footnote: the method works with any density assignment, NGP, CIC or  */
+/* TSC).  Cell i covers [i h, (i+1) h), centre (i + 1/2) h.  Along each  */
+/* axis, with u = x (N/L), i = floor(u), d = u - i - 1/2 in [-1/2, 1/2): */
+/*   NGP: weight 1 on cell i;                                            */
+/*   TSC: the quadratic B-spline of width 3h centred on the particle,    */
+/*        sampled at the cell centres:                                   */
+/*        W(i-1) = (1/2 - d)^2 / 2,  W(i) = 3/4 - d^2,                   */
+/*        W(i+1) = (1/2 + d)^2 / 2.                                      */
+/* The 3-D weight is the product over the axes (periodic cells).         */
+/* scheme: 0 NGP, 1 CIC (or_cic_deposit above), 2 TSC.                   */
+/* ------------------------------------------------------------------ */
+static void nearest_cell(double x, int N, double L, int *i, double *d)
+{
+    double u = x * ((double)N / L);
+    double fl = floor(u);
+    *d = (u - fl) - 0.5;
+    long ii = (long)fl;
+    ii %= N;
+    if (ii < 0) ii += N;
+    *i = (int)ii;
+}
+
+void or_assign_deposit(const double *pos, long npart, int N, double L, double mass,
+                       int scheme, double *rho)
+{
+    if (scheme == 1) {
+        or_cic_deposit(pos, npart, N, L, mass, rho);
+        return;
+    }
+    for (long p = 0; p < npart; ++p) {
+        int i[3];
+        double d[3], w[3][3];
+        for (int a = 0; a < 3; ++a) {
+            nearest_cell(pos[3 * p + a], N, L, &i[a], &d[a]);
+            w[a][0] = 0.5 * (0.5 - d[a]) * (0.5 - d[a]);
+            w[a][1] = 0.75 - d[a] * d[a];
+            w[a][2] = 0.5 * (0.5 + d[a]) * (0.5 + d[a]);
+        }
+        if (scheme == 0) {
+            rho[at(N, i[0], i[1], i[2])] += mass;
+            continue;
+        }
+        for (int a = -1; a <= 1; ++a)
+            for (int b = -1; b <= 1; ++b)
+                for (int c = -1; c <= 1; ++c)
+                    rho[at(N, i[0] + a, i[1] + b, i[2] + c)] +=
+                        mass * (w[0][a + 1] * w[1][b + 1] * w[2][c + 1]);
+    }
+}
+
 /* CIC with a per-particle value: rho[cell] += value[p] * w.  Used by the */
 /* displacement step below.                                              */
 static void cic_weighted(const double *pos, long npart, int N, double L,

@@ -380,6 +380,69 @@ def test_cic_textbook_definition(O):
     assert np.all(frac == 0.0) and list(cells[0]) == [0, 1, 2]
 
 
+# --------------------------------------------------------------- NGP / TSC
+def _cardinal_bspline(order):
+    """scipy's B-spline basis element of degree `order` on unit-spaced knots
+    centred on 0: the box, hat and quadratic kernels of NGP, CIC and TSC."""
+    from scipy.interpolate import BSpline
+    knots = np.arange(order + 2) - (order + 1) / 2.0
+    return BSpline.basis_element(knots, extrapolate=False)
+
+
+@pytest.mark.parametrize("scheme,order", [("ngp", 0), ("cic", 1), ("tsc", 2)])
+def test_assignment_is_the_cardinal_bspline(O, scheme, order):
+    """One particle gives cell c the product over axes of B((c + 1/2) - x/h),
+    B the cardinal B-spline of degree 0 (NGP), 1 (CIC) or 2 (TSC), with
+    periodic distances (Sec. I footnote names the three schemes)."""
+    N, L = 8, 12.0
+    h = L / N
+    B = _cardinal_bspline(order)
+    rng = np.random.default_rng(17 + order)
+    for x in rng.uniform(-0.3 * L, 1.3 * L, (12, 3)):
+        rho = O.assign_deposit(x[None, :], N, L, scheme, mass=1.0)
+        ref = np.ones((N, N, N))
+        for a in range(3):
+            dist = (np.arange(N) + 0.5) - x[a] / h
+            dist = (dist + N / 2) % N - N / 2          # minimum image, in cells
+            w = np.nan_to_num(B(dist))
+            shape = [1, 1, 1]
+            shape[a] = N
+            ref = ref * w.reshape(shape)
+        assert np.allclose(rho, ref, atol=1e-14), (scheme, x)
+
+
+@pytest.mark.parametrize("scheme", ["ngp", "cic", "tsc"])
+def test_assignment_lattice_and_mass(O, scheme):
+    """Particles on the cell centres give exactly 1 everywhere for every
+    scheme; any particle set deposits its total mass."""
+    N, L = 16, 20.0
+    rho = O.assign_deposit(synth.lattice_positions(N, L), N, L, scheme)
+    assert np.all(rho == 1.0)
+    rng = np.random.default_rng(23)
+    pos = rng.uniform(-L, 2 * L, (500, 3))
+    rho = O.assign_deposit(pos, N, L, scheme, mass=0.37)
+    assert rho.sum() == pytest.approx(500 * 0.37, rel=1e-13)
+    assert rho.min() >= 0.0
+
+
+def test_convergence_insensitive_to_tracer_and_mesh(O):
+    """Sec. I: with 8 N^3 particles on an N^3 mesh, or N^3 particles on an
+    (2N)^3 mesh, the relaxation converges at a rate similar to the default
+    N^3 on N^3 (here: FAS cycle counts to 1e-8 within two of each other, for
+    NGP, CIC and TSC densities of the same seeded field)."""
+    N, L, R = 16, 64.0, 8.0
+    cycles = {}
+    for label, n_lat, n_mesh in (("N3 on N3", N, N), ("8N3 on N3", 2 * N, N), ("N3 on 8N3", N, 2 * N)):
+        _, dh = synth.linear_field(n_lat, L, 0.8, 31)
+        pos = synth.zeldovich_positions(dh, n_lat, L)
+        for scheme in ("ngp", "cic", "tsc"):
+            b = synth.smooth_and_floor(O.assign_deposit(pos, n_mesh, L, scheme), L, R)
+            _, info = O.solve(b, L, tol=1e-8, max_cycles=40)
+            assert info["status"] == 0, (label, scheme)
+            cycles[(label, scheme)] = info["cycles"]
+    assert max(cycles.values()) - min(cycles.values()) <= 2, cycles
+
+
 # --------------------------------------------------------------- displacement
 def test_displace_zero_and_plane(O):
     N, L = 16, 32.0
@@ -458,6 +521,10 @@ MUTATIONS = {
     "restrict-index": ("acc += f[at(Nf, 2 * I + a, 2 * J + b, 2 * K + cc)];",
                        "acc += f[at(Nf, 2 * I + a, 2 * J + b, 2 * K)];"),
     "no-compat": ("        c -= m;\n        double mt", "        double mt"),
+    "tsc-side": ("w[a][0] = 0.5 * (0.5 - d[a]) * (0.5 - d[a]);",
+                 "w[a][0] = 0.5 * (0.5 + d[a]) * (0.5 + d[a]);"),
+    "ngp-cell": ("rho[at(N, i[0], i[1], i[2])] += mass;",
+                 "rho[at(N, i[0], i[1], i[2] + 1)] += mass;"),
 }
 
 
@@ -487,6 +554,8 @@ def test_mutations_are_caught(O, name, tmp_path):
         lambda: test_separable_potential(M),
         lambda: test_restriction_is_eight_son_mean(M),
         lambda: test_prolongation_reproduces_linear_fields(M),
+        lambda: test_assignment_is_the_cardinal_bspline(M, "ngp", 0),
+        lambda: test_assignment_is_the_cardinal_bspline(M, "tsc", 2),
     ]
     failed = 0
     for pin in pins:
