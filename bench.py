@@ -45,6 +45,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-batch", action="store_true")
     p.add_argument("--no-adjoint", action="store_true")
+    p.add_argument("--no-assignment", action="store_true")
     p.add_argument("--batch-count", type=int, default=64)
     p.add_argument("--adjoint-n", type=int, default=256)
     p.add_argument("--fd-directions", type=int, default=8)
@@ -205,6 +206,11 @@ def main():
     pos = synth.zeldovich_positions(dh, N, L).contiguous()
     del dh
     torch.cuda.empty_cache()
+    # page-locked host buffers of the end-to-end leg, made before any timed work
+    host = None
+    if not args.no_e2e:
+        host = {"pos": pos.cpu().pin_memory(),
+                "dl": [torch.empty((N, N, N), dtype=torch.float64).pin_memory() for _ in range(2)]}
 
     dtype = recon.RECON_MIXED if args.dtype == "mixed" else recon.RECON_F64
     solver = recon.Solver(N, L, dtype)
@@ -273,14 +279,16 @@ def main():
     e2e = None
     if not args.no_e2e:
         dl_dev = ref_dl.view(N, N, N).cpu()
-        pos_host = pos.cpu().pin_memory()
-        dl_host = [torch.empty((N, N, N), dtype=torch.float64).pin_memory() for _ in range(2)]
+        pos_host, dl_host = host["pos"], host["dl"]
         posbuf = [torch.empty_like(pos) for _ in range(2)]
+        dlbuf = [torch.empty((N, N, N), dtype=torch.float64, device=dev) for _ in range(2)]
+        psibuf = torch.empty((3, N, N, N), dtype=torch.float64, device=dev)
         copy = torch.cuda.Stream(device=dev)
 
         def run_host(K):
             h2d = [torch.cuda.Event() for _ in range(2)]
             used = [torch.cuda.Event() for _ in range(2)]
+            d2h = [None, None]
             with torch.cuda.stream(copy):
                 posbuf[0].copy_(pos_host, non_blocking=True)
                 h2d[0].record(copy)
@@ -298,13 +306,16 @@ def main():
                 used[cur].record(stream)
                 b = synth.smooth_and_floor(rho, L, R, fft_dtype=torch.float32)
                 solver.solve(b, phi=phi, tol=tol, max_cycles=40)
-                _, dl = solver.displace(phi, b)
+                if d2h[cur] is not None:
+                    stream.wait_event(d2h[cur])   # delta_r of step k-2 has left dlbuf[cur]
+                solver.displace(phi, b, psi=psibuf, dl=dlbuf[cur])
                 done = torch.cuda.Event()
                 done.record(stream)
                 with torch.cuda.stream(copy):
                     copy.wait_event(done)
-                    dl.record_stream(copy)
-                    dl_host[cur].copy_(dl, non_blocking=True)
+                    dl_host[cur].copy_(dlbuf[cur], non_blocking=True)
+                    d2h[cur] = torch.cuda.Event()
+                    d2h[cur].record(copy)
             stream.wait_stream(copy)
             return dl_host[(K - 1) % 2]
 
@@ -325,7 +336,7 @@ def main():
                "transfer": "positions of step k+1 copied in and delta_r of step k copied out by "
                            "the copy engines on a copy stream, overlapping step k",
                "max_abs_diff_vs_device_step": check}
-        del pos_host, dl_host, posbuf
+        del pos_host, dl_host, posbuf, dlbuf, psibuf, host
 
     # ---- FP64 GPU path on the same density (the comparison the metric names)
     fp64 = None
@@ -363,6 +374,11 @@ def main():
         batch = bench_batch(recon, synth, torch, dev, args.batch_count)
         solver = recon.Solver(N, L, dtype)
         autotune.apply(solver, N, dtype)
+
+    assign = None
+    if not args.no_assignment and rank == 0:
+        torch.cuda.empty_cache()
+        assign = bench_assignment(recon, synth, torch, dev, pos, W, autotune)
 
     adj = None
     if not args.no_adjoint and rank == 0:
@@ -407,6 +423,7 @@ def main():
                     "fields": "delta_r (displacement output, Lagrangian grid) vs the seeded "
                               "linear field"},
             "batched": batch,
+            "assignment": assign,
             "adjoint": adj,
             "gs_cell_updates_per_s": {"fas_newton": kern[1]["cell_updates_per_s"],
                                       "linear": roof.pop("cell_updates_per_s", None)},
@@ -422,6 +439,47 @@ def main():
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def bench_assignment(recon, synth, torch, dev, pos, W, autotune):
+    """NGP / CIC / TSC deposits of the workload's particles (timed), and the
+    convergence of mixed solves with the three schemes and three tracer /
+    mesh ratios (Sec. I: N^3 on N^3, 8N^3 on N^3, N^3 on 8N^3)."""
+    N, L, R, tol = W.N, W.L, W.R, W.tol
+    out = {"deposit_ms": {}, "convergence": []}
+    cases = [(f"{N}^3 particles", N, pos), (f"{N}^3 particles", N // 2, pos)]
+    _, dh = synth.linear_field(N // 2, L, W.sigma_lin, W.seed + 1, backend="torch", device=dev)
+    cases.append((f"{N // 2}^3 particles", N, synth.zeldovich_positions(dh, N // 2, L).contiguous()))
+    del dh
+    for label, mesh, P in cases:
+        s = recon.Solver(mesh, L, recon.RECON_MIXED)
+        autotune.apply(s, mesh, recon.RECON_MIXED)
+        for scheme in ("ngp", "cic", "tsc"):
+            rho = torch.zeros((mesh,) * 3, dtype=torch.float64, device=dev)
+            s.deposit(P, scheme, rho=rho)
+            if mesh == N and P is pos:
+                torch.cuda.synchronize()
+                a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                for _ in range(3):
+                    rho.zero_()
+                    s.deposit(P, scheme, rho=rho)
+                b_.record()
+                torch.cuda.synchronize()
+                out["deposit_ms"][scheme] = a.elapsed_time(b_) / 3
+            b = synth.smooth_and_floor(rho, L, R, fft_dtype=torch.float32)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, st = s.solve(b, tol=tol, max_cycles=40)
+            torch.cuda.synchronize()
+            out["convergence"].append({"particles": label, "mesh": f"{mesh}^3", "scheme": scheme,
+                                       "fas_cycles": st["cycles"], "outer": st["outer_iterations"],
+                                       "rel_residual": st["rel_residual"],
+                                       "solve_s": time.perf_counter() - t0})
+            del rho, b
+        s.close()
+    out["deposit_workload"] = f"{N}^3 particles on the {N}^3 mesh (mean 1)"
+    return out
 
 
 def bench_batch(recon, synth, torch, dev, count):

@@ -144,6 +144,20 @@ recon_status recon_set_config(recon_handle *h, const recon_config *cfg);
 recon_status recon_deposit_cic(recon_handle *h, const double *pos, long long n_part,
                                double mass, double *rho);
 
+/* Density assignment by nearest grid point, cloud in cell or triangular-
+ * shaped cloud (Sec. I footnote: the method works with any of the three).
+ * Cell i covers [i h, (i+1) h); along each axis u = x (N / L), i = floor(u)
+ * mod N, t = u - floor(u):
+ *   RECON_ASSIGN_NGP: mass on cell i;
+ *   RECON_ASSIGN_CIC: as recon_deposit_cic;
+ *   RECON_ASSIGN_TSC: the quadratic B-spline, weights (1 - t)^2 / 2,
+ *                     3/4 - (t - 1/2)^2, t^2 / 2 on cells i-1, i, i+1,
+ * times the product over the three axes.  pos, rho, mass and the errors as
+ * for recon_deposit_cic (rho is accumulated into). */
+typedef enum { RECON_ASSIGN_NGP = 0, RECON_ASSIGN_CIC = 1, RECON_ASSIGN_TSC = 2 } recon_assign;
+recon_status recon_deposit(recon_handle *h, recon_assign scheme, const double *pos, long long n_part,
+                           double mass, double *rho);
+
 /* Solve (*) (Sec. II.A: Gauss-Seidel relaxation of eq. update inside the
  * FAS V-cycles of eqs. PDE_H and corrections).
  * b:   device N^3, 1 + delta, every entry finite and > 0 (else RECON_E_DOMAIN).

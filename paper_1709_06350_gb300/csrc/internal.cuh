@@ -120,6 +120,9 @@ cudaError_t cic_cells(const double *pos, long long n, int N, double L, int *cell
                       double *frac, cudaStream_t s);
 cudaError_t cic_deposit(const double *pos, long long n, int N, double L, double mass,
                         double *rho, cudaStream_t s);
+// scheme: 0 NGP, 1 CIC, 2 TSC
+cudaError_t assign_deposit(int scheme, const double *pos, long long n, int N, double L, double mass,
+                           double *rho, cudaStream_t s);
 // ---- adjoint (recon_adjoint.cu)
 recon_status adjoint(recon_handle *H, const double *gbar, double *lam);
 void adj_free(recon_handle *H);

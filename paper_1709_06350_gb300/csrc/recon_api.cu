@@ -313,6 +313,20 @@ recon_status recon_deposit_cic(recon_handle *H, const double *pos, long long n_p
     return cuda_status(H, cic_deposit(pos, n_part, H->N, H->L, mass, rho, H->stream), "cic");
 }
 
+recon_status recon_deposit(recon_handle *H, recon_assign scheme, const double *pos, long long n_part,
+                           double mass, double *rho)
+{
+    if (!H) return RECON_E_INVALID;
+    if (scheme != RECON_ASSIGN_NGP && scheme != RECON_ASSIGN_CIC && scheme != RECON_ASSIGN_TSC)
+        return set_err(H, RECON_E_INVALID, "unknown assignment scheme");
+    if (n_part < 0 || (n_part > 0 && !pos) || !rho)
+        return set_err(H, RECON_E_INVALID, "bad particle count or NULL pointer");
+    if (n_part > 0 && !gpu_reachable(pos))
+        return set_err(H, RECON_E_INVALID, "pos must be device or page-locked host memory");
+    return cuda_status(H, assign_deposit((int)scheme, pos, n_part, H->N, H->L, mass, rho, H->stream),
+                       "deposit");
+}
+
 recon_status recon_solve(recon_handle *H, const double *b, double *phi, double tol, int max_cycles,
                          recon_stats *stats)
 {

@@ -188,6 +188,86 @@ cudaError_t cic_deposit(const double *pos, long long n, int N, double L, double 
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- NGP / TSC
+// Density assignment by nearest grid point or triangular-shaped cloud
+// (Sec. I footnote: the method works with NGP, CIC or TSC).  Along each
+// axis u = x N/L (FP64, one rounding), i = floor(u), t = u - i from the bits
+// of u; NGP puts the mass on cell i, TSC the quadratic B-spline weights
+//   (1 - t)^2 / 2,  3/4 - (t - 1/2)^2,  t^2 / 2   on cells i-1, i, i+1,
+// in 63-bit fixed point (the middle weight is one minus the other two,
+// exactly), corner weights (w_x w_y) w_z, converted to double by bit assembly.
+__device__ __forceinline__ void nearest_fixed(double x, int N, double inv_h, int &i, unsigned long long &t)
+{
+    const double u = __dmul_rn(x, inv_h);
+    if (!cic_fixed(u, N, i, t)) {   // far outside [0, L): the FP64 form
+        const double fl = floor(u);
+        const double tf = u - fl;
+        long long ii = (long long)fl % (long long)N;
+        if (ii < 0) ii += N;
+        i = (int)ii;
+        t = tf >= 1.0 ? ~0ull : (unsigned long long)ldexp(tf, 64);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_ngp_deposit(const double *__restrict__ pos, long long n, int N, double inv_h, double mass,
+              double *__restrict__ rho)
+{
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    int i[3];
+    for (int d = 0; d < 3; ++d) {
+        unsigned long long t;
+        nearest_fixed(pos[3 * p + d], N, inv_h, i[d], t);
+    }
+    atomicAdd(rho + offs(N, i[0], i[1], i[2]), mass);
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_tsc_deposit(const double *__restrict__ pos, long long n, int N, double inv_h, double mass,
+              double *__restrict__ rho)
+{
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    int c[3][3];
+    unsigned long long w[3][3];
+    for (int d = 0; d < 3; ++d) {
+        int i;
+        unsigned long long t;
+        nearest_fixed(pos[3 * p + d], N, inv_h, i, t);
+        const unsigned long long t63 = t >> 1, s63 = (1ull << 63) - t63;
+        w[d][0] = mul63(s63, s63) >> 1;
+        w[d][2] = mul63(t63, t63) >> 1;
+        w[d][1] = (1ull << 63) - w[d][0] - w[d][2];
+        c[d][0] = i == 0 ? N - 1 : i - 1;
+        c[d][1] = i;
+        c[d][2] = i + 1 == N ? 0 : i + 1;
+    }
+    const bool unit = mass == 1.0;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            const unsigned long long wab = mul63(w[0][a], w[1][b]);
+            const unsigned row = offs(N, c[0][a], c[1][b], 0);
+            for (int cc = 0; cc < 3; ++cc) {
+                const double v = fixed63_to_double(mul63(wab, w[2][cc]));
+                atomicAdd(rho + row + c[2][cc], unit ? v : __dmul_rn(mass, v));
+            }
+        }
+}
+
+cudaError_t assign_deposit(int scheme, const double *pos, long long n, int N, double L, double mass,
+                           double *rho, cudaStream_t s)
+{
+    if (scheme == 1) return cic_deposit(pos, n, N, L, mass, rho, s);
+    if (n == 0) return cudaSuccess;
+    note_launch();
+    if (scheme == 0)
+        k_ngp_deposit<<<blocks_for((size_t)n), kThreads, 0, s>>>(pos, n, N, (double)N / L, mass, rho);
+    else
+        k_tsc_deposit<<<blocks_for((size_t)n), kThreads, 0, s>>>(pos, n, N, (double)N / L, mass, rho);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- displace
 // Per Eulerian cell x_c: psi = -grad phi (central differences, FP64), the
 // mapped Lagrangian position q = x + grad phi (mod L), and

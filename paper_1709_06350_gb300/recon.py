@@ -65,6 +65,7 @@ _SIGS = {
     "recon_get_config": (_I, [_P, ctypes.POINTER(recon_config)]),
     "recon_set_config": (_I, [_P, ctypes.POINTER(recon_config)]),
     "recon_deposit_cic": (_I, [_P, _P, _LL, _D, _P]),
+    "recon_deposit": (_I, [_P, _I, _P, _LL, _D, _P]),
     "recon_solve": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(recon_stats)]),
     "recon_displace": (_I, [_P, _P, _P, _P, _P]),
     "recon_adjoint": (_I, [_P, _P, _P]),
@@ -186,6 +187,17 @@ def recon_deposit_cic(h, N: int, pos, mass: float, rho) -> None:
     n = pos.numel() // 3
     _check(load().recon_deposit_cic(h, _reachable_ptr(pos, torch.float64) if n else None, n,
                                     float(mass), _dev_ptr(rho, torch.float64, N ** 3)), h)
+
+
+ASSIGN = {"ngp": 0, "cic": 1, "tsc": 2}
+
+
+def recon_deposit(h, N: int, scheme, pos, mass: float, rho) -> None:
+    import torch
+    n = pos.numel() // 3
+    sc = ASSIGN[scheme] if isinstance(scheme, str) else int(scheme)
+    _check(load().recon_deposit(h, sc, _reachable_ptr(pos, torch.float64) if n else None, n,
+                                float(mass), _dev_ptr(rho, torch.float64, N ** 3)), h)
 
 
 def recon_solve(h, N: int, b, phi, tol: float, max_cycles: int, raise_on_noconv=True):
@@ -361,6 +373,18 @@ class Solver:
                               device=pos.device if pos.is_cuda else torch.device("cuda"))
         m = float(self.N) ** 3 / max(n, 1) if mass is None else float(mass)
         recon_deposit_cic(self.h, self.N, pos, m, rho)
+        return rho
+
+    def deposit(self, pos, scheme="cic", mass=None, rho=None):
+        """NGP / CIC / TSC density of pos (CUDA or pinned CPU tensor), mean 1
+        by default; accumulated into rho when given."""
+        import torch
+        n = pos.numel() // 3
+        if rho is None:
+            rho = torch.zeros((self.N,) * 3, dtype=torch.float64,
+                              device=pos.device if pos.is_cuda else torch.device("cuda"))
+        m = float(self.N) ** 3 / max(n, 1) if mass is None else float(mass)
+        recon_deposit(self.h, self.N, scheme, pos, m, rho)
         return rho
 
     def solve(self, b, phi=None, tol=1e-8, max_cycles=50, raise_on_noconv=True):
