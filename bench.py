@@ -46,6 +46,7 @@ def parse():
     p.add_argument("--no-batch", action="store_true")
     p.add_argument("--no-adjoint", action="store_true")
     p.add_argument("--no-assignment", action="store_true")
+    p.add_argument("--no-cubic", action="store_true")
     p.add_argument("--batch-count", type=int, default=64)
     p.add_argument("--adjoint-n", type=int, default=256)
     p.add_argument("--fd-directions", type=int, default=8)
@@ -380,6 +381,11 @@ def main():
         torch.cuda.empty_cache()
         assign = bench_assignment(recon, synth, torch, dev, pos, W, autotune)
 
+    cubic = None
+    if not args.no_cubic and rank == 0:
+        torch.cuda.empty_cache()
+        cubic = bench_cubic(recon, synth, torch, dev)
+
     adj = None
     if not args.no_adjoint and rank == 0:
         torch.cuda.empty_cache()
@@ -424,6 +430,7 @@ def main():
                               "linear field"},
             "batched": batch,
             "assignment": assign,
+            "cubic_test": cubic,
             "adjoint": adj,
             "gs_cell_updates_per_s": {"fas_newton": kern[1]["cell_updates_per_s"],
                                       "linear": roof.pop("cell_updates_per_s", None)},
@@ -479,6 +486,37 @@ def bench_assignment(recon, synth, torch, dev, pos, W, autotune):
             del rho, b
         s.close()
     out["deposit_workload"] = f"{N}^3 particles on the {N}^3 mesh (mean 1)"
+    return out
+
+
+def bench_cubic(recon, synth, torch, dev, tol=1e-3):
+    """Sec. III.A cubic test at the paper's sizes: 128^3 particles filling a
+    cube of side 10 Mpc/h at the centre of a 128 Mpc/h box, CIC on 128^3,
+    floor 0.05, no smoothing; FP64 and mixed solves to `tol`, and the
+    interior closed form lap(theta) = 3 (b_in^(1/3) - 1), Hbar = 0."""
+    N, L, l = 128, 128.0, 10.0
+    pos = torch.from_numpy(synth.cube_positions(N, L, l)).to(dev)
+    out = {"workload": f"{N}^3 particles in a {l:g} Mpc/h cube, box {L:g} Mpc/h, mesh {N}^3, "
+                       f"CIC, floor 0.05, tol {tol:g}"}
+    for name, dtype in (("fp64", recon.RECON_F64), ("mixed", recon.RECON_MIXED)):
+        s = recon.Solver(N, L, dtype)
+        b = synth.smooth_and_floor(s.deposit_cic(pos), L, 0.0)
+        phi = torch.zeros_like(b)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, st = s.solve(b, phi=phi, tol=tol, max_cycles=200, raise_on_noconv=False)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        c = N // 2
+        t = phi[c - 2:c + 2, c - 2:c + 2, c - 2:c + 2]
+        H = [(t.roll(-1, a) + t.roll(1, a) - 2 * t)[1:3, 1:3, 1:3] for a in range(3)]
+        lap = H[0] + H[1] + H[2]
+        expect = 3.0 * (float(b[c, c, c]) ** (1.0 / 3.0) - 1.0)
+        out[name] = {"seconds": dt, "cycles": st["cycles"], "outer": st["outer_iterations"],
+                     "rel_residual": st["rel_residual"], "lap_centre": float(lap.mean()),
+                     "lap_expected": expect,
+                     "hbar_max_rel": max(float((H[a] - lap / 3).abs().max()) for a in range(3)) / expect}
+        s.close()
     return out
 
 

@@ -178,6 +178,14 @@ def lattice_positions(N: int, L: float) -> np.ndarray:
     return np.ascontiguousarray(np.stack(q, axis=-1).reshape(-1, 3))
 
 
+def cube_positions(n: int, L: float, l: float) -> np.ndarray:
+    """The cubic test's particles: an n^3 lattice filling a cube of side l at
+    the centre of the box of side L (cell-centred sub-lattice), [n^3, 3]."""
+    s = (np.arange(n) + 0.5) * (l / n) + 0.5 * (L - l)
+    q = np.meshgrid(s, s, s, indexing="ij")
+    return np.ascontiguousarray(np.stack(q, axis=-1).reshape(-1, 3))
+
+
 def smooth_field(N: int, seed: int, amplitude: float, kmax: int = 3) -> np.ndarray:
     """A smooth periodic test field: a few random low-order Fourier modes.
 

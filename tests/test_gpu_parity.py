@@ -416,3 +416,32 @@ def test_convergence_with_tracer_and_mesh_ratios(R):
             counts[(label, scheme)] = st["cycles"] + st["outer_iterations"]
         s.close()
     assert max(counts.values()) - min(counts.values()) <= 2, counts
+
+
+# ------------------------------------------------------------------ cubic test
+def test_cubic_test(R, O):
+    """Sec. III.A cubic test at 64^3 (a cube of side 5 in a box of 64, the
+    paper's 10/128): after exactly 12 FAS cycles the FP64 GPU iterate equals
+    the oracle's; the mixed solve to 1e-3 has the interior closed form
+    lap(theta) = 3 (b_in^(1/3) - 1), Hbar = 0."""
+    from paper_1709_06350_gb300 import synth
+    N, L, l = 64, 64.0, 5.0
+    b = synth.smooth_and_floor(O.cic_deposit(synth.cube_positions(N, L, l), N, L), L, 0.0)
+    ref, info = O.solve(b, L, tol=1e-14, max_cycles=12)
+    s = R.Solver(N, L)
+    phi, st = s.solve(dev(b), tol=1e-14, max_cycles=12, raise_on_noconv=False)
+    assert st["cycles"] == info["cycles"] == 12
+    assert rel_l2(host(phi), ref) < 1e-9
+    s.close()
+    m = R.Solver(N, L, R.RECON_MIXED)
+    phim, stm = m.solve(dev(b), tol=1e-3, max_cycles=80)
+    assert stm["rel_residual"] < 1e-3
+    t = host(phim)
+    c = N // 2
+    H = [np.roll(t, -1, a) + np.roll(t, 1, a) - 2 * t for a in range(3)]
+    lap = sum(H)[c - 1:c + 1, c - 1:c + 1, c - 1:c + 1]
+    expect = 3.0 * (b[c, c, c] ** (1.0 / 3.0) - 1.0)
+    assert np.all(np.abs(lap / expect - 1.0) < 1e-3)
+    for a in range(3):
+        assert np.max(np.abs(H[a][c - 1:c + 1, c - 1:c + 1, c - 1:c + 1] - lap / 3.0)) < 1e-3 * expect
+    m.close()

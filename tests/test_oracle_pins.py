@@ -508,6 +508,27 @@ def test_adjoint_matches_finite_differences(O):
         assert np.sum(g * d) == pytest.approx(fd, rel=1e-6)
 
 
+# --------------------------------------------------------------- cubic test
+def test_cubic_test_interior(O):
+    """Sec. III.A cubic test, scaled: 32^3 particles filling a cube of side
+    2.5 at the centre of a 32^3 box (the paper's 10/128 ratio), CIC, floor.
+    Inside the cube the map is a uniform scaling: Hbar = 0 and lap(theta) =
+    3 (b_in^(1/3) - 1), the paper's 3 (L/l - 1) with the floor's mass taken
+    out of b_in."""
+    N, L, l = 32, 32.0, 2.5
+    b = synth.smooth_and_floor(O.cic_deposit(synth.cube_positions(N, L, l), N, L), L, 0.0)
+    t, info = O.solve(b, L, tol=1e-3, max_cycles=80)
+    assert info["status"] == 0
+    c = N // 2
+    H = [np.roll(t, -1, a) + np.roll(t, 1, a) - 2 * t for a in range(3)]   # h = 1
+    lap = sum(H)[c - 1:c + 1, c - 1:c + 1, c - 1:c + 1]
+    expect = 3.0 * (b[c, c, c] ** (1.0 / 3.0) - 1.0)
+    assert np.all(np.abs(lap / expect - 1.0) < 1e-3)
+    for a in range(3):
+        hbar = H[a][c - 1:c + 1, c - 1:c + 1, c - 1:c + 1] - lap / 3.0
+        assert np.max(np.abs(hbar)) < 1e-3 * expect
+
+
 # --------------------------------------------------------------- mutations
 MUTATIONS = {
     "edge-sign": ("- t[at(N, i - 1, j + 1, k)] - t[at(N, i + 1, j - 1, k)]) / q4;",
