@@ -367,3 +367,21 @@ def adjoint(theta, gbar_theta, h):
         if info != 0 or res > 1e-12:
             raise RuntimeError(f"oracle adjoint: GMRES did not converge (residual {res:.2e})")
     return sol[:n].reshape(N, N, N)
+
+
+# ---------------------------------------------------------------- post-processing
+def gaussianise(field):
+    """1-point Gaussianisation of a field (Sec. III, after Weinberg 1992 and
+    Neyrinck 2009), read as the rank mapping
+        g_i = mean + std * Phi^-1((rank_i + 1/2) / n),
+    rank_i the position of value i in ascending order with ties broken by
+    position (a stable sort), mean and std the input's (population std).
+    A library sort and scipy's ndtri are the steps.  Returns (g, rank)."""
+    from scipy.special import ndtri
+    f = _f64(field)
+    v = f.ravel()
+    order = np.argsort(v, kind="stable")
+    rank = np.empty(v.size, dtype=np.int64)
+    rank[order] = np.arange(v.size)
+    g = v.mean() + v.std() * ndtri((rank + 0.5) / v.size)
+    return g.reshape(f.shape), rank.reshape(f.shape)

@@ -529,6 +529,41 @@ def test_cubic_test_interior(O):
         assert np.max(np.abs(hbar)) < 1e-3 * expect
 
 
+# --------------------------------------------------------------- Gaussianisation
+def test_gaussianise_ranks_by_brute_force(O):
+    """Ranks against the counting definition #(v_j < v_i) + #(j < i, v_j == v_i),
+    with ties, both zero signs and negative values."""
+    rng = np.random.default_rng(41)
+    v = np.round(rng.standard_normal(300) * 3) / 2          # many ties
+    v[:4] = [0.0, -0.0, 0.0, -0.0]
+    _, rank = O.gaussianise(v)
+    for i in range(v.size):
+        assert rank[i] == np.sum(v < v[i]) + np.sum(v[:i] == v[i])
+
+
+def test_gaussianise_properties(O):
+    """The output keeps the input's order and mean, has the Gaussian
+    quantiles as its values, is invariant (after standardising) under a
+    monotonic map of the input, and leaves permuted Gaussian quantiles
+    unchanged up to their own mean and std."""
+    from scipy.special import ndtri
+    rng = np.random.default_rng(42)
+    v = rng.gamma(2.0, 1.0, (12, 12, 12)) - 2.0             # skewed
+    g, rank = O.gaussianise(v)
+    order = np.argsort(v, axis=None, kind="stable")
+    assert np.all(np.diff(g.ravel()[order]) > 0)
+    assert g.mean() == pytest.approx(v.mean(), abs=1e-12)
+    q = ndtri((np.arange(v.size) + 0.5) / v.size)
+    assert np.allclose(np.sort(g.ravel()), v.mean() + v.std() * q, atol=1e-12)
+    g2, _ = O.gaussianise(np.exp(v))
+    z = lambda a: (a - a.mean()) / a.std()
+    assert np.allclose(z(g2), z(g), atol=1e-12)
+    perm = rng.permutation(v.size)
+    w = q[perm]
+    gw, _ = O.gaussianise(w)
+    assert np.allclose(gw, w.mean() + w.std() * w, atol=1e-12)
+
+
 # --------------------------------------------------------------- mutations
 MUTATIONS = {
     "edge-sign": ("- t[at(N, i - 1, j + 1, k)] - t[at(N, i + 1, j - 1, k)]) / q4;",
