@@ -189,6 +189,17 @@ recon_status recon_solve(recon_handle *h, const double *b, double *phi, double t
 recon_status recon_displace(recon_handle *h, const double *phi, const double *b,
                             double *psi, double *deltaL);
 
+/* 1-point Gaussianisation of an N^3 field (Sec. III: tried on delta_r),
+ * read as the rank mapping
+ *     out_i = mean + std * Phi^-1((rank_i + 1/2) / N^3),
+ * rank_i the position of field_i in ascending order with ties broken by
+ * position (-0 equals +0), mean and std (population) of field.  field, out:
+ * device N^3, distinct; field must be finite.  The quantile is evaluated
+ * in FP32 (out carries ~1e-6 relative rounding).  The first call allocates
+ * 24 N^3 bytes of workspace, held by the handle until recon_destroy.
+ * Errors: RECON_E_INVALID, RECON_E_OOM, RECON_E_CUDA. */
+recon_status recon_gaussianise(recon_handle *h, const double *field, double *out);
+
 /* Adjoint of the last recon_solve on this handle (implicit-function theorem
  * on (*)): given gbar_phi = dLoss/dphi (device N^3), writes
  * gbar_b = dLoss/db (device N^3, zero-sum), i.e. lam with

@@ -13,6 +13,15 @@ constexpr int kFusedMinN = 128;       // grids of at least this size use the fus
 // Workspace of the adjoint (allocated at its first call): the potential of
 // every coarse level, the six cofactor arrays of every level, the iterate and
 // right side of every coarse level, the null vector of J^T.
+// workspace of recon_gaussianise (allocated at its first call)
+struct GaussWork {
+    size_t cap = 0;
+    unsigned long long *key[2] = {};
+    unsigned *idx[2] = {};
+    unsigned *counts = nullptr, *segsum = nullptr;
+    double *moments = nullptr;
+};
+
 struct AdjWork {
     bool ready = false;
     bool null_ready = false;   // cofactors and null vector match the last solve
@@ -56,6 +65,7 @@ struct recon_handle {
     bool have_solve = false;
 
     AdjWork adj;
+    GaussWork gauss;
     int adj_cycles = 0;
     double adj_rel = 0.0;
 
@@ -126,6 +136,9 @@ cudaError_t assign_deposit(int scheme, const double *pos, long long n, int N, do
 // ---- adjoint (recon_adjoint.cu)
 recon_status adjoint(recon_handle *H, const double *gbar, double *lam);
 void adj_free(recon_handle *H);
+cudaError_t gauss_alloc(recon_handle *H, size_t n);
+void gauss_free(recon_handle *H);
+cudaError_t gaussianise(recon_handle *H, const double *v, size_t n, double *g);
 
 // phi -> (hi, lo) FP32 parts (recon_mg.cu)
 __global__ void k_split_df(const double *__restrict__ a, float *__restrict__ hi, float *__restrict__ lo,

@@ -248,6 +248,7 @@ void recon_destroy(recon_handle *H)
     if (H->stream) cudaStreamSynchronize(H->stream);
     else cudaDeviceSynchronize();
     adj_free(H);
+    gauss_free(H);
     free_all(H);
     delete H;
 }
@@ -359,6 +360,14 @@ recon_status recon_displace(recon_handle *H, const double *phi, const double *b,
         return set_err(H, RECON_E_INVALID, "psi and deltaL must be device or page-locked host memory");
     return cuda_status(H, displace(H->N, H->L, phi, b, psi, deltaL, H->work64, H->work64b, H->stream),
                        "displace");
+}
+
+recon_status recon_gaussianise(recon_handle *H, const double *field, double *out)
+{
+    if (!H) return RECON_E_INVALID;
+    if (!field || !out) return set_err(H, RECON_E_INVALID, "NULL pointer");
+    if (field == out) return set_err(H, RECON_E_INVALID, "field and out must not alias");
+    return cuda_status(H, gaussianise(H, field, (size_t)H->N * H->N * H->N, out), "gaussianise");
 }
 
 recon_status recon_adjoint(recon_handle *H, const double *gbar_phi, double *gbar_b)

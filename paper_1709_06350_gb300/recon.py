@@ -69,6 +69,7 @@ _SIGS = {
     "recon_solve": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(recon_stats)]),
     "recon_displace": (_I, [_P, _P, _P, _P, _P]),
     "recon_adjoint": (_I, [_P, _P, _P]),
+    "recon_gaussianise": (_I, [_P, _P, _P]),
     "recon_last_error": (ctypes.c_char_p, [_P]),
     "recon_status_string": (ctypes.c_char_p, [_I]),
     "recon_kernel_launches": (ctypes.c_ulonglong, []),
@@ -218,6 +219,12 @@ def recon_displace(h, N: int, phi, b, psi, deltaL) -> None:
                                  _dev_ptr(b, torch.float64, N ** 3),
                                  _reachable_ptr(psi, torch.float64, 3 * N ** 3),
                                  _reachable_ptr(deltaL, torch.float64, N ** 3)), h)
+
+
+def recon_gaussianise(h, N: int, field, out) -> None:
+    import torch
+    _check(load().recon_gaussianise(h, _dev_ptr(field, torch.float64, N ** 3),
+                                    _dev_ptr(out, torch.float64, N ** 3)), h)
 
 
 def recon_adjoint(h, N: int, gbar_phi, gbar_b) -> None:
@@ -403,6 +410,13 @@ class Solver:
             dl = torch.empty_like(phi)
         recon_displace(self.h, self.N, phi, b, psi, dl)
         return psi, dl
+
+    def gaussianise(self, field):
+        """1-point Gaussianisation (rank mapping onto Gaussian quantiles)."""
+        import torch
+        out = torch.empty_like(field)
+        recon_gaussianise(self.h, self.N, field, out)
+        return out
 
     def adjoint(self, gbar_phi):
         import torch

@@ -445,3 +445,22 @@ def test_cubic_test(R, O):
     for a in range(3):
         assert np.max(np.abs(H[a][c - 1:c + 1, c - 1:c + 1, c - 1:c + 1] - lap / 3.0)) < 1e-3 * expect
     m.close()
+
+
+# ------------------------------------------------------------------ Gaussianisation
+@pytest.mark.parametrize("N", [16, 48, 64])
+def test_gaussianise_parity(R, O, N):
+    """The GPU radix sort's ranks equal a stable sort's (ties and both zero
+    signs included): the output orders exactly like the oracle's; values
+    agree to FP32 quantile rounding; a second call gives the same result."""
+    rng = np.random.default_rng(N)
+    v = np.round(rng.gamma(2.0, 1.0, (N,) * 3) * 64) / 64 - 2.0
+    v.ravel()[:3] = [0.0, -0.0, 0.0]
+    g_ref, _ = O.gaussianise(v)
+    s = R.Solver(N, float(N))
+    g = host(s.gaussianise(dev(v)))
+    assert np.max(np.abs(g - g_ref)) < 5e-6 * v.std()
+    assert np.array_equal(np.argsort(g, axis=None, kind="stable"),
+                          np.argsort(g_ref, axis=None, kind="stable"))
+    assert np.array_equal(host(s.gaussianise(dev(v))), g)
+    s.close()
