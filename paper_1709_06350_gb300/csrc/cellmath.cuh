@@ -170,6 +170,20 @@ __device__ __forceinline__ T root_polished(T p, T q)
     return sn;
 }
 
+// right of the cubic's local minimum: s > sqrt(-p/3).  FP32 tests the
+// equivalent s > 0 and 3 s^2 > -p (no square root); FP64 keeps the
+// square root of the definition.
+__device__ __forceinline__ bool right_of_min(double s, double p)
+{
+    return s > m_sqrt(p < 0.0 ? -p * (1.0 / 3.0) : 0.0);
+}
+__device__ __forceinline__ bool right_of_min(float s, float p) { return s > 0.0f && 3.0f * s * s > -p; }
+
+// the Newton quotient f / f': IEEE in FP64, the fast reciprocal form
+// (2 ulp) in the FP32 smoother, whose result the defect correction refines
+__device__ __forceinline__ double newton_quot(double f, double fp) { return f / fp; }
+__device__ __forceinline__ float newton_quot(float f, float fp) { return __fdividef(f, fp); }
+
 // Eq. update: theta_c - (h^2/6)(s_new - s).
 //   rule 1: s_new = largest root (the paper's update), Newton-polished;
 //   rule 0: one Newton step on the cubic from s, taken only right of the
@@ -178,12 +192,11 @@ template <typename T>
 __device__ __forceinline__ T point_update(T theta_c, T h2_6, T s, T p, T q, int rule)
 {
     T sn;
-    const T smin = m_sqrt(p < T(0) ? -p * T(1.0 / 3.0) : T(0));
     bool done = false;
-    if (rule == 0 && s > smin) {
+    if (rule == 0 && right_of_min(s, p)) {
         const T f = s * s * s + p * s + q;
         const T fp = T(3) * s * s + p;
-        sn = s - f / fp;
+        sn = s - newton_quot(f, fp);
         const T fn = sn * sn * sn + p * sn + q;
         done = m_abs(fn) <= m_abs(f);
     }
