@@ -659,7 +659,7 @@ def _time_launches(torch, stream, fn, reps):
 # (python bench.py --kernel-only 384); a launch at N^3 moves (N/384)^3 times
 # as much.  Valid for the kernels as they were captured: re-measure after a
 # change to either kernel.
-NCU_TRAFFIC_384 = {"LIN": 751.469312e6 + 208.285440e6, "FAS": 498.721280e6 + 201.100032e6}
+NCU_TRAFFIC_384 = {"LIN": 751.469312e6 + 208.285440e6, "FAS": 498.729216e6 + 200.596736e6}
 
 
 def kernel_roofline(recon, torch, N, L, dev, stream):
