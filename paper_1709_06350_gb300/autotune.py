@@ -22,7 +22,7 @@ CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "autotune_cache
 SPACE = {
     "nu1": (1, 2, 3),
     "nu2": (1, 2, 3),
-    "mixed_switch_rtol": (1e-3, 3e-4, 1e-4, 3e-5),
+    "mixed_switch_rtol": (1e-3, 3e-4, 2e-4, 1.5e-4, 1e-4, 3e-5),
     "mixed_linear_vcycles": (1, 2, 3, 4),
     "fused_chunk": (0, 16, 32, 64),
 }
