@@ -655,11 +655,11 @@ def _time_launches(torch, stream, fn, reps):
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
-# each fused smoother, from an ncu --set full capture of the 384^3 case
-# (python bench.py --kernel-only 384); a launch at N^3 moves (N/384)^3 times
-# as much.  Valid for the kernels as they were captured: re-measure after a
-# change to either kernel.
-NCU_TRAFFIC_384 = {"LIN": 751.469312e6 + 208.285440e6, "FAS": 498.729216e6 + 200.596736e6}
+# each fused smoother (the paired-FP32 kernels), from an ncu capture of the
+# 384^3 case (python bench.py --kernel-only 384; third launch of each); a
+# launch at N^3 moves (N/384)^3 times as much.  Valid for the kernels as they
+# were captured: re-measure after a change to either kernel.
+NCU_TRAFFIC_384 = {"LIN": 757.706496e6 + 207.453440e6, "FAS": 495.699968e6 + 199.885312e6}
 
 
 def kernel_roofline(recon, torch, N, L, dev, stream):

@@ -184,6 +184,22 @@ __device__ __forceinline__ bool right_of_min(float s, float p) { return s > 0.0f
 __device__ __forceinline__ double newton_quot(double f, double fp) { return f / fp; }
 __device__ __forceinline__ float newton_quot(float f, float fp) { return __fdividef(f, fp); }
 
+// keep the Newton step s_new = s - quot (quot = f / f') if |f(s_new)| <= |f(s)|.
+// FP64 evaluates f(s_new).  FP32 uses the same test in the cancellation-free
+// form: f(s + d) = f + f' d + 3 s d^2 + d^3 = d^2 (3 s + d) for d = -quot, so
+// the test is |d| |3 s + d| <= f'; recomputing f(s_new) in FP32 near
+// convergence gives rounding noise, which rejected good steps at random.
+__device__ __forceinline__ bool newton_keep(double s, double p, double q, double f, double, double sn,
+                                            double)
+{
+    const double fn = sn * sn * sn + p * sn + q;
+    return fabs(fn) <= fabs(f);
+}
+__device__ __forceinline__ bool newton_keep(float s, float, float, float, float fp, float, float quot)
+{
+    return fabsf(quot * (3.0f * s - quot)) <= fp;
+}
+
 // Eq. update: theta_c - (h^2/6)(s_new - s).
 //   rule 1: s_new = largest root (the paper's update), Newton-polished;
 //   rule 0: one Newton step on the cubic from s, taken only right of the
@@ -196,9 +212,9 @@ __device__ __forceinline__ T point_update(T theta_c, T h2_6, T s, T p, T q, int 
     if (rule == 0 && right_of_min(s, p)) {
         const T f = s * s * s + p * s + q;
         const T fp = T(3) * s * s + p;
-        sn = s - newton_quot(f, fp);
-        const T fn = sn * sn * sn + p * sn + q;
-        done = m_abs(fn) <= m_abs(f);
+        const T quot = newton_quot(f, fp);
+        sn = s - quot;
+        done = newton_keep(s, p, q, f, fp, sn, quot);
     }
     if (!done) sn = root_polished(p, q);
     return theta_c - h2_6 * (sn - s);

@@ -17,7 +17,10 @@
 #include <cmath>
 #include <cstdio>
 
+#include <type_traits>
+
 #include "cellmath.cuh"
+#include "cellmath2.cuh"
 #include "dfloat.cuh"
 #include "internal.cuh"
 
@@ -192,11 +195,16 @@ template <> struct Pair<float> { using type = float2; };
 template <> struct Pair<double> { using type = double2; };
 
 template <typename T, bool LIN>
-__global__ void __launch_bounds__(kFT, sizeof(T) == 8 ? 2 : (LIN ? 3 : 5))
+// CTAs per SM: FP64 2 (registers), linear 3 (shared memory), FP32 FAS 4
+// (64 registers for the paired updates without spills)
+__global__ void __launch_bounds__(kFT, sizeof(T) == 8 ? 2 : (LIN ? 3 : 4))
 k_sweep_fused(const T *__restrict__ src, T *__restrict__ dst, const T *__restrict__ g,
               const T *__restrict__ th, const double *__restrict__ cptr, double cval, int N,
               int CI, T ih2, T h2_6, int rule)
 {
+    // FP32: a thread's two rows 8 apart are relaxed together with paired
+    // FP32 instructions (cellmath2.cuh); FP64 relaxes them one by one
+    constexpr bool kPaired = std::is_same<T, float>::value;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sm = reinterpret_cast<T *>(smem_raw);
     const T c = LIN ? T(0) : (T)(cptr ? *cptr : cval);
@@ -252,8 +260,25 @@ k_sweep_fused(const T *__restrict__ src, T *__restrict__ dst, const T *__restric
         const int S0 = (w + 1) * kOR + (pr ^ 1) * kOH + lane + pr;
         const int O0 = (w + 1) * kOR + pr * kOH + lane;
         const unsigned gc = pb + (pr ? gcol1 : gcol0);
+        if constexpr (kPaired) {
+            // RED rows w and w + 8 as one pair of paired-FP32 updates
+            constexpr int D = 8 * kOR;
+            const Nb19<float2> nb = pack19(gather19<T>(sm, om, oc, op, S0, O0),
+                                           gather19<T>(sm, om, oc, op, S0 + D, O0 + D));
+            const float2 rhs = make_float2(g[gc + grow[0]], g[gc + grow[1]]);
+            float2 v;
+            if constexpr (LIN) {
+                v = lin_update2(pack19(gather19<T>(sm + kThBase, om, oc, op, S0, O0),
+                                       gather19<T>(sm + kThBase, om, oc, op, S0 + D, O0 + D)),
+                                nb, rhs, ih2, T(6) * h2_6);
+            } else {
+                v = fas_update2(nb, add2(rhs, f2(c)), ih2, h2_6, rule);
+            }
+            sm[rs + w * kRH + lane] = v.x;
+            sm[rs + (w + 8) * kRH + lane] = v.y;
+        }
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
+        for (int i = kPaired ? 2 : 0; i < 3; ++i) {
             if (i == 2 && w >= kRJ - 2 * kWarps) break;
             const int S = S0 + 8 * i * kOR, O = O0 + 8 * i * kOR;
             const Nb19<T> nb = gather19<T>(sm, om, oc, op, S, O);
@@ -293,30 +318,67 @@ k_sweep_fused(const T *__restrict__ src, T *__restrict__ dst, const T *__restric
         const int Q0 = (w + 1) * kRH + lane;
         const unsigned sb = (unsigned)s * NN;
         const int gk0 = k0 + 2 * lane;
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            const int gj = j0 + w + 8 * i;
-            if (gj >= N || gk0 >= N) continue;
-            const int S = S0 + 8 * i * kOR, O = O0 + 8 * i * kOR, Q = Q0 + 8 * i * kRH;
-            Nb19<T> nb = gather19<T>(sm, om, oc, op, S, O);
-            nb.xp = sm[rp + Q + pb];
-            nb.xm = sm[rm + Q + pb];
-            nb.yp = sm[rc + Q + kRH + pb];
-            nb.ym = sm[rc + Q - kRH + pb];
-            nb.zp = sm[rc + Q + 1];
-            nb.zm = sm[rc + Q];
-            const unsigned gb = sb + (unsigned)gj * (unsigned)N + (unsigned)gk0;
-            T vb;
+        if constexpr (kPaired) {
+            // tile rows w and w + 8 as one pair of paired-FP32 updates; a
+            // row or column outside the grid (ragged tile) is computed from
+            // the wrapped halo values but neither read from g nor stored
+            constexpr int D = 8 * kOR, DR = 8 * kRH;
+            const int gj = j0 + w;
+            const bool in0 = gk0 < N && gj < N, in1 = gk0 < N && gj + 8 < N;
+            Nb19<T> a = gather19<T>(sm, om, oc, op, S0, O0);
+            Nb19<T> b = gather19<T>(sm, om, oc, op, S0 + D, O0 + D);
+            a.xp = sm[rp + Q0 + pb];
+            a.xm = sm[rm + Q0 + pb];
+            a.yp = sm[rc + Q0 + kRH + pb];
+            a.ym = sm[rc + Q0 - kRH + pb];
+            a.zp = sm[rc + Q0 + 1];
+            a.zm = sm[rc + Q0];
+            b.xp = sm[rp + Q0 + DR + pb];
+            b.xm = sm[rm + Q0 + DR + pb];
+            b.yp = sm[rc + Q0 + DR + kRH + pb];
+            b.ym = sm[rc + Q0 + DR - kRH + pb];
+            b.zp = sm[rc + Q0 + DR + 1];
+            b.zm = sm[rc + Q0 + DR];
+            const unsigned gb0 = sb + (unsigned)gj * (unsigned)N + (unsigned)gk0;
+            const unsigned gb1 = gb0 + 8u * (unsigned)N;
+            const float2 rhs = make_float2(in0 ? g[gb0 + pb] : T(1), in1 ? g[gb1 + pb] : T(1));
+            float2 vb;
             if constexpr (LIN) {
-                vb = lin_update<T>(gather19<T>(sm + kThBase, om, oc, op, S, O), nb, g[gb + pb], ih2);
+                vb = lin_update2(pack19(gather19<T>(sm + kThBase, om, oc, op, S0, O0),
+                                        gather19<T>(sm + kThBase, om, oc, op, S0 + D, O0 + D)),
+                                 pack19(a, b), rhs, ih2, T(6) * h2_6);
             } else {
-                vb = fas_update<T>(nb, g[gb + pb] + c, ih2, h2_6, rule);
+                vb = fas_update2(pack19(a, b), add2(rhs, f2(c)), ih2, h2_6, rule);
             }
-            const T vr = sm[rc + Q + 1 - pb];
-            typename Pair<T>::type v;
-            v.x = pb ? vr : vb;
-            v.y = pb ? vb : vr;
-            *reinterpret_cast<typename Pair<T>::type *>(dst + gb) = v;
+            const T vr0 = sm[rc + Q0 + 1 - pb], vr1 = sm[rc + Q0 + DR + 1 - pb];
+            if (in0) *reinterpret_cast<float2 *>(dst + gb0) = pb ? make_float2(vr0, vb.x) : make_float2(vb.x, vr0);
+            if (in1) *reinterpret_cast<float2 *>(dst + gb1) = pb ? make_float2(vr1, vb.y) : make_float2(vb.y, vr1);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int gj = j0 + w + 8 * i;
+                if (gj >= N || gk0 >= N) continue;
+                const int S = S0 + 8 * i * kOR, O = O0 + 8 * i * kOR, Q = Q0 + 8 * i * kRH;
+                Nb19<T> nb = gather19<T>(sm, om, oc, op, S, O);
+                nb.xp = sm[rp + Q + pb];
+                nb.xm = sm[rm + Q + pb];
+                nb.yp = sm[rc + Q + kRH + pb];
+                nb.ym = sm[rc + Q - kRH + pb];
+                nb.zp = sm[rc + Q + 1];
+                nb.zm = sm[rc + Q];
+                const unsigned gb = sb + (unsigned)gj * (unsigned)N + (unsigned)gk0;
+                T vb;
+                if constexpr (LIN) {
+                    vb = lin_update<T>(gather19<T>(sm + kThBase, om, oc, op, S, O), nb, g[gb + pb], ih2);
+                } else {
+                    vb = fas_update<T>(nb, g[gb + pb] + c, ih2, h2_6, rule);
+                }
+                const T vr = sm[rc + Q + 1 - pb];
+                typename Pair<T>::type v;
+                v.x = pb ? vr : vb;
+                v.y = pb ? vb : vr;
+                *reinterpret_cast<typename Pair<T>::type *>(dst + gb) = v;
+            }
         }
     };
 
@@ -1213,7 +1275,7 @@ static cudaError_t lin_sweep(int N, double h, float *e, const float *f, const fl
         float *a = e, *b = work;
         for (int it = 0; it < sweeps; ++it) {
             const cudaError_t err = fused_sweep_launch<float, true>(N, a, b, f, th, nullptr, 0.0, ih2,
-                                                                   0.0f, 0, s);
+                                                                   (float)(h * h / 6.0), 0, s);
             if (err != cudaSuccess) return err;
             float *tmp = a;
             a = b;
