@@ -659,7 +659,7 @@ def _time_launches(torch, stream, fn, reps):
 # 384^3 case (python bench.py --kernel-only 384; third launch of each); a
 # launch at N^3 moves (N/384)^3 times as much.  Valid for the kernels as they
 # were captured: re-measure after a change to either kernel.
-NCU_TRAFFIC_384 = {"LIN": 757.706496e6 + 207.453440e6, "FAS": 495.699968e6 + 199.885312e6}
+NCU_TRAFFIC_384 = {"LIN": 756.065280e6 + 208.592384e6, "FAS": 495.699968e6 + 199.885312e6}
 
 
 def kernel_roofline(recon, torch, N, L, dev, stream):

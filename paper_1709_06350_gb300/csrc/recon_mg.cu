@@ -69,9 +69,11 @@ k_rb_pass(const T *__restrict__ src, T *__restrict__ dst, const T *__restrict__ 
 //   OLD  ring of 6 planes of src, tile + 2-cell halo.  Each row is stored
 //        colour-split: the cells of even k first, then those of odd k, so
 //        that a warp reading one neighbour of 32 same-colour cells reads 32
-//        consecutive words (no bank conflicts).
+//        consecutive words (no bank conflicts).  The linear variant (LIN)
+//        stores an (e, theta) pair per position instead (e at float 2x,
+//        theta at 2x + 1): one 64-bit load brings both operands of a
+//        neighbour.
 //   RED  ring of 4 planes holding only the new red values, tile + 1 halo.
-//   TH   (linear variant) ring of 6 planes of theta, laid out like OLD.
 //
 // Step s (one barrier): the red cells of plane s+2 (they read only OLD) and
 // the black cells of plane s (faces from RED planes s-1..s+1, edges and
@@ -102,8 +104,11 @@ constexpr int kOPlane = kOJ * kOR;           // 1360 elements per OLD / TH plane
 constexpr int kRPlane = kRJ * kRH;           // 594 elements per RED plane
 constexpr int kLoadsPerThread = (kOPlane + kFT - 1) / kFT;   // 6
 constexpr int kOSlots = 6, kRSlots = 4;
-constexpr int kRedBase = kOSlots * kOPlane;  // RED ring after the OLD ring
-constexpr int kThBase = kRedBase + kRSlots * kRPlane;        // TH ring after RED
+// The OLD ring holds one value per position (FAS) or an (e, theta) pair per
+// position (LIN: e at float 2x, theta at 2x + 1, so one 64-bit load brings
+// both operands of a neighbour); the RED ring follows it.
+template <bool LIN>
+__host__ __device__ constexpr int red_base() { return (LIN ? 2 : 1) * kOSlots * kOPlane; }
 static_assert(kTK / 2 == 32 && kRH == 33 && kWarps == 8 && kTJ == 2 * kWarps,
               "warp w owns tile rows w and w + 8 and red index = lane");
 static_assert(kRJ - 2 * kWarps == 2, "RED rows 16 and 17 go to warps 0 and 1");
@@ -111,7 +116,7 @@ static_assert(kRJ - 2 * kWarps == 2, "RED rows 16 and 17 go to warps 0 and 1");
 template <typename T, bool LIN>
 constexpr size_t fused_smem_bytes()
 {
-    return sizeof(T) * (size_t)(kThBase + (LIN ? kOSlots * kOPlane : 0));
+    return sizeof(T) * (size_t)(red_base<LIN>() + kRSlots * kRPlane);
 }
 
 __device__ __forceinline__ int wrap1(int x, int N) { return x < 0 ? x + N : (x >= N ? x - N : x); }
@@ -170,6 +175,39 @@ __device__ __forceinline__ Nb19<T> gather19(const T *sm, int pm, int pc, int pp,
     return v;
 }
 
+// (e, theta) of the 19-point neighbourhood from the linear smoother's
+// interleaved OLD ring (position x: e at float 2x, theta at 2x + 1); same
+// positions as gather19.
+__device__ __forceinline__ void gather19_il(const float *sm, int pm, int pc, int pp, int S, int O,
+                                            Nb19<float> &e, Nb19<float> &t)
+{
+    const float2 *s2 = reinterpret_cast<const float2 *>(sm);
+    auto ld = [&](int x, float &ev, float &tv) {
+        const float2 v = s2[x];
+        ev = v.x;
+        tv = v.y;
+    };
+    ld(pc + S, e.c, t.c);
+    ld(pp + S, e.xp, t.xp);
+    ld(pm + S, e.xm, t.xm);
+    ld(pc + S + kOR, e.yp, t.yp);
+    ld(pc + S - kOR, e.ym, t.ym);
+    ld(pc + O + 1, e.zp, t.zp);
+    ld(pc + O, e.zm, t.zm);
+    ld(pp + S + kOR, e.xpyp, t.xpyp);
+    ld(pm + S - kOR, e.xmym, t.xmym);
+    ld(pm + S + kOR, e.xmyp, t.xmyp);
+    ld(pp + S - kOR, e.xpym, t.xpym);
+    ld(pc + O + kOR + 1, e.ypzp, t.ypzp);
+    ld(pc + O - kOR, e.ymzm, t.ymzm);
+    ld(pc + O - kOR + 1, e.ymzp, t.ymzp);
+    ld(pc + O + kOR, e.ypzm, t.ypzm);
+    ld(pp + O + 1, e.xpzp, t.xpzp);
+    ld(pm + O, e.xmzm, t.xmzm);
+    ld(pm + O + 1, e.xmzp, t.xmzp);
+    ld(pp + O, e.xpzm, t.xpzm);
+}
+
 // The nonlinear cell update (eq. update).
 template <typename T>
 __device__ __forceinline__ T fas_update(const Nb19<T> &nb, T rhs, T ih2, T h2_6, int rule)
@@ -225,15 +263,20 @@ k_sweep_fused(const T *__restrict__ src, T *__restrict__ dst, const T *__restric
         goff[t] = (unsigned)wrap1(j0 - 2 + (r < kOJ ? r : 0), N) * (unsigned)N +
                   (unsigned)wrap1(k0 - 2 + q, N);
     }
-    auto issue_plane = [&](int slot, int p) {   // slot: element offset of an OLD plane
+    auto issue_plane = [&](int slot, int p) {   // slot: position offset of an OLD plane
         const unsigned pb = (unsigned)wrap1(p, N) * NN;
-#pragma unroll
-        for (int t = 0; t < kLoadsPerThread; ++t)
-            if (soff[t] >= 0) cp_async_elem(sm + slot + soff[t], src + pb + goff[t]);
         if constexpr (LIN) {
 #pragma unroll
             for (int t = 0; t < kLoadsPerThread; ++t)
-                if (soff[t] >= 0) cp_async_elem(sm + kThBase + slot + soff[t], th + pb + goff[t]);
+                if (soff[t] >= 0) {
+                    T *d = sm + 2 * (slot + soff[t]);
+                    cp_async_elem(d, src + pb + goff[t]);
+                    cp_async_elem(d + 1, th + pb + goff[t]);
+                }
+        } else {
+#pragma unroll
+            for (int t = 0; t < kLoadsPerThread; ++t)
+                if (soff[t] >= 0) cp_async_elem(sm + slot + soff[t], src + pb + goff[t]);
         }
         cp_async_commit();
     };
@@ -263,15 +306,16 @@ k_sweep_fused(const T *__restrict__ src, T *__restrict__ dst, const T *__restric
         if constexpr (kPaired) {
             // RED rows w and w + 8 as one pair of paired-FP32 updates
             constexpr int D = 8 * kOR;
-            const Nb19<float2> nb = pack19(gather19<T>(sm, om, oc, op, S0, O0),
-                                           gather19<T>(sm, om, oc, op, S0 + D, O0 + D));
             const float2 rhs = make_float2(g[gc + grow[0]], g[gc + grow[1]]);
             float2 v;
             if constexpr (LIN) {
-                v = lin_update2(pack19(gather19<T>(sm + kThBase, om, oc, op, S0, O0),
-                                       gather19<T>(sm + kThBase, om, oc, op, S0 + D, O0 + D)),
-                                nb, rhs, ih2, T(6) * h2_6);
+                Nb19<T> ea, ta, eb, tb;
+                gather19_il(sm, om, oc, op, S0, O0, ea, ta);
+                gather19_il(sm, om, oc, op, S0 + D, O0 + D, eb, tb);
+                v = lin_update2(pack19(ta, tb), pack19(ea, eb), rhs, ih2, T(6) * h2_6);
             } else {
+                const Nb19<float2> nb = pack19(gather19<T>(sm, om, oc, op, S0, O0),
+                                               gather19<T>(sm, om, oc, op, S0 + D, O0 + D));
                 v = fas_update2(nb, add2(rhs, f2(c)), ih2, h2_6, rule);
             }
             sm[rs + w * kRH + lane] = v.x;
@@ -281,13 +325,14 @@ k_sweep_fused(const T *__restrict__ src, T *__restrict__ dst, const T *__restric
         for (int i = kPaired ? 2 : 0; i < 3; ++i) {
             if (i == 2 && w >= kRJ - 2 * kWarps) break;
             const int S = S0 + 8 * i * kOR, O = O0 + 8 * i * kOR;
-            const Nb19<T> nb = gather19<T>(sm, om, oc, op, S, O);
             const T rhs = g[gc + grow[i]];
             T v;
             if constexpr (LIN) {
-                v = lin_update<T>(gather19<T>(sm + kThBase, om, oc, op, S, O), nb, rhs, ih2);
+                Nb19<T> e, t;
+                gather19_il(sm, om, oc, op, S, O, e, t);
+                v = lin_update<T>(t, e, rhs, ih2);
             } else {
-                v = fas_update<T>(nb, rhs + c, ih2, h2_6, rule);
+                v = fas_update<T>(gather19<T>(sm, om, oc, op, S, O), rhs + c, ih2, h2_6, rule);
             }
             sm[rs + (w + 8 * i) * kRH + lane] = v;
         }
@@ -295,13 +340,14 @@ k_sweep_fused(const T *__restrict__ src, T *__restrict__ dst, const T *__restric
             const int r = lane, prc = (p + j0 + r) & 1, h = kRH - 1;
             const int S = (r + 1) * kOR + (prc ^ 1) * kOH + h + prc;
             const int O = (r + 1) * kOR + prc * kOH + h;
-            const Nb19<T> nb = gather19<T>(sm, om, oc, op, S, O);
             const T rhs = g[pb + crow + (prc ? ccol1 : ccol0)];
             T v;
             if constexpr (LIN) {
-                v = lin_update<T>(gather19<T>(sm + kThBase, om, oc, op, S, O), nb, rhs, ih2);
+                Nb19<T> e, t;
+                gather19_il(sm, om, oc, op, S, O, e, t);
+                v = lin_update<T>(t, e, rhs, ih2);
             } else {
-                v = fas_update<T>(nb, rhs + c, ih2, h2_6, rule);
+                v = fas_update<T>(gather19<T>(sm, om, oc, op, S, O), rhs + c, ih2, h2_6, rule);
             }
             sm[rs + r * kRH + h] = v;
         }
@@ -325,8 +371,14 @@ k_sweep_fused(const T *__restrict__ src, T *__restrict__ dst, const T *__restric
             constexpr int D = 8 * kOR, DR = 8 * kRH;
             const int gj = j0 + w;
             const bool in0 = gk0 < N && gj < N, in1 = gk0 < N && gj + 8 < N;
-            Nb19<T> a = gather19<T>(sm, om, oc, op, S0, O0);
-            Nb19<T> b = gather19<T>(sm, om, oc, op, S0 + D, O0 + D);
+            Nb19<T> a, b, ta, tb;   // ta, tb: theta (linear smoother)
+            if constexpr (LIN) {
+                gather19_il(sm, om, oc, op, S0, O0, a, ta);
+                gather19_il(sm, om, oc, op, S0 + D, O0 + D, b, tb);
+            } else {
+                a = gather19<T>(sm, om, oc, op, S0, O0);
+                b = gather19<T>(sm, om, oc, op, S0 + D, O0 + D);
+            }
             a.xp = sm[rp + Q0 + pb];
             a.xm = sm[rm + Q0 + pb];
             a.yp = sm[rc + Q0 + kRH + pb];
@@ -344,9 +396,7 @@ k_sweep_fused(const T *__restrict__ src, T *__restrict__ dst, const T *__restric
             const float2 rhs = make_float2(in0 ? g[gb0 + pb] : T(1), in1 ? g[gb1 + pb] : T(1));
             float2 vb;
             if constexpr (LIN) {
-                vb = lin_update2(pack19(gather19<T>(sm + kThBase, om, oc, op, S0, O0),
-                                        gather19<T>(sm + kThBase, om, oc, op, S0 + D, O0 + D)),
-                                 pack19(a, b), rhs, ih2, T(6) * h2_6);
+                vb = lin_update2(pack19(ta, tb), pack19(a, b), rhs, ih2, T(6) * h2_6);
             } else {
                 vb = fas_update2(pack19(a, b), add2(rhs, f2(c)), ih2, h2_6, rule);
             }
@@ -359,7 +409,12 @@ k_sweep_fused(const T *__restrict__ src, T *__restrict__ dst, const T *__restric
                 const int gj = j0 + w + 8 * i;
                 if (gj >= N || gk0 >= N) continue;
                 const int S = S0 + 8 * i * kOR, O = O0 + 8 * i * kOR, Q = Q0 + 8 * i * kRH;
-                Nb19<T> nb = gather19<T>(sm, om, oc, op, S, O);
+                Nb19<T> nb, nt;   // nt: theta (linear smoother)
+                if constexpr (LIN) {
+                    gather19_il(sm, om, oc, op, S, O, nb, nt);
+                } else {
+                    nb = gather19<T>(sm, om, oc, op, S, O);
+                }
                 nb.xp = sm[rp + Q + pb];
                 nb.xm = sm[rm + Q + pb];
                 nb.yp = sm[rc + Q + kRH + pb];
@@ -369,7 +424,7 @@ k_sweep_fused(const T *__restrict__ src, T *__restrict__ dst, const T *__restric
                 const unsigned gb = sb + (unsigned)gj * (unsigned)N + (unsigned)gk0;
                 T vb;
                 if constexpr (LIN) {
-                    vb = lin_update<T>(gather19<T>(sm + kThBase, om, oc, op, S, O), nb, g[gb + pb], ih2);
+                    vb = lin_update<T>(nt, nb, g[gb + pb], ih2);
                 } else {
                     vb = fas_update<T>(nb, g[gb + pb] + c, ih2, h2_6, rule);
                 }
@@ -389,12 +444,13 @@ k_sweep_fused(const T *__restrict__ src, T *__restrict__ dst, const T *__restric
     cp_async_wait<0>();
     __syncthreads();
     if (i0 + 3 <= i1 + 1) issue_plane(5 * kOPlane, i0 + 3);
-    red_plane(i0 - 1, 0 * kOPlane, 1 * kOPlane, 2 * kOPlane, kRedBase + 0 * kRPlane);
-    red_plane(i0, 1 * kOPlane, 2 * kOPlane, 3 * kOPlane, kRedBase + 1 * kRPlane);
-    red_plane(i0 + 1, 2 * kOPlane, 3 * kOPlane, 4 * kOPlane, kRedBase + 2 * kRPlane);
+    constexpr int kRB = red_base<LIN>();
+    red_plane(i0 - 1, 0 * kOPlane, 1 * kOPlane, 2 * kOPlane, kRB + 0 * kRPlane);
+    red_plane(i0, 1 * kOPlane, 2 * kOPlane, 3 * kOPlane, kRB + 1 * kRPlane);
+    red_plane(i0 + 1, 2 * kOPlane, 3 * kOPlane, 4 * kOPlane, kRB + 2 * kRPlane);
     // ring slots of OLD planes s-1 .. s+4 and RED planes s-1 .. s+2
     int o0 = 1 * kOPlane, o1 = 2 * kOPlane, o2 = 3 * kOPlane, o3 = 4 * kOPlane, o4 = 5 * kOPlane, o5 = 0;
-    int q0 = kRedBase, q1 = kRedBase + kRPlane, q2 = kRedBase + 2 * kRPlane, q3 = kRedBase + 3 * kRPlane;
+    int q0 = kRB, q1 = kRB + kRPlane, q2 = kRB + 2 * kRPlane, q3 = kRB + 3 * kRPlane;
     for (int s = i0; s < i1; ++s) {
         cp_async_wait<0>();   // this thread's copies of plane s+3 have landed
         __syncthreads();      // everyone's; RED s+1 written; slots of planes s-2 free
