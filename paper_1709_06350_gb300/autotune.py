@@ -8,7 +8,6 @@ nothing itself.
 """
 from __future__ import annotations
 
-import itertools
 import json
 import os
 import time
@@ -18,7 +17,8 @@ from . import recon, synth
 # tuned schedules, keyed by GPU name, grid size and dtype (written by tune())
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "autotune_cache.json")
 
-# candidate values; the search is a coordinate descent from the defaults
+# candidate values; the search is a coordinate descent from the cached
+# config for the same GPU, N and dtype, else from the defaults
 SPACE = {
     "nu1": (1, 2, 3),
     "nu2": (1, 2, 3),
@@ -70,43 +70,70 @@ def _time(solver, b, tol, reps):
     return best, st
 
 
+def descend(measure, start: dict, space: dict = SPACE, rounds: int = 2, verbose: bool = False):
+    """Coordinate descent over `space` from `start`.  measure(cfg) returns
+    (seconds, converged) or None when the config is rejected; a candidate is
+    kept only if it converged and is faster than the best so far, so the
+    result is never slower than `start`.  Returns (best_cfg, best_seconds,
+    number of configs measured)."""
+    best_cfg = dict(start)
+    m = measure(best_cfg)
+    if m is None or not m[1]:
+        raise ValueError("the starting config does not converge")
+    best_t, n = m[0], 1
+    for _ in range(rounds):
+        improved = False
+        for k, values in space.items():
+            for v in values:
+                if v == best_cfg[k]:
+                    continue
+                cand = dict(best_cfg, **{k: v})
+                if cand.get("nu1", 1) + cand.get("nu2", 1) < 1:
+                    continue
+                m = measure(cand)
+                if m is None:
+                    continue
+                n += 1
+                if verbose:
+                    print(f"  {cand} -> {m[0] * 1e3:.2f} ms")
+                if m[1] and m[0] < best_t:
+                    best_t, best_cfg, improved = m[0], cand, True
+        if not improved:
+            break
+    return best_cfg, best_t, n
+
+
 def tune(N: int, L: float | None = None, dtype: int = recon.RECON_MIXED, tol: float = 1e-8,
          reps: int = 2, path: str = CACHE, rounds: int = 2, verbose: bool = False) -> dict:
-    """Coordinate descent over SPACE; returns and caches the best config."""
+    """Coordinate descent over SPACE, started from the cached config for this
+    (GPU, N, dtype) when there is one (else from the defaults), so a re-tune
+    never replaces a schedule with a slower one; returns and caches the best."""
     import torch
     L = float(L if L is not None else N)
     b = _field(N, L, 9000 + N, torch.device("cuda", 0))
     solver = recon.Solver(N, L, dtype)
     base = solver.config()
-    best_cfg = {k: base[k] for k in SPACE}
-    best_t, _ = _time(solver, b, tol, reps)
-    trials = [(dict(best_cfg), best_t)]
-    for _ in range(rounds):
-        improved = False
-        for k, values in SPACE.items():
-            for v in values:
-                if v == best_cfg[k]:
-                    continue
-                cand = dict(best_cfg, **{k: v})
-                if cand["nu1"] + cand["nu2"] < 1:
-                    continue
-                solver.configure(**cand)
-                try:
-                    t, st = _time(solver, b, tol, reps)
-                except recon.ReconError:
-                    continue
-                trials.append((cand, t))
-                if verbose:
-                    print(f"  {cand} -> {t * 1e3:.2f} ms")
-                if st["rel_residual"] < tol and t < best_t:
-                    best_t, best_cfg, improved = t, cand, True
-            solver.configure(**best_cfg)
-        if not improved:
-            break
+    defaults = {k: base[k] for k in SPACE}
+
+    def measure(cfg):
+        solver.configure(**cfg)
+        try:
+            t, st = _time(solver, b, tol, reps)
+        except recon.ReconError:
+            return None
+        return t, st["rel_residual"] < tol
+
+    m = measure(defaults)
+    default_t = m[0] if m is not None else float("inf")
+    start = cached_config(N, dtype, path) or defaults
+    try:
+        best_cfg, best_t, n = descend(measure, start, SPACE, rounds, verbose)
+    except ValueError:   # a cached schedule that no longer converges
+        best_cfg, best_t, n = descend(measure, defaults, SPACE, rounds, verbose)
     solver.close()
     cache = load_cache(path)
-    cache[_key(N, dtype)] = {"config": best_cfg, "seconds": best_t, "trials": len(trials),
-                             "default_seconds": trials[0][1]}
+    cache[_key(N, dtype)] = {"config": best_cfg, "seconds": best_t, "trials": n + 1,
+                             "default_seconds": default_t}
     os.makedirs(os.path.dirname(path), exist_ok=True)
     with open(path, "w") as f:
         json.dump(cache, f, indent=1)
