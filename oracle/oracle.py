@@ -305,6 +305,100 @@ def displace(theta, b, L):
     return psi, dl
 
 
+def displace_adjoint(theta, b, L, gbar_psi=None, gbar_dl=None):
+    """Adjoint of ``displace`` (Sec. II.B as restated there): given the
+    gradients of a loss with respect to psi [3,N,N,N] and delta_r [N,N,N]
+    (None = zero), return its gradients with respect to theta and b.
+
+    The forward map, cell c at x_c = (i + 1/2) h:
+      g_c = central-difference gradient of theta,  psi_c = -g_c,
+      q_c = x_c + g_c (mod L),  A_c = I + H_c theta,  v_c = 3 - tr(A_c^-1),
+      num = CIC(q, b v),  den = CIC(q, b),  delta_r = num / max(den, 1e-12).
+    Chain rule, in reverse order (plain FP64 numpy; the CIC cells and
+    fractions come from ``cic_cells``, the same formula as the forward):
+      gN = gbar_dl / max(den, eps),  gD = -gbar_dl num / den^2 (den > eps),
+      per cell: gwv = sum_corners gN W,  gwb = sum_corners gD W,
+                gq_d = sum_corners (b v gN + b gD) dW/dq_d  (dW/dq_d = +-W_other / h),
+      gbar_b = gwv v + gwb,  gv = gwv b,  dv/dA = A^-2 (A symmetric),
+      gbar_theta = sum_ab D_ab(gv (A^-2)_ab) - sum_d D_d(gq_d - gbar_psi_d),
+    with D_ab the (self-adjoint) second-difference stencils of eq.
+    discrete_examples and D_d the (anti-self-adjoint) central differences.
+    """
+    t, bb = _f64(theta), _f64(b)
+    N = _grid_n(t)
+    h = L / N
+    gps = np.zeros((3, N, N, N)) if gbar_psi is None else _f64(gbar_psi).reshape(3, N, N, N)
+    gdl = np.zeros((N, N, N)) if gbar_dl is None else _f64(gbar_dl).reshape(N, N, N)
+
+    def sh(a, s, ax):            # sh(a, 1, ax)[i] = a[i + 1] (periodic)
+        return np.roll(a, -s, axis=ax)
+
+    def d1(a, ax):               # central difference
+        return (sh(a, 1, ax) - sh(a, -1, ax)) / (2.0 * h)
+
+    def d2(a, ax, bx):           # second-difference stencils D_ab
+        if ax == bx:
+            return (sh(a, 1, ax) + sh(a, -1, ax) - 2.0 * a) / (h * h)
+        return (sh(sh(a, 1, ax), 1, bx) + sh(sh(a, -1, ax), -1, bx)
+                - sh(sh(a, -1, ax), 1, bx) - sh(sh(a, 1, ax), -1, bx)) / (4.0 * h * h)
+
+    # forward intermediates
+    g = [d1(t, a) for a in range(3)]
+    A = np.empty((N, N, N, 3, 3))
+    for a in range(3):
+        for c in range(3):
+            A[..., a, c] = d2(t, a, c) + (1.0 if a == c else 0.0)
+    Ainv = np.linalg.inv(A)
+    v = 3.0 - np.trace(Ainv, axis1=-2, axis2=-1)
+    x = (np.arange(N) + 0.5) * h
+    X = np.meshgrid(x, x, x, indexing="ij")
+    q = np.empty((N, N, N, 3))
+    for a in range(3):
+        qa = np.fmod(X[a] + g[a], L)
+        q[..., a] = np.where(qa < 0.0, qa + L, qa)
+    cells, frac = cic_cells(q.reshape(-1, 3), N, L)
+    wv, wb = (bb * v).ravel(), bb.ravel()
+    corners = []
+    for ca in (0, 1):
+        for cb in (0, 1):
+            for cc in (0, 1):
+                off = np.array([ca, cb, cc])
+                idx = (cells + off) % N
+                flat = (idx[:, 0] * N + idx[:, 1]) * N + idx[:, 2]
+                w1 = np.where(off == 1, frac, 1.0 - frac)          # per-axis weights
+                sgn = np.where(off == 1, 1.0, -1.0) / h             # d w1 / d q
+                W = w1[:, 0] * w1[:, 1] * w1[:, 2]
+                dW = np.stack([sgn[0] * w1[:, 1] * w1[:, 2],
+                               w1[:, 0] * sgn[1] * w1[:, 2],
+                               w1[:, 0] * w1[:, 1] * sgn[2]], axis=1)
+                corners.append((flat, W, dW))
+    num = np.zeros(N ** 3)
+    den = np.zeros(N ** 3)
+    for flat, W, _ in corners:
+        np.add.at(num, flat, wv * W)
+        np.add.at(den, flat, wb * W)
+    gd = gdl.ravel()
+    gN = gd / np.maximum(den, 1e-12)
+    gD = np.where(den > 1e-12, -gd * num / np.where(den > 1e-12, den, 1.0) ** 2, 0.0)
+    gwv = np.zeros(N ** 3)
+    gwb = np.zeros(N ** 3)
+    gq = np.zeros((N ** 3, 3))
+    for flat, W, dW in corners:
+        gwv += gN[flat] * W
+        gwb += gD[flat] * W
+        gq += (wv * gN[flat] + wb * gD[flat])[:, None] * dW
+    gb = (gwv * v.ravel() + gwb).reshape(N, N, N)
+    gv = (gwv * bb.ravel()).reshape(N, N, N)
+    G = gv[..., None, None] * (Ainv @ Ainv)
+    gt = np.zeros((N, N, N))
+    for a in range(3):
+        for c in range(3):
+            gt += d2(G[..., a, c], a, c)
+    for a in range(3):
+        gt -= d1(gq[:, a].reshape(N, N, N) - gps[a], a)
+    return gt, gb
+
+
 def cofactors(theta, h) -> np.ndarray:
     """adj(I + H theta) entries (xx, yy, zz, xy, yz, xz) as [6,N,N,N]."""
     t = _f64(theta)
