@@ -599,7 +599,7 @@ def bench_adjoint(recon, synth, torch, dev, n, directions):
     central finite differences along random directions."""
     L = 2.0 * n
     w = synth.WORKLOADS.get("adjoint-256")
-    _, dh = synth.linear_field(n, L, 0.8, w.seed if w else 5000, backend="torch", device=dev)
+    delta_lin, dh = synth.linear_field(n, L, 0.8, w.seed if w else 5000, backend="torch", device=dev)
     pos = synth.zeldovich_positions(dh, n, L).contiguous()
     s = recon.Solver(n, L, recon.RECON_F64)
     b = synth.smooth_and_floor(s.deposit_cic(pos), L, 4.0)
@@ -629,12 +629,65 @@ def bench_adjoint(recon, synth, torch, dev, n, directions):
         lm = float((wv * pm).sum())
         fd = (lp - lm) / (2 * eps)
         errs.append(abs(float((g * d).sum()) - fd) / abs(fd))
+    out = {"workload": f"{n}^3, L = {L:g} Mpc/h, sigma_lin = 0.8, R = 4 Mpc/h, FP64",
+           "solve_seconds": t_solve, "adjoint_seconds_first": t_adj,
+           "adjoint_seconds_repeat": t_adj2, "fd_directions": directions,
+           "fd_max_rel_error": max(errs) if errs else None, "fd_step": eps}
+    try:
+        out["delta_r_loss"] = _adjoint_delta_r_loss(recon, torch, s, aux, b, phi, delta_lin, n, L, gen)
+    except Exception as ex:   # reported, never fatal to the bench line
+        out["delta_r_loss"] = {"error": f"{type(ex).__name__}: {ex}"}
     aux.close()
     s.close()
-    return {"workload": f"{n}^3, L = {L:g} Mpc/h, sigma_lin = 0.8, R = 4 Mpc/h, FP64",
-            "solve_seconds": t_solve, "adjoint_seconds_first": t_adj,
-            "adjoint_seconds_repeat": t_adj2, "fd_directions": directions,
-            "fd_max_rel_error": max(errs) if errs else None, "fd_step": eps}
+    return out
+
+
+def _adjoint_delta_r_loss(recon, torch, s, aux, b, phi, delta_lin, n, L, gen, directions=4):
+    """The loss of the adjoint workload on the reconstructed density:
+    sum over |k| < 0.5 h/Mpc of |FFT(delta_r) - FFT(delta_L, seed)|^2, delta_r
+    the FP64 output at phi(b).  Its gradient with respect to b is the output's
+    adjoint (direct b term) plus the solve's adjoint of its phi term; checked
+    against central finite differences along smooth directions (FP64 solves
+    to 1e-13)."""
+    import math
+    kf = 2 * math.pi / L
+    f = torch.fft.fftfreq(n, d=1.0 / n, device=b.device) * kf
+    fz = torch.fft.rfftfreq(n, d=1.0 / n, device=b.device) * kf
+    kk = torch.sqrt(f[:, None, None] ** 2 + f[None, :, None] ** 2 + fz[None, None, :] ** 2)
+    mask = (kk < 0.5).to(torch.float64)
+    ref = torch.fft.rfftn(delta_lin.to(torch.float64))
+
+    def loss_of(dl):
+        return float((mask * (torch.fft.rfftn(dl) - ref).abs() ** 2).sum())
+
+    _, dl = s.displace_fp64(phi, b)
+    dlr = dl.detach().clone().requires_grad_(True)
+    (mask * (torch.fft.rfftn(dlr) - ref).abs() ** 2).sum().backward()
+    gdl = dlr.grad.contiguous()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    gphi, gb_direct = s.displace_adjoint(phi, b, None, gdl)
+    gb = gb_direct + s.adjoint(gphi)
+    torch.cuda.synchronize()
+    t_grad = time.perf_counter() - t0
+    # directions inside the loss's band (|k| < 0.5 h/Mpc, unit rms): a white
+    # direction barely moves this loss, and its difference quotient drowns
+    # in the solves' residual
+    eps, errs = 1e-5, []
+    for _ in range(directions):
+        d = torch.randn((n, n, n), dtype=torch.float64, device=b.device, generator=gen)
+        d = torch.fft.irfftn(torch.fft.rfftn(d) * mask, s=(n, n, n))
+        d = d / d.pow(2).mean().sqrt()
+        vals = []
+        for sg in (1.0, -1.0):
+            bp = b + sg * eps * d
+            pp, _ = aux.solve(bp, tol=1e-13, max_cycles=80)
+            vals.append(loss_of(aux.displace_fp64(pp, bp)[1]))
+        fd = (vals[0] - vals[1]) / (2 * eps)
+        errs.append(abs(float((gb * d).sum()) - fd) / abs(fd))
+    return {"loss": "sum_{|k|<0.5 h/Mpc} |FFT(delta_r) - FFT(delta_L seed)|^2, delta_r FP64",
+            "gradient_seconds": t_grad, "fd_directions": directions, "fd_step": eps,
+            "fd_max_rel_error": max(errs)}
 
 
 def _time_launches(torch, stream, fn, reps):

@@ -189,6 +189,38 @@ recon_status recon_solve(recon_handle *h, const double *b, double *phi, double t
 recon_status recon_displace(recon_handle *h, const double *phi, const double *b,
                             double *psi, double *deltaL);
 
+/* The same output as recon_displace (Sec. II.B restated above), evaluated in
+ * plain FP64: per cell q = x + g (mod L) with x = (i + 1/2) h and g the
+ * central-difference gradient, the CIC cell and fraction of u = q N/L - 1/2
+ * per axis, v and both CIC sums in FP64 (FP64 atomics).  This is the map
+ * whose gradient recon_displace_adjoint returns; use it where a gradient is
+ * checked against finite differences.  Same arguments, workspace and errors
+ * as recon_displace. */
+recon_status recon_displace_fp64(recon_handle *h, const double *phi, const double *b,
+                                 double *psi, double *deltaL);
+
+/* Adjoint of the reconstruction output (the map of recon_displace_fp64;
+ * Sec. II.B, carried by the chain rule, no counterpart printed in the
+ * paper): given gbar_psi = dLoss/dpsi (device 3 N^3, component-major, or
+ * NULL for zero) and gbar_deltaL = dLoss/ddeltaL (device N^3 or NULL),
+ * writes gbar_phi = dLoss/dphi and gbar_b = dLoss/db (device N^3 each,
+ * overwritten) at the given phi and b (device N^3):
+ *   gN = gbar_deltaL / max(den, 1e-12),  gD = -gbar_deltaL num / den^2,
+ *   per cell: gbar_b = v sum W gN + sum W gD,  gv = b sum W gN,
+ *             gq = sum (b v gN + b gD) dW/dq  over the 8 CIC corners W,
+ *   gbar_phi = sum_ab D_ab(gv (A^-2)_ab) - sum_d D_d(gq_d - gbar_psi_d),
+ * with A = I + H phi, D_ab the stencils of eq. discrete_examples and D_d
+ * central differences.  The CIC weights are piecewise linear, so the map is
+ * differentiable except where some q lies on a cell face.  For a loss on
+ * the output of a solve, pass gbar_phi on to recon_adjoint and add its
+ * gbar_b to this one.  The first call allocates 9 N^3 doubles of workspace,
+ * held by the handle until recon_destroy; also uses 2 N^3 doubles of the
+ * handle workspace.  Outputs must not alias an input or each other.
+ * Errors: RECON_E_INVALID, RECON_E_OOM, RECON_E_CUDA. */
+recon_status recon_displace_adjoint(recon_handle *h, const double *phi, const double *b,
+                                    const double *gbar_psi, const double *gbar_deltaL,
+                                    double *gbar_phi, double *gbar_b);
+
 /* 1-point Gaussianisation of an N^3 field (Sec. III: tried on delta_r),
  * read as the rank mapping
  *     out_i = mean + std * Phi^-1((rank_i + 1/2) / N^3),

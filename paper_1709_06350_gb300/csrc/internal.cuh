@@ -66,6 +66,7 @@ struct recon_handle {
 
     AdjWork adj;
     GaussWork gauss;
+    double *dadj = nullptr;   // 9 N^3: recon_displace_adjoint (allocated at its first call)
     int adj_cycles = 0;
     double adj_rel = 0.0;
 
@@ -133,6 +134,13 @@ cudaError_t cic_deposit(const double *pos, long long n, int N, double L, double 
 // scheme: 0 NGP, 1 CIC, 2 TSC
 cudaError_t assign_deposit(int scheme, const double *pos, long long n, int N, double L, double mass,
                            double *rho, cudaStream_t s);
+// FP64 form of the reconstruction output, and its adjoint (recon_cic.cu);
+// num, den: N^3 doubles of scratch each, G9: 9 N^3 doubles
+cudaError_t displace_fp64(int N, double L, const double *phi, const double *b, double *psi,
+                          double *deltaL, double *num, double *den, cudaStream_t s);
+cudaError_t displace_adjoint(int N, double L, const double *phi, const double *b, const double *gpsi,
+                             const double *gdl, double *gphi, double *gb, double *num, double *den,
+                             double *G9, cudaStream_t s);
 // ---- adjoint (recon_adjoint.cu)
 recon_status adjoint(recon_handle *H, const double *gbar, double *lam);
 void adj_free(recon_handle *H);

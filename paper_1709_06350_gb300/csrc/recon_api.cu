@@ -249,6 +249,7 @@ void recon_destroy(recon_handle *H)
     else cudaDeviceSynchronize();
     adj_free(H);
     gauss_free(H);
+    if (H->dadj) cudaFree(H->dadj);
     free_all(H);
     delete H;
 }
@@ -368,6 +369,40 @@ recon_status recon_gaussianise(recon_handle *H, const double *field, double *out
     if (!field || !out) return set_err(H, RECON_E_INVALID, "NULL pointer");
     if (field == out) return set_err(H, RECON_E_INVALID, "field and out must not alias");
     return cuda_status(H, gaussianise(H, field, (size_t)H->N * H->N * H->N, out), "gaussianise");
+}
+
+recon_status recon_displace_fp64(recon_handle *H, const double *phi, const double *b, double *psi,
+                                 double *deltaL)
+{
+    if (!H) return RECON_E_INVALID;
+    if (!phi || !b || !psi || !deltaL) return set_err(H, RECON_E_INVALID, "NULL pointer");
+    if (!gpu_reachable(psi) || !gpu_reachable(deltaL))
+        return set_err(H, RECON_E_INVALID, "psi and deltaL must be device or page-locked host memory");
+    return cuda_status(H, displace_fp64(H->N, H->L, phi, b, psi, deltaL, H->work64, H->work64b, H->stream),
+                       "displace_fp64");
+}
+
+recon_status recon_displace_adjoint(recon_handle *H, const double *phi, const double *b,
+                                    const double *gbar_psi, const double *gbar_deltaL,
+                                    double *gbar_phi, double *gbar_b)
+{
+    if (!H) return RECON_E_INVALID;
+    if (!phi || !b || !gbar_phi || !gbar_b) return set_err(H, RECON_E_INVALID, "NULL pointer");
+    const void *ins[4] = {phi, b, gbar_psi, gbar_deltaL};
+    for (const void *q : ins)
+        if (q && (q == gbar_phi || q == gbar_b))
+            return set_err(H, RECON_E_INVALID, "gbar_phi and gbar_b must not alias an input");
+    if (gbar_phi == gbar_b) return set_err(H, RECON_E_INVALID, "gbar_phi and gbar_b must differ");
+    H->err.clear();
+    const size_t n = (size_t)H->N * H->N * H->N;
+    if (!H->dadj && cudaMalloc(&H->dadj, sizeof(double) * 9 * n) != cudaSuccess) {
+        cudaGetLastError();
+        H->dadj = nullptr;
+        return set_err(H, RECON_E_OOM, "recon_displace_adjoint: cannot allocate its 9 N^3 doubles");
+    }
+    return cuda_status(H, displace_adjoint(H->N, H->L, phi, b, gbar_psi, gbar_deltaL, gbar_phi, gbar_b,
+                                           H->work64, H->work64b, H->dadj, H->stream),
+                       "displace_adjoint");
 }
 
 recon_status recon_adjoint(recon_handle *H, const double *gbar_phi, double *gbar_b)

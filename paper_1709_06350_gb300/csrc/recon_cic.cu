@@ -369,6 +369,248 @@ k_displace_finish(const float2 *__restrict__ acc, size_t n, double *__restrict__
     }
 }
 
+// ---- the reconstruction output in plain FP64, and its adjoint ----------
+// Per cell c at x_c = (i + 1/2) h, evaluated with the operations of a plain
+// IEEE evaluation of the definition (explicit roundings, no fused
+// multiply-add), so that the CIC cells of q match any host's bit for bit:
+//   g = central-difference gradient of phi,  psi = -g,
+//   q = x + g (mod L),  per axis u = q N/L - 1/2 (CIC cell and fraction),
+//   A = I + H phi (stencils of eq. discrete_examples),  v = 3 - tr(A^-1),
+// and delta_r = CIC(q, b v) / max(CIC(q, b), 1e-12).  This is the map whose
+// gradient recon_displace_adjoint computes; recon_displace evaluates the same
+// map from FP32 parts of phi (about 1e-6 of rounding in delta_r).
+struct CellFwd {
+    int c0[3], c1[3];   // CIC cells along each axis
+    double f[3];        // CIC fractions
+    double g[3];        // central-difference gradient of phi
+    double ai[6];       // A^-1: xx, yy, zz, xy, yz, xz
+    double v;           // 3 - tr(A^-1)
+};
+
+__device__ __forceinline__ void cell_forward64(const double *__restrict__ t, int N, double L, double h,
+                                               double nl, int i, int j, int k, CellFwd &o)
+{
+    const double two_h = 2.0 * h;
+    const int own[3] = {i, j, k};
+    const double tp[3] = {t[offs(N, wp(i, N), j, k)], t[offs(N, i, wp(j, N), k)], t[offs(N, i, j, wp(k, N))]};
+    const double tm[3] = {t[offs(N, wm(i, N), j, k)], t[offs(N, i, wm(j, N), k)], t[offs(N, i, j, wm(k, N))]};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        o.g[a] = __ddiv_rn(__dsub_rn(tp[a], tm[a]), two_h);
+        const double x = __dmul_rn(__dadd_rn((double)own[a], 0.5), h);
+        double q = fmod(__dadd_rn(x, o.g[a]), L);
+        if (q < 0.0) q = __dadd_rn(q, L);
+        cic_axis(q, N, nl, o.c0[a], o.f[a]);
+        o.c1[a] = o.c0[a] + 1 == N ? 0 : o.c0[a] + 1;
+    }
+    const Nb19<double> n = load19<double>(t, N, i, j, k);
+    const double h2 = h * h, q4 = 4.0 * h2;
+    const double axx = 1.0 + ((n.xp + n.xm) - 2.0 * n.c) / h2;
+    const double ayy = 1.0 + ((n.yp + n.ym) - 2.0 * n.c) / h2;
+    const double azz = 1.0 + ((n.zp + n.zm) - 2.0 * n.c) / h2;
+    const double axy = (((n.xpyp + n.xmym) - n.xmyp) - n.xpym) / q4;
+    const double ayz = (((n.ypzp + n.ymzm) - n.ymzp) - n.ypzm) / q4;
+    const double axz = (((n.xpzp + n.xmzm) - n.xmzp) - n.xpzm) / q4;
+    // adj(A) and det(A) (first-row expansion)
+    const double cxx = ayy * azz - ayz * ayz, cyy = axx * azz - axz * axz, czz = axx * ayy - axy * axy;
+    const double cxy = axz * ayz - axy * azz, cyz = axy * axz - axx * ayz, cxz = axy * ayz - axz * ayy;
+    const double det = axx * cxx + axy * cxy + axz * cxz;
+    o.v = 3.0 - (cxx + cyy + czz) / det;
+    const double id = 1.0 / det;
+    o.ai[0] = cxx * id;
+    o.ai[1] = cyy * id;
+    o.ai[2] = czz * id;
+    o.ai[3] = cxy * id;
+    o.ai[4] = cyz * id;
+    o.ai[5] = cxz * id;
+}
+
+// CIC weight of corner (a, bq, cz) and its derivative along each axis of q
+// (d f / d q = 1 / h, the lower corner weighs 1 - f)
+__device__ __forceinline__ double corner_w(const double f[3], int a, int bq, int cz)
+{
+    return ((a ? f[0] : 1.0 - f[0]) * (bq ? f[1] : 1.0 - f[1])) * (cz ? f[2] : 1.0 - f[2]);
+}
+
+// psi (if non-null) and the CIC sums num = sum b v W, den = sum b W (FP64
+// atomics; num and den start at zero)
+__global__ void __launch_bounds__(kRowX * kRowY)
+k_disp64_deposit(const double *__restrict__ t, const double *__restrict__ b, int N, double L,
+                 double h, double nl, double *__restrict__ psi, double *__restrict__ num,
+                 double *__restrict__ den)
+{
+    const size_t n = (size_t)N * N * N;
+    FOR_ROWS(N, i, j)
+    for (int k = threadIdx.x; k < N; k += kRowX) {
+        CellFwd o;
+        cell_forward64(t, N, L, h, nl, i, j, k, o);
+        const unsigned id = offs(N, i, j, k);
+        if (psi) {
+            psi[id] = -o.g[0];
+            psi[n + id] = -o.g[1];
+            psi[2 * n + id] = -o.g[2];
+        }
+        const double wb = b[id], wv = wb * o.v;
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int bq = 0; bq < 2; ++bq)
+#pragma unroll
+                for (int cz = 0; cz < 2; ++cz) {
+                    const double W = corner_w(o.f, a, bq, cz);
+                    const unsigned c = offs(N, a ? o.c1[0] : o.c0[0], bq ? o.c1[1] : o.c0[1], cz ? o.c1[2] : o.c0[2]);
+                    atomicAdd(num + c, wv * W);
+                    atomicAdd(den + c, wb * W);
+                }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_disp64_finish(const double *__restrict__ num, const double *__restrict__ den, size_t n,
+                double *__restrict__ out)
+{
+    const size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id < n) out[id] = num[id] / (den[id] > 1e-12 ? den[id] : 1e-12);
+}
+
+// adjoint of the quotient, in place: num <- gbar / max(den, eps),
+// den <- -gbar num / den^2 where den > eps (else 0)
+__global__ void __launch_bounds__(kThreads)
+k_dadj_quot(double *__restrict__ num, double *__restrict__ den, const double *__restrict__ gdl, size_t n)
+{
+    const size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id < n) {
+        const double d = den[id], nm = num[id], gd = gdl[id];
+        num[id] = gd / (d > 1e-12 ? d : 1e-12);
+        den[id] = d > 1e-12 ? (-gd * nm) / (d * d) : 0.0;
+    }
+}
+
+// per cell: gbar_b, and the nine fields the potential's gradient is built
+// from -- gv (A^-2)_ab (xx, yy, zz, xy, yz, xz) and gq_d - gbar_psi_d -- in
+// G9 = [9][N^3].  gN, gD: the quotient adjoint on the q-grid (null: no
+// delta_r term); gpsi: [3][N^3] or null.
+__global__ void __launch_bounds__(kRowX * kRowY)
+k_dadj_cells(const double *__restrict__ t, const double *__restrict__ b, const double *__restrict__ gN,
+             const double *__restrict__ gD, const double *__restrict__ gpsi, int N, double L, double h,
+             double nl, double *__restrict__ gb_out, double *__restrict__ G9)
+{
+    const size_t n = (size_t)N * N * N;
+    const double ih = 1.0 / h;
+    FOR_ROWS(N, i, j)
+    for (int k = threadIdx.x; k < N; k += kRowX) {
+        CellFwd o;
+        cell_forward64(t, N, L, h, nl, i, j, k, o);
+        const unsigned id = offs(N, i, j, k);
+        const double wb = b[id], wv = wb * o.v;
+        double gwv = 0.0, gwb = 0.0, gq[3] = {0.0, 0.0, 0.0};
+        if (gN) {
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                for (int bq = 0; bq < 2; ++bq)
+#pragma unroll
+                    for (int cz = 0; cz < 2; ++cz) {
+                        const double w0 = a ? o.f[0] : 1.0 - o.f[0];
+                        const double w1 = bq ? o.f[1] : 1.0 - o.f[1];
+                        const double w2 = cz ? o.f[2] : 1.0 - o.f[2];
+                        const double s0 = a ? ih : -ih, s1 = bq ? ih : -ih, s2 = cz ? ih : -ih;
+                        const unsigned c = offs(N, a ? o.c1[0] : o.c0[0], bq ? o.c1[1] : o.c0[1], cz ? o.c1[2] : o.c0[2]);
+                        const double n_c = gN[c], d_c = gD[c];
+                        const double W = (w0 * w1) * w2;
+                        gwv += n_c * W;
+                        gwb += d_c * W;
+                        const double e = wv * n_c + wb * d_c;
+                        gq[0] += e * (s0 * w1 * w2);
+                        gq[1] += e * (w0 * s1 * w2);
+                        gq[2] += e * (w0 * w1 * s2);
+                    }
+        }
+        gb_out[id] = gwv * o.v + gwb;
+        const double gv = gwv * wb;
+        // (A^-1)^2, symmetric
+        const double *m = o.ai;   // xx, yy, zz, xy, yz, xz
+        const double sxx = m[0] * m[0] + m[3] * m[3] + m[5] * m[5];
+        const double syy = m[3] * m[3] + m[1] * m[1] + m[4] * m[4];
+        const double szz = m[5] * m[5] + m[4] * m[4] + m[2] * m[2];
+        const double sxy = m[0] * m[3] + m[3] * m[1] + m[5] * m[4];
+        const double syz = m[3] * m[5] + m[1] * m[4] + m[4] * m[2];
+        const double sxz = m[0] * m[5] + m[3] * m[4] + m[5] * m[2];
+        G9[id] = gv * sxx;
+        G9[n + id] = gv * syy;
+        G9[2 * n + id] = gv * szz;
+        G9[3 * n + id] = gv * sxy;
+        G9[4 * n + id] = gv * syz;
+        G9[5 * n + id] = gv * sxz;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) G9[(6 + a) * n + id] = gq[a] - (gpsi ? gpsi[a * n + id] : 0.0);
+    }
+}
+
+// gbar_phi = sum_a D_aa(G_aa) + 2 sum_{a<b} D_ab(G_ab) - sum_d D_d(Y_d): the
+// second-difference stencils are self-adjoint, the central difference is
+// anti-self-adjoint (periodic grid)
+__global__ void __launch_bounds__(kRowX * kRowY)
+k_dadj_theta(const double *__restrict__ G9, int N, double h, double *__restrict__ out)
+{
+    const size_t n = (size_t)N * N * N;
+    const double ih2 = 1.0 / (h * h), iq4 = 1.0 / (4.0 * h * h), i2h = 1.0 / (2.0 * h);
+    FOR_ROWS(N, i, j)
+    for (int k = threadIdx.x; k < N; k += kRowX) {
+        const int ip = wp(i, N), im = wm(i, N), jp = wp(j, N), jm = wm(j, N), kp = wp(k, N), km = wm(k, N);
+        const double *Gxx = G9, *Gyy = G9 + n, *Gzz = G9 + 2 * n;
+        const double *Gxy = G9 + 3 * n, *Gyz = G9 + 4 * n, *Gxz = G9 + 5 * n;
+        const double *Yx = G9 + 6 * n, *Yy = G9 + 7 * n, *Yz = G9 + 8 * n;
+        const unsigned c = offs(N, i, j, k);
+        double r = ((Gxx[offs(N, ip, j, k)] + Gxx[offs(N, im, j, k)]) - 2.0 * Gxx[c]) * ih2;
+        r += ((Gyy[offs(N, i, jp, k)] + Gyy[offs(N, i, jm, k)]) - 2.0 * Gyy[c]) * ih2;
+        r += ((Gzz[offs(N, i, j, kp)] + Gzz[offs(N, i, j, km)]) - 2.0 * Gzz[c]) * ih2;
+        r += 2.0 * (((Gxy[offs(N, ip, jp, k)] + Gxy[offs(N, im, jm, k)]) - Gxy[offs(N, im, jp, k)]) - Gxy[offs(N, ip, jm, k)]) * iq4;
+        r += 2.0 * (((Gyz[offs(N, i, jp, kp)] + Gyz[offs(N, i, jm, km)]) - Gyz[offs(N, i, jm, kp)]) - Gyz[offs(N, i, jp, km)]) * iq4;
+        r += 2.0 * (((Gxz[offs(N, ip, j, kp)] + Gxz[offs(N, im, j, km)]) - Gxz[offs(N, im, j, kp)]) - Gxz[offs(N, ip, j, km)]) * iq4;
+        r -= (Yx[offs(N, ip, j, k)] - Yx[offs(N, im, j, k)]) * i2h;
+        r -= (Yy[offs(N, i, jp, k)] - Yy[offs(N, i, jm, k)]) * i2h;
+        r -= (Yz[offs(N, i, j, kp)] - Yz[offs(N, i, j, km)]) * i2h;
+        out[c] = r;
+    }
+}
+
+// FP64 output: num, den: N^3 doubles of scratch each
+cudaError_t displace_fp64(int N, double L, const double *phi, const double *b, double *psi,
+                          double *deltaL, double *num, double *den, cudaStream_t s)
+{
+    const size_t n = (size_t)N * N * N;
+    cudaError_t e = cudaMemsetAsync(num, 0, sizeof(double) * n, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(den, 0, sizeof(double) * n, s);
+    if (e != cudaSuccess) return e;
+    note_launch(2);
+    k_disp64_deposit<<<row_grid(N), row_block(), 0, s>>>(phi, b, N, L, L / N, (double)N / L, psi, num, den);
+    k_disp64_finish<<<blocks_for(n), kThreads, 0, s>>>(num, den, n, deltaL);
+    return cudaGetLastError();
+}
+
+// adjoint: num, den: N^3 doubles of scratch each; G9: 9 N^3 doubles
+cudaError_t displace_adjoint(int N, double L, const double *phi, const double *b, const double *gpsi,
+                             const double *gdl, double *gphi, double *gb, double *num, double *den,
+                             double *G9, cudaStream_t s)
+{
+    const size_t n = (size_t)N * N * N;
+    const double h = L / N, nl = (double)N / L;
+    if (gdl) {
+        cudaError_t e = cudaMemsetAsync(num, 0, sizeof(double) * n, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(den, 0, sizeof(double) * n, s);
+        if (e != cudaSuccess) return e;
+        note_launch(2);
+        k_disp64_deposit<<<row_grid(N), row_block(), 0, s>>>(phi, b, N, L, h, nl, nullptr, num, den);
+        k_dadj_quot<<<blocks_for(n), kThreads, 0, s>>>(num, den, gdl, n);
+    }
+    note_launch(2);
+    k_dadj_cells<<<row_grid(N), row_block(), 0, s>>>(phi, b, gdl ? num : nullptr, gdl ? den : nullptr, gpsi,
+                                                    N, L, h, nl, gb, G9);
+    k_dadj_theta<<<row_grid(N), row_block(), 0, s>>>(G9, N, h, gphi);
+    return cudaGetLastError();
+}
+
 // scratch: N^3 doubles of room (the float2 sums); split: N^3 doubles of
 // room for the FP32 parts of phi
 cudaError_t displace(int N, double L, const double *phi, const double *b, double *psi,

@@ -69,6 +69,8 @@ _SIGS = {
     "recon_solve": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(recon_stats)]),
     "recon_displace": (_I, [_P, _P, _P, _P, _P]),
     "recon_adjoint": (_I, [_P, _P, _P]),
+    "recon_displace_fp64": (_I, [_P, _P, _P, _P, _P]),
+    "recon_displace_adjoint": (_I, [_P, _P, _P, _P, _P, _P, _P]),
     "recon_gaussianise": (_I, [_P, _P, _P]),
     "recon_last_error": (ctypes.c_char_p, [_P]),
     "recon_status_string": (ctypes.c_char_p, [_I]),
@@ -219,6 +221,25 @@ def recon_displace(h, N: int, phi, b, psi, deltaL) -> None:
                                  _dev_ptr(b, torch.float64, N ** 3),
                                  _reachable_ptr(psi, torch.float64, 3 * N ** 3),
                                  _reachable_ptr(deltaL, torch.float64, N ** 3)), h)
+
+
+def recon_displace_fp64(h, N: int, phi, b, psi, deltaL) -> None:
+    import torch
+    _check(load().recon_displace_fp64(h, _dev_ptr(phi, torch.float64, N ** 3),
+                                      _dev_ptr(b, torch.float64, N ** 3),
+                                      _reachable_ptr(psi, torch.float64, 3 * N ** 3),
+                                      _reachable_ptr(deltaL, torch.float64, N ** 3)), h)
+
+
+def recon_displace_adjoint(h, N: int, phi, b, gbar_psi, gbar_deltaL, gbar_phi, gbar_b) -> None:
+    """gbar_psi / gbar_deltaL: CUDA tensors or None (zero)."""
+    import torch
+    gp = None if gbar_psi is None else _dev_ptr(gbar_psi, torch.float64, 3 * N ** 3)
+    gd = None if gbar_deltaL is None else _dev_ptr(gbar_deltaL, torch.float64, N ** 3)
+    _check(load().recon_displace_adjoint(h, _dev_ptr(phi, torch.float64, N ** 3),
+                                         _dev_ptr(b, torch.float64, N ** 3), gp, gd,
+                                         _dev_ptr(gbar_phi, torch.float64, N ** 3),
+                                         _dev_ptr(gbar_b, torch.float64, N ** 3)), h)
 
 
 def recon_gaussianise(h, N: int, field, out) -> None:
@@ -410,6 +431,25 @@ class Solver:
             dl = torch.empty_like(phi)
         recon_displace(self.h, self.N, phi, b, psi, dl)
         return psi, dl
+
+    def displace_fp64(self, phi, b, psi=None, dl=None):
+        """The same output as displace() in plain FP64 (the map whose gradient
+        displace_adjoint returns)."""
+        import torch
+        if psi is None:
+            psi = torch.empty((3,) + tuple(phi.shape), dtype=torch.float64, device=phi.device)
+        if dl is None:
+            dl = torch.empty_like(phi)
+        recon_displace_fp64(self.h, self.N, phi, b, psi, dl)
+        return psi, dl
+
+    def displace_adjoint(self, phi, b, gbar_psi=None, gbar_dl=None):
+        """(dLoss/dphi, dLoss/db) from dLoss/dpsi and dLoss/ddelta_r (None: zero)."""
+        import torch
+        gphi = torch.empty_like(phi)
+        gb = torch.empty_like(b)
+        recon_displace_adjoint(self.h, self.N, phi, b, gbar_psi, gbar_dl, gphi, gb)
+        return gphi, gb
 
     def gaussianise(self, field):
         """1-point Gaussianisation (rank mapping onto Gaussian quantiles)."""
