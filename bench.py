@@ -49,7 +49,7 @@ def parse():
     p.add_argument("--no-cubic", action="store_true")
     p.add_argument("--batch-count", type=int, default=64)
     p.add_argument("--adjoint-n", type=int, default=256)
-    p.add_argument("--fd-directions", type=int, default=8)
+    p.add_argument("--fd-directions", type=int, default=32)
     p.add_argument("--cpu-sample-n", type=int, default=128)
     p.add_argument("--kernel-only", type=int, default=0, metavar="N",
                    help="only time the roofline kernel at N^3 (small case for profilers)")
