@@ -476,6 +476,82 @@ def test_displace_linear_limit(O):
     assert 0.85 < np.log10(errs[1] / errs[0]) < 1.15
 
 
+def _plane_zeldovich(N, L, A):
+    """A 1-D Zel'dovich map without shell crossing and its potential in closed
+    form.  Lagrangian q moves to x = q - (A/k) sin(kq), k = 2 pi / L, so the
+    linear density is delta_L(q) = -d psi/dq = A cos(kq) and, for A < 1, the
+    map is monotone (no shell crossing).  Its inverse q(x) is the gradient of
+    x^2/2 + theta(x) with theta' = q - x = (A/k) sin(k q(x)); integrating in q
+    (dx = (1 - A cos kq) dq) gives the closed form
+        theta(x) = -(A/k^2) cos(k q) + (A^2 / (4 k^2)) cos(2 k q),  q = q(x).
+    q(x) solves Kepler's equation x = q - (A/k) sin(kq) (Newton, to round-off).
+    Returns theta and q at the cell centres x = (i + 1/2) h."""
+    k = 2.0 * np.pi / L
+    x = (np.arange(N) + 0.5) * (L / N)
+    q = x.copy()
+    for _ in range(60):
+        q -= (q - (A / k) * np.sin(k * q) - x) / (1.0 - A * np.cos(k * q))
+    assert np.max(np.abs(q - (A / k) * np.sin(k * q) - x)) < 1e-12 * L
+    theta = -(A / k**2) * np.cos(k * q) + (A**2 / (4.0 * k**2)) * np.cos(2.0 * k * q)
+    return theta, q, x
+
+
+@pytest.mark.parametrize("A", [0.3, 0.5])
+def test_displace_recovers_plane_zeldovich(O, A):
+    """P10 (Sec. II.B, eq. reconstructed_density; steps B2-B3): a Zel'dovich
+    map without shell crossing is recovered exactly in the continuum, so the
+    reconstructed density at the Lagrangian grid must converge to the seeded
+    delta_L(q) = A cos(kq) and psi = x - q to the exact displacement as N
+    doubles -- at O(1) amplitude, where a wrong sign of q = x + grad theta,
+    a dropped mass weight in either CIC average, or a wrong sign in
+    v = 3 - tr((I+H)^-1) leaves an O(A) error that does not shrink.
+    A <= 0.5 keeps b <= 2, so Eulerian cells sit at most 2h apart in q and
+    every Lagrangian cell receives CIC weight (at A = 0.7 some cells in the
+    densest region get none)."""
+    L = 100.0
+    errs, perrs = [], []
+    for N in (16, 32, 64):
+        h = L / N
+        th, q, x = _plane_zeldovich(N, L, A)
+        t = np.broadcast_to(th[:, None, None], (N,) * 3).copy()
+        psi, dr = O.displace(t, O.det_grid(t, h), L)
+        # the map is plane-symmetric: every (j, k) column carries the same profile
+        assert np.all(dr == dr[:, :1, :1]) and np.all(psi[1] == 0.0) and np.all(psi[2] == 0.0)
+        qg = (np.arange(N) + 0.5) * h
+        errs.append(np.sqrt(np.mean((dr[:, 0, 0] - A * np.cos(2 * np.pi * qg / L)) ** 2)))
+        perrs.append(np.max(np.abs(psi[0][:, 0, 0] - (x - q))))
+    assert errs[-1] < 0.02 * A
+    assert errs[1] < 0.75 * errs[0] and errs[2] < 0.75 * errs[1]
+    # psi is a central difference of the closed-form theta: second order
+    assert 2.5 < perrs[0] / perrs[1] < 5.0 and 2.5 < perrs[1] / perrs[2] < 5.0
+
+
+def test_paper_eps_plane_closed_form(O):
+    """The paper's epsilon (Sec. II.A.2, eq. discretisition): rms over cells of
+    lap_h theta - Sigma, Sigma = the cubic's largest root - 3.  For a plane
+    theta(x) the discrete Hessian is diag(a, 0, 0), a = D_xx theta, and the
+    cubic factorises: s^3 + p s + q = (s - a)^2 (s + 2a) - 27 rhs.  Choosing
+    for every cell a root s* = 3 + a + d (d small, so s* > |a|, the largest
+    root) and rhs = (s* - a)^2 (s* + 2a) / 27 makes L_h = -d in closed form:
+    epsilon = rms(d).  The right side is split into g + c with c != 0."""
+    N, L = 12, 30.0
+    h = L / N
+    x = np.arange(N) / N
+    f = 2.0 * np.sin(2 * np.pi * x) + 0.5 * np.cos(6 * np.pi * x)
+    t = np.broadcast_to(f[:, None, None], (N,) * 3).copy()
+    a = (np.roll(f, -1) + np.roll(f, 1) - 2 * f) / h**2
+    rng = np.random.default_rng(5)
+    d = 0.05 * rng.standard_normal((N,) * 3)
+    s_star = 3.0 + a[:, None, None] + d
+    assert np.all(s_star > np.abs(a)[:, None, None])
+    rhs = (s_star - a[:, None, None]) ** 2 * (s_star + 2 * a[:, None, None]) / 27.0
+    c = 0.37
+    eps = O.paper_eps(t, rhs - c, c, h)
+    assert eps == pytest.approx(np.sqrt(np.mean(d**2)), rel=1e-9)
+    # the exact plane solution (rhs = 1 + a) has epsilon 0 to round-off
+    assert O.paper_eps(t, np.broadcast_to(1.0 + a[:, None, None], (N,) * 3) - c, c, h) < 1e-13
+
+
 # --------------------------------------------------------------- adjoint
 def test_jacobian_matches_finite_differences(O):
     N, h = 8, 1.0
@@ -581,6 +657,12 @@ MUTATIONS = {
                  "w[a][0] = 0.5 * (0.5 + d[a]) * (0.5 + d[a]);"),
     "ngp-cell": ("rho[at(N, i[0], i[1], i[2])] += mass;",
                  "rho[at(N, i[0], i[1], i[2] + 1)] += mass;"),
+    "displace-q-sign": ("double qq = fmod(x[d] + g[d], L);",
+                        "double qq = fmod(x[d] - g[d], L);"),
+    "displace-den-unweighted": ("wb[id] = b[id];", "wb[id] = 1.0;"),
+    "displace-v-sign": ("double v = 3.0 - inv_tr;", "double v = inv_tr - 3.0;"),
+    "eps-no-compat": ("or_cell_cubic(t, N, h, i, j, k, g[at(N, i, j, k)] + c, &s, &p, &q);\n                double L",
+                      "or_cell_cubic(t, N, h, i, j, k, g[at(N, i, j, k)], &s, &p, &q);\n                double L"),
 }
 
 
@@ -612,6 +694,8 @@ def test_mutations_are_caught(O, name, tmp_path):
         lambda: test_prolongation_reproduces_linear_fields(M),
         lambda: test_assignment_is_the_cardinal_bspline(M, "ngp", 0),
         lambda: test_assignment_is_the_cardinal_bspline(M, "tsc", 2),
+        lambda: test_displace_recovers_plane_zeldovich(M, 0.5),
+        lambda: test_paper_eps_plane_closed_form(M),
     ]
     failed = 0
     for pin in pins:
