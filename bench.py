@@ -691,8 +691,9 @@ def _adjoint_delta_r_loss(recon, torch, s, aux, b, phi, delta_lin, n, L, gen, di
 
 
 def _time_launches(torch, stream, fn, reps):
-    """Mean time of one launch: (time of fn(reps) - time of fn(1)) / (reps - 1),
-    so per-call set-up (the linear smoother's cofactor pass) drops out."""
+    """Mean time of one launch: (time of fn(reps + 1) - time of fn(1)) / reps,
+    so per-call set-up drops out (both counts are odd: an odd number of
+    ping-pong sweeps ends with the same copy back into the caller's array)."""
     def timed(k):
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -703,16 +704,16 @@ def _time_launches(torch, stream, fn, reps):
         return a.elapsed_time(b) / 1e3
     fn(2)
     t1 = min(timed(1) for _ in range(3))
-    tr = timed(reps)
-    return (tr - t1) / (reps - 1)
+    tr = timed(reps + 1)
+    return (tr - t1) / reps
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
-# each fused smoother (the paired-FP32 kernels), from an ncu capture of the
-# 384^3 case (python bench.py --kernel-only 384; third launch of each); a
-# launch at N^3 moves (N/384)^3 times as much.  Valid for the kernels as they
-# were captured: re-measure after a change to either kernel.
-NCU_TRAFFIC_384 = {"LIN": 756.065280e6 + 208.592384e6, "FAS": 495.699968e6 + 199.885312e6}
+# each register-blocked fused smoother, from an ncu capture of the 384^3 case
+# (python bench.py --kernel-only 384; third launch of each); a launch at N^3
+# moves (N/384)^3 times as much.  Valid for the kernels as they were
+# captured: re-measure after a change to either kernel.
+NCU_TRAFFIC_384 = {"LIN": 722.541312e6 + 211.707392e6, "FAS": 463.279360e6 + 201.707520e6}
 
 
 def kernel_roofline(recon, torch, N, L, dev, stream):
@@ -745,8 +746,10 @@ def kernel_roofline(recon, torch, N, L, dev, stream):
     del th, g, work, e, work7
     out = []
     for key, name, t, bpc in (
-            ("LIN", "k_sweep_fused<float, LIN> (FP32 red-black smoother of J e = f, one sweep)", t_lin, 16.0),
-            ("FAS", "k_sweep_fused<float, FAS> (FP32 red-black Newton smoother, one sweep)", t_fas, 12.0)):
+            ("LIN", "k_sweep_reg<LIN> (FP32 red-black smoother of J e = f, one fused sweep, 2x2 register blocks)",
+             t_lin, 16.0),
+            ("FAS", "k_sweep_reg<FAS> (FP32 red-black Newton smoother, one fused sweep, 2x2 register blocks)",
+             t_fas, 12.0)):
         alg = bpc * N ** 3
         ach = alg / t / 1e9
         out.append({"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",

@@ -89,7 +89,9 @@ typedef struct {
                                    significand, FP32 pipes) while iterating;
                                    0 = plain FP64 arithmetic for both          */
     int fused_chunk;            /* planes per thread block of the fused smoother
-                                   sweeps (grids >= 128^3): 8..128, 0 = by size  */
+                                   sweeps (grids >= 128^3): 4..128, 0 = by size;
+                                   on grids of side a multiple of 64 it is taken
+                                   down to a multiple of 4 that divides N       */
 } recon_config;
 
 #define RECON_HISTORY_MAX 64

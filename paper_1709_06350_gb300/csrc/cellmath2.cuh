@@ -42,7 +42,7 @@ __device__ __forceinline__ float2 rcp2(float2 a) { return make_float2(rcp_approx
 // the largest root of s^3 + p s + q (eq. root), Newton-polished: the
 // fallback of the paired update, kept out of line so that the common path
 // stays small in the instruction cache
-__device__ __noinline__ float root_polished_ool(float p, float q) { return root_polished(p, q); }
+static __device__ __noinline__ float root_polished_ool(float p, float q) { return root_polished(p, q); }
 
 // Two cells' neighbourhoods as one Nb19<float2>: cell 0 in .x, cell 1 in .y.
 __device__ __forceinline__ Nb19<float2> pack19(const Nb19<float> &a, const Nb19<float> &b)

@@ -83,6 +83,15 @@ unsigned long long launch_count();
 
 // Dynamic shared-memory limits of the fused kernels (set before any capture).
 cudaError_t prepare_kernels();
+// Register-blocked fused FP32 sweeps (recon_sweep.cu): sides a multiple of 64.
+cudaError_t prepare_reg_sweeps();
+bool reg_sweep_ok(int N, const float *src, const float *dst, const float *g, const float *th);
+int reg_sweep_chunk(int N, int want);
+// one sweep src -> dst; lin: J e = f with theta th (else the FAS cubic with
+// right side g + c, c from cptr or cval); chunk: planes per CTA (0 = by size)
+cudaError_t reg_sweep_launch(bool lin, int N, const float *src, float *dst, const float *g, const float *th,
+                             const double *cptr, double cval, float ih2, float h2_6, int rule, int chunk,
+                             cudaStream_t s);
 // Planes per CTA of the fused sweeps enqueued next on this host thread (0 = auto).
 void set_fused_chunk(int c);
 

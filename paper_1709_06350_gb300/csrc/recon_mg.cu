@@ -491,6 +491,7 @@ cudaError_t prepare_kernels()
     cudaError_t e = fused_attr<float, false>();
     if (e == cudaSuccess) e = fused_attr<double, false>();
     if (e == cudaSuccess) e = fused_attr<float, true>();
+    if (e == cudaSuccess) e = prepare_reg_sweeps();
     if (e == cudaSuccess) g_kernels_ready = true;
     return e;
 }
@@ -529,6 +530,21 @@ cudaError_t sweep(int N, double h, int rule, T *t, const T *g, const double *cpt
                   double cval, int sweeps, T *work, cudaStream_t s)
 {
     const T ih2 = (T)(1.0 / (h * h)), h2_6 = (T)(h * h / 6.0);
+    if constexpr (std::is_same<T, float>::value) {
+        if (reg_sweep_ok(N, t, work, g, nullptr) && reg_sweep_ok(N, work, t, g, nullptr)) {
+            T *a = t, *b = work;
+            for (int it = 0; it < sweeps; ++it) {
+                const cudaError_t e = reg_sweep_launch(false, N, a, b, g, nullptr, cptr, cval, ih2, h2_6, rule,
+                                                       g_fused_chunk, s);
+                if (e != cudaSuccess) return e;
+                T *tmp = a;
+                a = b;
+                b = tmp;
+            }
+            if (a != t) return cudaMemcpyAsync(t, a, sizeof(T) * (size_t)N * N * N, cudaMemcpyDeviceToDevice, s);
+            return cudaSuccess;
+        }
+    }
     if (N >= kFusedMinN && pair_aligned(t) && pair_aligned(work)) {
         T *a = t, *b = work;
         for (int it = 0; it < sweeps; ++it) {
@@ -1327,6 +1343,19 @@ static cudaError_t lin_sweep(int N, double h, float *e, const float *f, const fl
                              const float *th, int sweeps, float *work, cudaStream_t s)
 {
     const float ih2 = (float)(1.0 / (h * h));
+    if (reg_sweep_ok(N, e, work, f, th) && reg_sweep_ok(N, work, e, f, th)) {
+        float *a = e, *b = work;
+        for (int it = 0; it < sweeps; ++it) {
+            const cudaError_t err = reg_sweep_launch(true, N, a, b, f, th, nullptr, 0.0, ih2, (float)(h * h / 6.0),
+                                                     0, g_fused_chunk, s);
+            if (err != cudaSuccess) return err;
+            float *tmp = a;
+            a = b;
+            b = tmp;
+        }
+        if (a != e) return cudaMemcpyAsync(e, a, sizeof(float) * (size_t)N * N * N, cudaMemcpyDeviceToDevice, s);
+        return cudaSuccess;
+    }
     if (lin_fused(N, e, work)) {
         float *a = e, *b = work;
         for (int it = 0; it < sweeps; ++it) {
