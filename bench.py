@@ -4,8 +4,9 @@
 One step = one whole reconstruction of a seeded 512^3 Zel'dovich field
 (L = 512 Mpc/h, sigma_lin = 1, smoothing R = 2 Mpc/h) with particles already
 resident in HBM:
-    CIC deposit -> Gaussian smoothing / floor (input conditioning, FP32 torch FFT)
-    -> mixed-precision FAS solve to ||r|| / ||b - 1|| < 1e-8 -> displacement.
+    CIC deposit -> density preparation (Gaussian window, floor, mean 1:
+    recon_smooth_density) -> mixed-precision FAS solve to ||r|| / ||b - 1||
+    < 1e-8 -> displacement.
 All reconstruction steps run in librecon's hand-written sm_103a kernels.
 
 Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
@@ -50,7 +51,6 @@ def parse():
     p.add_argument("--batch-count", type=int, default=64)
     p.add_argument("--adjoint-n", type=int, default=256)
     p.add_argument("--fd-directions", type=int, default=32)
-    p.add_argument("--cpu-sample-n", type=int, default=128)
     p.add_argument("--kernel-only", type=int, default=0, metavar="N",
                    help="only time the roofline kernel at N^3 (small case for profilers)")
     return p.parse_args()
@@ -110,49 +110,99 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- CPU side
-def oracle_sample(n: int, seed: int):
-    """Oracle reconstruction of one n^3 realisation of the same recipe
-    (h = 1 Mpc/h, sigma_lin = 1, R = 2 Mpc/h).  Returns (seconds, info)."""
+def workload_config(W):
+    """The config dict both arms report for workload W (same keys, same values)."""
+    return {"workload": (f"{W.name}: {W.N}^3 seeded Zel'dovich field, L = {W.L:g} Mpc/h, "
+                         f"sigma_lin = {W.sigma_lin}, R = {W.R:g} Mpc/h, CIC + density preparation "
+                         f"+ solve to ||r||/||b-1|| < {W.tol:g} + displacement"),
+            "l2": "inputs larger than L2 (particle positions "
+                  f"{3 * 8 * W.N ** 3 / 1e9:.1f} GB, fields {W.N ** 3 * 8 / 1e9:.2f} GB)"}
+
+
+def oracle_calibration(W, n: int = 64):
+    """The oracle's whole reconstruction of one n^3 realisation of W's recipe
+    (same h, sigma_lin and R in cells) against one oracle sweep of its density:
+    both cost O(n^3), so their ratio carries over to W's grid.  Returns
+    (seconds of the reconstruction, seconds of one sweep, FAS cycles)."""
+    import numpy as np
     from oracle import oracle as O
     from paper_1709_06350_gb300 import synth
-    L = float(n)
-    _, dh = synth.linear_field(n, L, 1.0, seed)
+    h = W.L / W.N
+    L = n * h
+    _, dh = synth.linear_field(n, L, W.sigma_lin, W.seed + 17)
     pos = synth.zeldovich_positions(dh, n, L)
     t0 = time.perf_counter()
     rho = O.cic_deposit(pos, n, L)
-    t1 = time.perf_counter()
-    b = synth.smooth_and_floor(rho, L, 2.0)        # input conditioning: not timed
-    t2 = time.perf_counter()
-    theta, info = O.solve(b, L, tol=1e-8, max_cycles=40)
+    b = O.smooth_and_floor(rho, L, W.R)
+    theta, info = O.solve(b, L, tol=W.tol, max_cycles=40)
     O.displace(theta, b, L)
-    t3 = time.perf_counter()
-    return (t1 - t0) + (t3 - t2), info
+    t_rec = time.perf_counter() - t0
+    t_sw = min(_oracle_sweep_seconds(b, h) for _ in range(3))
+    return t_rec, t_sw, info["cycles"]
+
+
+def _oracle_sweep_seconds(b, h):
+    """One oracle Gauss-Seidel sweep (red-black, snapshot order, Newton rule)
+    of the density b from theta = 0."""
+    import numpy as np
+    from oracle import oracle as O
+    th = np.zeros_like(b)
+    t0 = time.perf_counter()
+    O.sweep(th, b, 0.0, h)
+    return time.perf_counter() - t0
+
+
+def oracle_workload_density(W):
+    """W's density built by the oracle (CIC and density preparation) from the
+    generator's seeded particles; for the reference arm, which has no GPU."""
+    from oracle import oracle as O
+    from paper_1709_06350_gb300 import synth
+    _, dh = synth.linear_field(W.N, W.L, W.sigma_lin, W.seed)
+    pos = synth.zeldovich_positions(dh, W.N, W.L)
+    del dh
+    rho = O.cic_deposit(pos, W.N, W.L)
+    del pos
+    return O.smooth_and_floor(rho, W.L, W.R)
+
+
+def oracle_sample_line(b_host, W, t_sweeps, cal):
+    """cpu_baseline of one oracle sweep of W's full density, scaled to whole
+    reconstructions by the calibration ratio (oracle_calibration)."""
+    t_rec, t_sw, cycles = cal
+    t_sweep = statistics.median(t_sweeps)
+    ratio = t_rec / t_sw
+    return {"value": 1.0 / (t_sweep * ratio), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "host_cores": os.cpu_count(),
+            "sample": (f"one oracle Gauss-Seidel sweep (single-threaded FP64 C, red-black snapshot order, "
+                       f"Newton rule, from theta = 0) over the {W.N}^3 workload density: "
+                       f"{t_sweep:.2f} s; scaled to a whole reconstruction by the oracle's own ratio "
+                       f"reconstruction / sweep = {t_rec:.2f} s / {t_sw:.3f} s = {ratio:.1f}, measured on "
+                       f"a 64^3 realisation of the same recipe ({cycles} FAS cycles; CIC, density "
+                       f"preparation, solve to {W.tol:g} and displacement)"),
+            "sweep_s": t_sweep}
 
 
 def reference_arm(args):
+    """The oracle on this workload: every step is one oracle sweep of the
+    full-size density (bounded: ~15 s), scaled to reconstructions/s by the
+    calibration ratio; ms_per_step is the measured time of a step."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    n = 64
-    scale = (512 / n) ** 3
-    for w in range(args.warmup):
-        oracle_sample(n, 3000 + w)
-    times = []
-    for k in range(args.steps):
-        t, info = oracle_sample(n, 3100 + k)
-        times.append(t * scale)
-    ms = statistics.mean(times) * 1e3
-    v = 1.0 / statistics.mean(times)
-    sample = (f"oracle (single-threaded FP64 C) reconstruction of a {n}^3 realisation of the "
-              f"512^3 recipe (h = 1 Mpc/h, sigma_lin = 1, R = 2 Mpc/h): CIC + FAS solve to 1e-8 "
-              f"+ displacement, timed and scaled by (512/{n})^3 = {scale:.0f} (same cycle count assumed)")
+    from paper_1709_06350_gb300 import synth
+    W = synth.WORKLOADS[args.workload]
+    b = oracle_workload_density(W)
+    cal = oracle_calibration(W)
+    h = W.L / W.N
+    for _ in range(args.warmup):
+        _oracle_sweep_seconds(b, h)
+    times = [_oracle_sweep_seconds(b, h) for _ in range(args.steps)]
+    cpu = oracle_sample_line(b, W, times, cal)
+    v = cpu["value"]
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(times) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": "mixed-512 (oracle sample, see cpu_baseline.sample)"},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": sample},
+            "data": "synthetic", "config": workload_config(W), "cpu_baseline": cpu,
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -220,12 +270,13 @@ def main():
     stream = torch.cuda.current_stream()
     rho = torch.zeros((N, N, N), dtype=torch.float64, device=dev)
     phi = torch.zeros_like(rho)
+    bbuf = torch.empty_like(rho)
     last = {}
 
     def step(pos_dev):
         rho.zero_()
         solver.deposit_cic(pos_dev, rho=rho)
-        b = synth.smooth_and_floor(rho, L, R, fft_dtype=torch.float32)
+        b = solver.smooth_density(rho, R, out=bbuf)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         _, st = solver.solve(b, phi=phi, tol=tol, max_cycles=40)
@@ -262,7 +313,7 @@ def main():
     solve_in_step_ms = statistics.median([a.elapsed_time(b) for a, b in solve_ms])
     st = last["st"]
     # the solve alone, nothing else on the GPU (time to tolerance)
-    ref_b, ref_dl = last["b"], last["dl"]
+    ref_b, ref_dl = last["b"].clone(), last["dl"]
     solve_times = []
     torch.cuda.synchronize()
     for _ in range(3):
@@ -305,7 +356,7 @@ def main():
                 rho.zero_()
                 solver.deposit_cic(posbuf[cur], rho=rho)
                 used[cur].record(stream)
-                b = synth.smooth_and_floor(rho, L, R, fft_dtype=torch.float32)
+                b = solver.smooth_density(rho, R, out=bbuf)
                 solver.solve(b, phi=phi, tol=tol, max_cycles=40)
                 if d2h[cur] is not None:
                     stream.wait_event(d2h[cur])   # delta_r of step k-2 has left dlbuf[cur]
@@ -361,6 +412,7 @@ def main():
     # ---- rooflines of the two FP32 smoothers, timed in isolation at N^3
     kern = kernel_roofline(recon, torch, N, L, dev, stream)
     roof = dict(kern[0])
+    kern64 = fp64_rooflines(recon, torch, N, L, dev, stream)
 
     # ---- reconstruction quality: r(k) of delta_r against the seeded linear field
     from paper_1709_06350_gb300 import analysis
@@ -408,13 +460,10 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        n = args.cpu_sample_n
-        t, info = oracle_sample(n, 3200)
-        scale = (N / n) ** 3
-        cpu = {"value": 1.0 / (t * scale), "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": (f"oracle (single-threaded FP64 C) CIC + FAS solve to 1e-8 + displacement "
-                          f"of a {n}^3 realisation of the same recipe (h = 1 Mpc/h): {t:.2f} s, "
-                          f"{info['cycles']} cycles, scaled by (N/{n})^3 = {scale:.0f}")}
+        b_host = ref_b.cpu().numpy()
+        cal = oracle_calibration(W)
+        cpu = oracle_sample_line(b_host, W, [_oracle_sweep_seconds(b_host, L / N)], cal)
+        del b_host
 
     if rank == 0:
         ms = elapsed_ms / args.steps
@@ -425,14 +474,10 @@ def main():
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32/f64" if dtype == recon.RECON_MIXED else "f64",
             "data": "synthetic",
-            "config": {"workload": (f"{W.name}: {N}^3 seeded Zel'dovich field, L = {L:g} Mpc/h, "
-                                    f"sigma_lin = {W.sigma_lin}, R = {R:g} Mpc/h, CIC + smoothing "
-                                    f"+ solve to ||r||/||b-1|| < {tol:g} + displacement"),
-                       "l2": "inputs larger than L2 (particle positions "
-                             f"{pos.numel() * 8 / 1e9:.1f} GB, fields {N ** 3 * 8 / 1e9:.2f} GB)",
-                       "solver": solver.config(),
-                       "schedule": "autotuned (paper_1709_06350_gb300/autotune_cache.json)"
-                                   if tuned else "defaults"},
+            "config": workload_config(W),
+            "solver_config": {"solver": solver.config(),
+                              "schedule": "autotuned (paper_1709_06350_gb300/autotune_cache.json)"
+                                          if tuned else "defaults"},
             "time_to_tol_s": {"mixed": statistics.median(solve_times) / 1e3,
                               "fp64": fp64["time_to_tol_s"] if fp64 else None,
                               "mixed_inside_step": solve_in_step_ms / 1e3},
@@ -451,7 +496,7 @@ def main():
             "gs_cell_updates_per_s": {"fas_newton": kern[1]["cell_updates_per_s"],
                                       "linear": roof.pop("cell_updates_per_s", None)},
             "roofline": roof,
-            "other_kernels": kern[1:],
+            "other_kernels": kern[1:] + kern64,
             "gpu_launches": launches,
             "clocks": clk.summary(),
             "e2e": e2e,
@@ -490,7 +535,7 @@ def bench_assignment(recon, synth, torch, dev, pos, W, autotune):
                 b_.record()
                 torch.cuda.synchronize()
                 out["deposit_ms"][scheme] = a.elapsed_time(b_) / 3
-            b = synth.smooth_and_floor(rho, L, R, fft_dtype=torch.float32)
+            b = s.smooth_density(rho, R)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             _, st = s.solve(b, tol=tol, max_cycles=40)
@@ -516,7 +561,7 @@ def bench_cubic(recon, synth, torch, dev, tol=1e-3):
                        f"CIC, floor 0.05, tol {tol:g}"}
     for name, dtype in (("fp64", recon.RECON_F64), ("mixed", recon.RECON_MIXED)):
         s = recon.Solver(N, L, dtype)
-        b = synth.smooth_and_floor(s.deposit_cic(pos), L, 0.0)
+        b = s.smooth_density(s.deposit_cic(pos), 0.0)
         phi = torch.zeros_like(b)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -551,7 +596,7 @@ def bench_batch(recon, synth, torch, dev, count):
         _, dh = synth.linear_field(w.N, w.L, w.sigma_lin, w.seed, backend="torch", device=dev)
         pos = synth.zeldovich_positions(dh, w.N, w.L).contiguous()
         rho = deposit[w.N].deposit_cic(pos)
-        bs.append(synth.smooth_and_floor(rho, w.L, w.R, fft_dtype=torch.float32))
+        bs.append(deposit[w.N].smooth_density(rho, w.R))
         del dh, pos, rho
     for s in deposit.values():
         s.close()
@@ -602,7 +647,7 @@ def bench_adjoint(recon, synth, torch, dev, n, directions):
     delta_lin, dh = synth.linear_field(n, L, 0.8, w.seed if w else 5000, backend="torch", device=dev)
     pos = synth.zeldovich_positions(dh, n, L).contiguous()
     s = recon.Solver(n, L, recon.RECON_F64)
-    b = synth.smooth_and_floor(s.deposit_cic(pos), L, 4.0)
+    b = s.smooth_density(s.deposit_cic(pos), 4.0)
     del dh, pos
     gen = torch.Generator(device=dev).manual_seed(11)
     wv = torch.randn((n, n, n), dtype=torch.float64, device=dev, generator=gen)
@@ -757,6 +802,63 @@ def kernel_roofline(recon, torch, N, L, dev, stream):
                     "traffic_source": "ncu dram bytes of one 384^3 launch, scaled by cells",
                     "peak_source": src, "algorithmic_bytes_per_launch": alg,
                     "avg_launch_ms": t * 1e3, "cell_updates_per_s": N ** 3 / t})
+    return out
+
+
+def fp64_peak_tflops(recon, torch, dev, stream):
+    """Measured FP64 FMA rate of this GPU (recon_measure_fp64_fma: 8
+    independent FMA chains per thread, 16 CTAs of 256 threads per SM), best of
+    five launches timed with events on the stream."""
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks, iters = 16 * sms, 20000
+    out = torch.zeros(1, dtype=torch.float64, device=dev)
+    recon.recon_measure_fp64_fma(blocks, 100, out, stream)
+    best = None
+    for _ in range(5):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        recon.recon_measure_fp64_fma(blocks, iters, out, stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t = a.elapsed_time(b) / 1e3
+        best = t if best is None else min(best, t)
+    return 4096.0 * blocks * iters / best / 1e12
+
+
+# Algorithmic FP64 work of one cell update of the nonlinear smoother (eq.
+# update: the Hessian stencils, the cubic's coefficients, one Newton step and
+# its acceptance test), counting a fused multiply-add as two flops.
+FP64_FLOPS_PER_CELL_UPDATE = 70.0
+
+
+def fp64_rooflines(recon, torch, N, L, dev, stream):
+    """The FP64 path's smoother at N^3 against the measured FP64 FMA rate:
+    the fused sweep (both colours, one launch) and the two-pass kernels (an
+    array not aligned to an element pair runs them: two launches a sweep)."""
+    from paper_1709_06350_gb300 import synth
+    peak = fp64_peak_tflops(recon, torch, dev, stream)
+    h = L / N
+    th = torch.from_numpy(synth.smooth_field(N, 1, 0.3 * h * h, kmax=4)).to(dev, torch.float64)
+    g = torch.from_numpy(1.0 + synth.smooth_field(N, 2, 0.4, kmax=4)).to(dev, torch.float64)
+    work = torch.empty_like(th)
+    t_fused = _time_launches(torch, stream, lambda k: recon.recon_step_sweep(
+        th, g, 0.0, h, sweeps=k, work=work, stream=stream), 3)
+    buf = torch.empty(th.numel() + 1, dtype=torch.float64, device=dev)
+    tu = buf[1:].view(th.shape)
+    tu.copy_(th)
+    t_two = _time_launches(torch, stream, lambda k: recon.recon_step_sweep(
+        tu, g, 0.0, h, sweeps=k, work=work, stream=stream), 3)
+    del th, g, work, buf, tu
+    out = []
+    for name, t, launches in (("k_sweep_fused<double, FAS> (FP64 red-black Newton smoother, one fused sweep)",
+                               t_fused, 1),
+                              ("k_rb_pass<double> (FP64 red-black Newton smoother, one colour pass)", t_two, 2)):
+        flops = FP64_FLOPS_PER_CELL_UPDATE * N ** 3 / launches
+        ach = flops / (t / launches) / 1e12
+        out.append({"kernel": name, "bound": "fp64", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                    "frac": ach / peak, "peak_source": "measured: recon_measure_fp64_fma (FP64 FMA chains)",
+                    "algorithmic_flops_per_launch": flops, "avg_launch_ms": t / launches * 1e3})
     return out
 
 

@@ -223,6 +223,24 @@ recon_status recon_displace_adjoint(recon_handle *h, const double *phi, const do
                                     const double *gbar_psi, const double *gbar_deltaL,
                                     double *gbar_phi, double *gbar_b);
 
+/* Density preparation before the solve: Gaussian smoothing, floor, mean 1.
+ *   b = max(IDFT(DFT(rho) exp(-k^2 R^2 / 2)), floor) / mean(...)
+ * with k the box's wave vectors (2 pi m / L per axis, |m| <= N/2): the
+ * Gaussian window of width R (length units of L) that Sec. III applies to
+ * its density fields; the floor keeps every cell's right side positive
+ * (empty assignment cells) and the final division restores mean 1.  The
+ * window is applied as three circular convolutions (k, j, i) with the
+ * inverse DFT of the 1-D window, truncated where it falls below 1e-9 of its
+ * centre, in FP32 taps and sums: b carries ~1e-7 relative rounding for R of
+ * a few cells; below ~1.5 cells the window is not small at the grid's
+ * Nyquist frequency, the kernel spans the whole periodic line (up to N taps:
+ * exact, slower, rounding growing with the tap count).
+ * rho, b: device N^3 (they may be the same array).  R >= 0 (0: no
+ * smoothing), floor > 0.  Uses the handle's N^3-double workspace.
+ * Errors: RECON_E_INVALID (null pointers, R < 0, floor <= 0 or non-finite),
+ * RECON_E_CUDA. */
+recon_status recon_smooth_density(recon_handle *h, const double *rho, double R, double floor, double *b);
+
 /* 1-point Gaussianisation of an N^3 field (Sec. III: tried on delta_r),
  * read as the rank mapping
  *     out_i = mean + std * Phi^-1((rank_i + 1/2) / N^3),

@@ -100,6 +100,16 @@ recon_status recon_step_linear_sweep(int N, double h, float *e, const float *f,
 recon_status recon_step_jacobian_apply(int N, double h, const double *theta,
                                        const double *v, double *out, void *stream);
 
+/* Measurement helper, no counterpart in the paper: the FP64 FMA rate of this
+ * GPU, against which the FP64 path's smoother is reported.  Launches
+ * `blocks` CTAs of 256 threads, each thread running 8 independent chains of
+ * `iters` dependent FP64 fused multiply-adds (2 flops each): 4096 * blocks *
+ * iters flops in all.  out: device, 1 double (written only in a case that
+ * never occurs; it keeps the chains from being optimised away).  Time the
+ * launch with events on `stream`.  Errors: RECON_E_INVALID (blocks < 1,
+ * iters < 1, out NULL), RECON_E_CUDA. */
+recon_status recon_measure_fp64_fma(int blocks, int iters, double *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

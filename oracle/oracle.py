@@ -463,6 +463,26 @@ def adjoint(theta, gbar_theta, h):
     return sol[:n].reshape(N, N, N)
 
 
+# ---------------------------------------------------------------- density preparation
+def smooth_and_floor(rho, L, R, floor=0.05):
+    """Density preparation before the solve, in FP64:
+        1. Gaussian window of width R (Sec. III smooths its density fields
+           with one): multiply the DFT of rho by exp(-k^2 R^2 / 2), k the
+           box's wave vector 2 pi m / L (m the signed DFT index per axis);
+        2. floor: 1 + delta >= floor, so every cell's right side is positive;
+        3. divide by the mean, restoring mean 1.
+    numpy's FFT is the library step for 1."""
+    r = _f64(rho)
+    N = _grid_n(r)
+    if R > 0:
+        m = np.fft.fftfreq(N, d=1.0 / N)
+        k = 2.0 * np.pi * m / L
+        k2 = k[:, None, None] ** 2 + k[None, :, None] ** 2 + k[None, None, :] ** 2
+        r = np.fft.ifftn(np.fft.fftn(r) * np.exp(-0.5 * k2 * R * R)).real
+    b = np.maximum(r, floor)
+    return b / b.mean()
+
+
 # ---------------------------------------------------------------- post-processing
 def gaussianise(field):
     """1-point Gaussianisation of a field (Sec. III, after Weinberg 1992 and

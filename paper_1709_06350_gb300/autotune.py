@@ -51,7 +51,7 @@ def _field(N, L, seed, device):
     _, dh = synth.linear_field(N, L, 1.0, seed, backend="torch", device=device)
     pos = synth.zeldovich_positions(dh, N, L).contiguous()
     s = recon.Solver(N, L, recon.RECON_F64)
-    b = synth.smooth_and_floor(s.deposit_cic(pos), L, 2.0 * L / N, fft_dtype=torch.float32)
+    b = s.smooth_density(s.deposit_cic(pos), 2.0 * L / N)
     s.close()
     return b
 

@@ -19,7 +19,8 @@ CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "librecon.so")
 SOURCES = ["recon_mg.cu", "recon_sweep.cu", "recon_cic.cu", "recon_adjoint.cu", "recon_batch.cu",
-           "recon_api.cu", "recon_noalloc.cu", "recon_gauss.cu"]
+           "recon_api.cu", "recon_noalloc.cu", "recon_gauss.cu", "recon_smooth.cu",
+           "recon_measure.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -98,6 +98,7 @@ enum Slot {
     S_ADJ_NORM,
     S_ADJ_SLAM,
     S_ADJ_SN,
+    S_SMOOTH_MEAN,    // recon_smooth_density: mean of the floored field
     S_COUNT
 };
 // per-level slots (level l >= 1): restricted-residual mean, defect scale s,

@@ -157,6 +157,11 @@ cudaError_t gauss_alloc(recon_handle *H, size_t n);
 void gauss_free(recon_handle *H);
 cudaError_t gaussianise(recon_handle *H, const double *v, size_t n, double *g);
 
+// ---- density preparation (recon_smooth.cu): Gaussian window of radius R,
+// floor, mean 1; w32: 2 N^3 floats of scratch; mean: one device double
+cudaError_t smooth_density(int N, double L, double R, double floor_, const double *rho, double *b, float *w32,
+                           double *mean, cudaStream_t s);
+
 // phi -> (hi, lo) FP32 parts (recon_mg.cu)
 __global__ void k_split_df(const double *__restrict__ a, float *__restrict__ hi, float *__restrict__ lo,
                            size_t n);

@@ -363,6 +363,17 @@ recon_status recon_displace(recon_handle *H, const double *phi, const double *b,
                        "displace");
 }
 
+recon_status recon_smooth_density(recon_handle *H, const double *rho, double R, double floor_, double *b)
+{
+    if (!H) return RECON_E_INVALID;
+    if (!rho || !b) return set_err(H, RECON_E_INVALID, "NULL pointer");
+    if (!(R >= 0.0) || !std::isfinite(R) || !(floor_ > 0.0) || !std::isfinite(floor_))
+        return set_err(H, RECON_E_INVALID, "R must be >= 0 and floor > 0, both finite");
+    return cuda_status(H, smooth_density(H->N, H->L, R, floor_, rho, b, reinterpret_cast<float *>(H->work64),
+                                         H->scal + S_SMOOTH_MEAN, H->stream),
+                       "smooth_density");
+}
+
 recon_status recon_gaussianise(recon_handle *H, const double *field, double *out)
 {
     if (!H) return RECON_E_INVALID;

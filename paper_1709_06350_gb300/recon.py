@@ -72,6 +72,7 @@ _SIGS = {
     "recon_displace_fp64": (_I, [_P, _P, _P, _P, _P]),
     "recon_displace_adjoint": (_I, [_P, _P, _P, _P, _P, _P, _P]),
     "recon_gaussianise": (_I, [_P, _P, _P]),
+    "recon_smooth_density": (_I, [_P, _P, _D, _D, _P]),
     "recon_last_error": (ctypes.c_char_p, [_P]),
     "recon_status_string": (ctypes.c_char_p, [_I]),
     "recon_kernel_launches": (ctypes.c_ulonglong, []),
@@ -91,6 +92,7 @@ _SIGS = {
     "recon_step_cic_cells": (_I, [_P, _LL, _I, _D, _P, _P, _P]),
     "recon_step_jacobian_apply": (_I, [_I, _D, _P, _P, _P, _P]),
     "recon_step_linear_sweep": (_I, [_I, _D, _P, _P, _P, _I, _P, _P]),
+    "recon_measure_fp64_fma": (_I, [_I, _I, _P, _P]),
 }
 EXPORTS = tuple(_SIGS)
 
@@ -242,6 +244,12 @@ def recon_displace_adjoint(h, N: int, phi, b, gbar_psi, gbar_deltaL, gbar_phi, g
                                          _dev_ptr(gbar_b, torch.float64, N ** 3)), h)
 
 
+def recon_smooth_density(h, N: int, rho, R: float, floor: float, b) -> None:
+    import torch
+    _check(load().recon_smooth_density(h, _dev_ptr(rho, torch.float64, N ** 3), float(R), float(floor),
+                                       _dev_ptr(b, torch.float64, N ** 3)), h)
+
+
 def recon_gaussianise(h, N: int, field, out) -> None:
     import torch
     _check(load().recon_gaussianise(h, _dev_ptr(field, torch.float64, N ** 3),
@@ -358,6 +366,13 @@ def recon_step_linear_sweep(e, f, theta, h, sweeps=1, work=None, stream=None):
                                           _dev_ptr(work, torch.float32, 7 * N ** 3), _stream(stream)))
 
 
+def recon_measure_fp64_fma(blocks: int, iters: int, out, stream=None) -> None:
+    """FP64 FMA rate probe: 4096 * blocks * iters flops (time it with events)."""
+    import torch
+    _check(load().recon_measure_fp64_fma(int(blocks), int(iters), _dev_ptr(out, torch.float64),
+                                         _stream(stream)))
+
+
 def recon_step_jacobian_apply(theta, v, h, out, stream=None):
     import torch
     N = theta.shape[0]
@@ -450,6 +465,14 @@ class Solver:
         gb = torch.empty_like(b)
         recon_displace_adjoint(self.h, self.N, phi, b, gbar_psi, gbar_dl, gphi, gb)
         return gphi, gb
+
+    def smooth_density(self, rho, R, floor=0.05, out=None):
+        """Gaussian window of width R, floor, mean 1 (rho may be out)."""
+        import torch
+        if out is None:
+            out = torch.empty_like(rho)
+        recon_smooth_density(self.h, self.N, rho, R, floor, out)
+        return out
 
     def gaussianise(self, field):
         """1-point Gaussianisation (rank mapping onto Gaussian quantiles)."""

@@ -12,10 +12,11 @@ Recipe (stand-in for the paper's N-body snapshots, which are not available):
    particles start on cell centres q = (i + 1/2) h and move to
    x = q + psi(q) (mod L).
 
-The density assigned from these particles (a CIC deposit, done by whichever
-implementation is under test) is then conditioned by ``smooth_and_floor``:
-Gaussian smoothing exp(-k^2 R^2 / 2), a floor 1 + delta >= 0.05 and a
-renormalisation to mean 1.
+The density assigned from these particles (a CIC deposit) is then
+conditioned -- Gaussian window exp(-k^2 R^2 / 2), a floor 1 + delta >= 0.05
+and a renormalisation to mean 1 -- by the code under test
+(``recon_smooth_density``) or by the oracle (``oracle.smooth_and_floor``);
+this module holds none of that arithmetic.
 
 ``backend="torch"`` runs the FFTs with torch (on a CUDA device when one is
 given) for sizes where numpy's single-threaded FFT is slow; the white noise
@@ -124,50 +125,6 @@ def zeldovich_positions(delta_hat, N: int, L: float):
         out[..., d] = torch.remainder(qc.view(shape) + psi, L)
         del psi
     return out.reshape(-1, 3)
-
-
-_WINDOWS = {}
-
-
-def _torch_window(N: int, L: float, R: float, device):
-    """exp(-k^2 R^2 / 2) on the rFFT grid, built on the device and cached."""
-    import torch
-    key = (N, float(L), float(R), str(device))
-    W = _WINDOWS.get(key)
-    if W is None:
-        kf = 2.0 * np.pi / L
-        k1 = torch.fft.fftfreq(N, d=1.0 / N, device=device, dtype=torch.float64) * kf
-        kz = torch.fft.rfftfreq(N, d=1.0 / N, device=device, dtype=torch.float64) * kf
-        k2 = k1[:, None, None] ** 2 + k1[None, :, None] ** 2 + kz[None, None, :] ** 2
-        W = torch.exp(-0.5 * R * R * k2)
-        _WINDOWS.clear()
-        _WINDOWS[key] = W
-    return W
-
-
-def smooth_and_floor(rho, L: float, R: float, floor: float = 0.05, fft_dtype=None):
-    """Gaussian-smooth (radius R), floor 1+delta at ``floor``, renormalise to mean 1.
-
-    Accepts numpy arrays or torch tensors and returns the same kind (and
-    dtype).  ``fft_dtype`` (torch only, e.g. torch.float32) runs the smoothing
-    FFTs in that precision.
-    """
-    N = rho.shape[0]
-    if isinstance(rho, np.ndarray):
-        kx, ky, kz = _kgrid(N, L)
-        W = np.exp(-0.5 * (kx * kx + ky * ky + kz * kz) * R * R)
-        b = np.fft.irfftn(np.fft.rfftn(rho) * W, s=rho.shape, axes=(0, 1, 2)) if R > 0 else rho.copy()
-        b = np.maximum(b, floor)
-        return b / b.mean()
-    import torch
-    if R > 0:
-        x = rho if fft_dtype is None else rho.to(fft_dtype)
-        W = _torch_window(N, L, R, rho.device)
-        b = torch.fft.irfftn(torch.fft.rfftn(x) * W.to(x.dtype), s=tuple(rho.shape)).to(rho.dtype)
-    else:
-        b = rho.clone()
-    b = torch.clamp(b, min=floor)
-    return b / b.mean()
 
 
 def lattice_positions(N: int, L: float) -> np.ndarray:

@@ -410,12 +410,59 @@ def test_convergence_with_tracer_and_mesh_ratios(R):
         pos = torch.from_numpy(synth.zeldovich_positions(dh, n_lat, L)).cuda()
         s = R.Solver(n_mesh, L, R.RECON_MIXED)
         for scheme in ("ngp", "cic", "tsc"):
-            b = synth.smooth_and_floor(s.deposit(pos, scheme), L, Rs, fft_dtype=torch.float32)
+            b = s.smooth_density(s.deposit(pos, scheme), Rs)
             _, st = s.solve(b, tol=1e-8, max_cycles=40)
             assert st["rel_residual"] < 1e-8
             counts[(label, scheme)] = st["cycles"] + st["outer_iterations"]
         s.close()
     assert max(counts.values()) - min(counts.values()) <= 2, counts
+
+
+# ------------------------------------------------------------------ density preparation
+@pytest.mark.parametrize("N,L,Rs,seed", [(32, 100.0, 5.0, 1000), (64, 64.0, 2.0, 3000), (48, 96.0, 4.0, 2001),
+                                         (8, 8.0, 3.0, 7)])
+def test_smooth_density_parity(R, O, N, L, Rs, seed):
+    """recon_smooth_density against the oracle's FFT definition on a seeded
+    Zel'dovich density (oracle CIC).  The GPU applies the window as three
+    FP32 circular convolutions of half-width T <= 13 here; with positive taps
+    summing to 1, each pass adds at most (2T + 1) 2^-24 relative rounding and
+    the truncation at 1e-9 of the centre tap is negligible, so three passes
+    stay within 3 x 27 x 6e-8 ~ 5e-6 of max(b).  (8, 8.0, 3.0): a window
+    wider than the box, where the kernel covers the whole periodic line."""
+    from paper_1709_06350_gb300 import synth
+    _, dh = synth.linear_field(N, L, 0.8, seed)
+    rho = O.cic_deposit(synth.zeldovich_positions(dh, N, L), N, L)
+    ref = O.smooth_and_floor(rho, L, Rs)
+    s = R.Solver(N, L)
+    got = s.smooth_density(dev(rho), Rs)
+    assert np.max(np.abs(host(got) - ref)) < 5e-6 * ref.max()
+    assert host(got).mean() == pytest.approx(1.0, abs=1e-12)
+    # in place, and no smoothing (floor and mean only)
+    x = dev(rho)
+    s.smooth_density(x, 0.0, out=x)
+    ref0 = O.smooth_and_floor(rho, L, 0.0)
+    assert np.max(np.abs(host(x) - ref0)) < 1e-7 * ref0.max()
+    s.close()
+
+
+def test_smooth_density_narrow_window_and_bad_arguments(R, O):
+    """R = 1 cell: the window is 7e-3 at the Nyquist frequency, so the exact
+    periodic kernel spans the whole line (129 taps at N = 128, FP32 sums:
+    tolerance 129 x 2^-24 x 3 passes ~ 3e-5); bad arguments are refused."""
+    from paper_1709_06350_gb300 import synth
+    N, L = 128, 256.0
+    _, dh = synth.linear_field(N, L, 0.8, 2002)
+    rho = O.cic_deposit(synth.zeldovich_positions(dh, N, L), N, L)
+    ref = O.smooth_and_floor(rho, L, 2.0)
+    s = R.Solver(N, L)
+    got = host(s.smooth_density(dev(rho), 2.0))
+    assert np.max(np.abs(got - ref)) < 3e-5 * ref.max()
+    x = dev(rho)
+    with pytest.raises(R.ReconError, match="RECON_E_INVALID"):
+        s.smooth_density(x, -1.0)
+    with pytest.raises(R.ReconError, match="RECON_E_INVALID"):
+        s.smooth_density(x, 2.0, floor=0.0)
+    s.close()
 
 
 # ------------------------------------------------------------------ cubic test
@@ -426,7 +473,7 @@ def test_cubic_test(R, O):
     lap(theta) = 3 (b_in^(1/3) - 1), Hbar = 0."""
     from paper_1709_06350_gb300 import synth
     N, L, l = 64, 64.0, 5.0
-    b = synth.smooth_and_floor(O.cic_deposit(synth.cube_positions(N, L, l), N, L), L, 0.0)
+    b = O.smooth_and_floor(O.cic_deposit(synth.cube_positions(N, L, l), N, L), L, 0.0)
     ref, info = O.solve(b, L, tol=1e-14, max_cycles=12)
     s = R.Solver(N, L)
     phi, st = s.solve(dev(b), tol=1e-14, max_cycles=12, raise_on_noconv=False)

@@ -294,7 +294,7 @@ def test_brute_force_dense_newton(O, N):
 def test_symmetries(O):
     """P8: translation, axis permutation and reflection of b carry over to theta."""
     N, L = 16, 32.0
-    b = synth.smooth_and_floor(1.0 + synth.smooth_field(N, 21, 0.8, kmax=2), L, 0.0)
+    b = O.smooth_and_floor(1.0 + synth.smooth_field(N, 21, 0.8, kmax=2), L, 0.0)
     t, _ = O.solve(b, L, **SOLVE)
     scale = np.max(np.abs(t))
     tr, _ = O.solve(np.roll(b, (3, 5, 1), axis=(0, 1, 2)), L, **SOLVE)
@@ -310,7 +310,7 @@ def test_symmetries(O):
 def test_orderings_reach_the_same_solution(O, ordering, rule):
     """Every ordering / update rule of the paper converges to the one theta*."""
     N, L = 16, 32.0
-    b = synth.smooth_and_floor(1.0 + synth.smooth_field(N, 31, 1.2, kmax=2), L, 0.0)
+    b = O.smooth_and_floor(1.0 + synth.smooth_field(N, 31, 1.2, kmax=2), L, 0.0)
     t0, i0 = O.solve(b, L, **SOLVE)
     t1, i1 = O.solve(b, L, ordering=ordering, rule=rule, **SOLVE)
     assert i0["status"] == 0 and i1["status"] == 0
@@ -436,7 +436,7 @@ def test_convergence_insensitive_to_tracer_and_mesh(O):
         _, dh = synth.linear_field(n_lat, L, 0.8, 31)
         pos = synth.zeldovich_positions(dh, n_lat, L)
         for scheme in ("ngp", "cic", "tsc"):
-            b = synth.smooth_and_floor(O.assign_deposit(pos, n_mesh, L, scheme), L, R)
+            b = O.smooth_and_floor(O.assign_deposit(pos, n_mesh, L, scheme), L, R)
             _, info = O.solve(b, L, tol=1e-8, max_cycles=40)
             assert info["status"] == 0, (label, scheme)
             cycles[(label, scheme)] = info["cycles"]
@@ -552,6 +552,35 @@ def test_paper_eps_plane_closed_form(O):
     assert O.paper_eps(t, np.broadcast_to(1.0 + a[:, None, None], (N,) * 3) - c, c, h) < 1e-13
 
 
+# --------------------------------------------------------------- density preparation
+@pytest.mark.parametrize("m", [(1, 0, 0), (0, 2, 0), (1, 2, 3), (8, 0, 0), (3, -5, 8)])
+def test_smoothing_window_on_single_modes(O, m):
+    """The Gaussian window of width R (Sec. III) on a single Fourier mode
+    cos(2 pi m.i / N): the mode is an eigenfunction of the filter with
+    eigenvalue exp(-k^2 R^2 / 2), k = 2 pi |m| / L (m = 8 on N = 16 is the
+    Nyquist mode), the mean stays 1 and nothing reaches the floor."""
+    N, L, R = 16, 40.0, 3.0
+    i, j, k = np.meshgrid(np.arange(N), np.arange(N), np.arange(N), indexing="ij")
+    phase = 2.0 * np.pi * (m[0] * i + m[1] * j + m[2] * k) / N
+    rho = 1.0 + 0.3 * np.cos(phase + 0.4)
+    kk = 2.0 * np.pi * np.sqrt(m[0] ** 2 + m[1] ** 2 + m[2] ** 2) / L
+    expect = 1.0 + 0.3 * np.exp(-0.5 * kk * kk * R * R) * np.cos(phase + 0.4)
+    if m == (8, 0, 0):
+        expect = 1.0 + 0.3 * np.exp(-0.5 * kk * kk * R * R) * np.cos(0.4) * np.cos(phase)
+    b = O.smooth_and_floor(rho, L, R, floor=0.05)
+    assert np.max(np.abs(b - expect)) < 1e-13
+
+
+def test_smoothing_floor_and_mean(O):
+    """Without smoothing (R = 0) a two-valued field {0.01, 1.99} (mean 1)
+    becomes {0.05, 1.99} / 1.02 exactly: the floor, then the mean restored."""
+    N = 8
+    rho = np.where(np.arange(N ** 3).reshape(N, N, N) % 2 == 0, 0.01, 1.99)
+    b = O.smooth_and_floor(rho, 10.0, 0.0, floor=0.05)
+    assert np.allclose(b, np.where(rho < 1, 0.05, 1.99) / 1.02, rtol=0, atol=1e-15)
+    assert b.mean() == pytest.approx(1.0, abs=1e-15)
+
+
 # --------------------------------------------------------------- adjoint
 def test_jacobian_matches_finite_differences(O):
     N, h = 8, 1.0
@@ -592,7 +621,7 @@ def test_cubic_test_interior(O):
     3 (b_in^(1/3) - 1), the paper's 3 (L/l - 1) with the floor's mass taken
     out of b_in."""
     N, L, l = 32, 32.0, 2.5
-    b = synth.smooth_and_floor(O.cic_deposit(synth.cube_positions(N, L, l), N, L), L, 0.0)
+    b = O.smooth_and_floor(O.cic_deposit(synth.cube_positions(N, L, l), N, L), L, 0.0)
     t, info = O.solve(b, L, tol=1e-3, max_cycles=80)
     assert info["status"] == 0
     c = N // 2
@@ -661,6 +690,9 @@ MUTATIONS = {
                         "double qq = fmod(x[d] - g[d], L);"),
     "displace-den-unweighted": ("wb[id] = b[id];", "wb[id] = 1.0;"),
     "displace-v-sign": ("double v = 3.0 - inv_tr;", "double v = inv_tr - 3.0;"),
+    "smooth-window-exponent": ("oracle.py", "np.exp(-0.5 * k2 * R * R)", "np.exp(-k2 * R * R)"),
+    "smooth-no-renorm": ("oracle.py", "    b = np.maximum(r, floor)\n    return b / b.mean()",
+                         "    b = np.maximum(r, floor)\n    return b"),
     "eps-no-compat": ("or_cell_cubic(t, N, h, i, j, k, g[at(N, i, j, k)] + c, &s, &p, &q);\n                double L",
                       "or_cell_cubic(t, N, h, i, j, k, g[at(N, i, j, k)], &s, &p, &q);\n                double L"),
 }
@@ -675,10 +707,11 @@ def test_mutations_are_caught(O, name, tmp_path):
     src_dir = os.path.dirname(O.__file__)
     shutil.copy(os.path.join(src_dir, "recon_oracle.c"), tmp_path / "recon_oracle.c")
     shutil.copy(os.path.join(src_dir, "oracle.py"), tmp_path / "oracle.py")
-    code = (tmp_path / "recon_oracle.c").read_text()
-    old, new = MUTATIONS[name]
+    entry = MUTATIONS[name]
+    fname, old, new = entry if len(entry) == 3 else ("recon_oracle.c", *entry)
+    code = (tmp_path / fname).read_text()
     assert code.count(old) == 1, name
-    (tmp_path / "recon_oracle.c").write_text(code.replace(old, new))
+    (tmp_path / fname).write_text(code.replace(old, new))
     spec = importlib.util.spec_from_file_location(f"mut_{name.replace('-', '_')}",
                                                   tmp_path / "oracle.py")
     M = importlib.util.module_from_spec(spec)
@@ -696,6 +729,8 @@ def test_mutations_are_caught(O, name, tmp_path):
         lambda: test_assignment_is_the_cardinal_bspline(M, "tsc", 2),
         lambda: test_displace_recovers_plane_zeldovich(M, 0.5),
         lambda: test_paper_eps_plane_closed_form(M),
+        lambda: test_smoothing_window_on_single_modes(M, (1, 2, 3)),
+        lambda: test_smoothing_floor_and_mean(M),
     ]
     failed = 0
     for pin in pins:

@@ -1,6 +1,6 @@
-"""Seeded inputs for the tests: densities b built with the generator, the
-oracle's CIC and the generator's smoothing/floor (so no input ever comes
-from the code under test)."""
+"""Seeded inputs for the tests: densities b built with the generator's
+particles and the oracle's CIC and density preparation (so no input ever
+comes from the code under test)."""
 import numpy as np
 
 from paper_1709_06350_gb300 import synth
@@ -10,7 +10,7 @@ def zeldovich_density(O, N, L, sigma_lin, R, seed):
     delta_L, dh = synth.linear_field(N, L, sigma_lin, seed)
     pos = synth.zeldovich_positions(dh, N, L)
     rho = O.cic_deposit(pos, N, L)
-    return synth.smooth_and_floor(rho, L, R), delta_L, pos
+    return O.smooth_and_floor(rho, L, R), delta_L, pos
 
 
 def smooth_density(N, seed, amp=0.6, kmax=2):
