@@ -48,6 +48,7 @@ def parse():
     p.add_argument("--no-adjoint", action="store_true")
     p.add_argument("--no-assignment", action="store_true")
     p.add_argument("--no-cubic", action="store_true")
+    p.add_argument("--no-1024", action="store_true", help="skip the 1024^3 time-to-tolerance section")
     p.add_argument("--batch-count", type=int, default=64)
     p.add_argument("--adjoint-n", type=int, default=256)
     p.add_argument("--fd-directions", type=int, default=32)
@@ -453,6 +454,15 @@ def main():
         torch.cuda.empty_cache()
         cubic = bench_cubic(recon, synth, torch, dev)
 
+    big = None
+    if not args.no_1024 and rank == 0 and args.workload == "mixed-512":
+        torch.cuda.empty_cache()
+        try:
+            big = bench_1024(recon, synth, torch, dev, stream, autotune)
+        except Exception as ex:   # reported, never fatal to the bench line
+            big = {"error": f"{type(ex).__name__}: {ex}"}
+        torch.cuda.empty_cache()
+
     adj = None
     if not args.no_adjoint and rank == 0:
         torch.cuda.empty_cache()
@@ -493,6 +503,7 @@ def main():
             "assignment": assign,
             "cubic_test": cubic,
             "adjoint": adj,
+            "mixed_1024": big,
             "gs_cell_updates_per_s": {"fas_newton": kern[1]["cell_updates_per_s"],
                                       "linear": roof.pop("cell_updates_per_s", None)},
             "roofline": roof,
@@ -548,6 +559,56 @@ def bench_assignment(recon, synth, torch, dev, pos, W, autotune):
         s.close()
     out["deposit_workload"] = f"{N}^3 particles on the {N}^3 mesh (mean 1)"
     return out
+
+
+def bench_1024(recon, synth, torch, dev, stream, autotune):
+    """The 1024^3 workload (L = 1024 Mpc/h, sigma_lin = 1, R = 2 Mpc/h): the
+    mixed solve's time to ||r|| / ||b - 1|| < 1e-8 (median of three, b on the
+    device), the FP64 GPU path on the same density, their difference, and
+    the two FP32 smoothers' rooflines at 1024^3."""
+    W = synth.WORKLOADS["mixed-1024"]
+    N, L = W.N, W.L
+    _, dh = synth.linear_field(N, L, W.sigma_lin, W.seed, backend="torch", device=dev)
+    pos = synth.zeldovich_positions(dh, N, L).contiguous()
+    del dh
+    s = recon.Solver(N, L, recon.RECON_MIXED)
+    autotune.apply(s, N, recon.RECON_MIXED)
+    b = s.smooth_density(s.deposit_cic(pos), W.R)
+    del pos
+    torch.cuda.empty_cache()
+    phi = torch.zeros_like(b)
+    _, st = s.solve(b, phi=phi, tol=W.tol, max_cycles=40)
+    times = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        _, st = s.solve(b, phi=phi, tol=W.tol, max_cycles=40)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        times.append(a0.elapsed_time(a1) / 1e3)
+    s.close()
+    s64 = recon.Solver(N, L, recon.RECON_F64)
+    p64 = torch.zeros_like(b)
+    torch.cuda.synchronize()
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    _, st64 = s64.solve(b, phi=p64, tol=W.tol, max_cycles=40)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    diff = float(torch.linalg.norm(p64 - phi) / torch.linalg.norm(p64))
+    s64.close()
+    del b, phi, p64
+    torch.cuda.empty_cache()
+    kern = kernel_roofline(recon, torch, N, L, dev, stream)
+    return {"workload": f"{W.name}: {N}^3, L = {L:g} Mpc/h, sigma_lin = {W.sigma_lin}, R = {W.R:g} Mpc/h",
+            "time_to_tol_s": {"mixed": statistics.median(times), "fp64": a0.elapsed_time(a1) / 1e3},
+            "mixed": {"fas_cycles": st["cycles"], "outer_iterations": st["outer_iterations"],
+                      "rel_residual": st["rel_residual"]},
+            "fp64": {"cycles": st64["cycles"], "rel_residual": st64["rel_residual"]},
+            "mixed_vs_fp64_rel_l2": diff,
+            "smoothers": [{k: v for k, v in x.items() if k in ("kernel", "avg_launch_ms", "achieved", "frac")}
+                          for x in kern]}
 
 
 def bench_cubic(recon, synth, torch, dev, tol=1e-3):
@@ -687,14 +748,26 @@ def bench_adjoint(recon, synth, torch, dev, n, directions):
     return out
 
 
-def _adjoint_delta_r_loss(recon, torch, s, aux, b, phi, delta_lin, n, L, gen, directions=4):
+def _adjoint_delta_r_loss(recon, torch, s, aux, b, phi, delta_lin, n, L, gen, directions=32):
     """The loss of the adjoint workload on the reconstructed density:
     sum over |k| < 0.5 h/Mpc of |FFT(delta_r) - FFT(delta_L, seed)|^2, delta_r
     the FP64 output at phi(b).  Its gradient with respect to b is the output's
-    adjoint (direct b term) plus the solve's adjoint of its phi term; checked
-    against central finite differences along smooth directions (FP64 solves
-    to 1e-13)."""
+    adjoint (direct b term) plus the solve's adjoint of its phi term.
+
+    Checked by central differences along `directions` random directions in
+    the loss's band (|k| < 0.5 h/Mpc, unit rms), each with a step that moves
+    no q across a CIC cell face: the CIC weights are piecewise linear, so a
+    step that crosses a face measures a kink, not the gradient.  Per
+    direction d the largest such step follows from the map: with u the CIC
+    coordinate of every q and du/deps its response to b + eps d (from two
+    solves 1e-7 apart), eps_safe = min over cells and axes of (distance of u
+    to its nearest face) / |du/deps|; the check uses eps = eps_safe / 2 and
+    verifies that no cell changed.  The perturbed solves start from phi(b)
+    (FP64, resumed V-cycles to the FP64 floor), so the difference of two
+    solves carries the O(eps) response and not the solves' own iteration
+    error."""
     import math
+    h = L / n
     kf = 2 * math.pi / L
     f = torch.fft.fftfreq(n, d=1.0 / n, device=b.device) * kf
     fz = torch.fft.rfftfreq(n, d=1.0 / n, device=b.device) * kf
@@ -704,6 +777,25 @@ def _adjoint_delta_r_loss(recon, torch, s, aux, b, phi, delta_lin, n, L, gen, di
 
     def loss_of(dl):
         return float((mask * (torch.fft.rfftn(dl) - ref).abs() ** 2).sum())
+
+    def ucoords(p):
+        # u = q N / L - 1/2 per axis, q = x + central gradient of phi (mod L)
+        out = []
+        idx = torch.arange(n, device=b.device, dtype=torch.float64)
+        for ax in range(3):
+            g = (torch.roll(p, -1, ax) - torch.roll(p, 1, ax)) / (2 * h)
+            shape = [1, 1, 1]
+            shape[ax] = n
+            q = torch.remainder(((idx + 0.5) * h).view(shape) + g, L)
+            out.append(q / h - 0.5)
+        return out
+
+    aux.configure(start=recon.START_GUESS)
+
+    def solve(bb):
+        p = phi.clone()
+        _, st = aux.solve(bb, phi=p, tol=1e-15, max_cycles=12, raise_on_noconv=False)
+        return p, st["rel_residual"]
 
     _, dl = s.displace_fp64(phi, b)
     dlr = dl.detach().clone().requires_grad_(True)
@@ -715,24 +807,37 @@ def _adjoint_delta_r_loss(recon, torch, s, aux, b, phi, delta_lin, n, L, gen, di
     gb = gb_direct + s.adjoint(gphi)
     torch.cuda.synchronize()
     t_grad = time.perf_counter() - t0
-    # directions inside the loss's band (|k| < 0.5 h/Mpc, unit rms): a white
-    # direction barely moves this loss, and its difference quotient drowns
-    # in the solves' residual
-    eps, errs = 1e-5, []
+    u0 = ucoords(phi)
+    dist = [torch.minimum(u - torch.floor(u), torch.ceil(u) - u) for u in u0]
+    errs, steps, crossings, resid = [], [], [], []
     for _ in range(directions):
         d = torch.randn((n, n, n), dtype=torch.float64, device=b.device, generator=gen)
         d = torch.fft.irfftn(torch.fft.rfftn(d) * mask, s=(n, n, n))
         d = d / d.pow(2).mean().sqrt()
-        vals = []
+        e0 = 1e-7
+        pp, _ = solve(b + e0 * d)
+        pm, _ = solve(b - e0 * d)
+        dphi = (pp - pm) / (2 * e0)
+        du = [(torch.roll(dphi, -1, ax) - torch.roll(dphi, 1, ax)) / (2 * h * h) for ax in range(3)]
+        eps = 0.5 * min(float((dist[ax] / du[ax].abs().clamp_min(1e-300)).min()) for ax in range(3))
+        vals, cross = [], 0
         for sg in (1.0, -1.0):
             bp = b + sg * eps * d
-            pp, _ = aux.solve(bp, tol=1e-13, max_cycles=80)
-            vals.append(loss_of(aux.displace_fp64(pp, bp)[1]))
+            p2, rr = solve(bp)
+            resid.append(rr)
+            vals.append(loss_of(aux.displace_fp64(p2, bp)[1]))
+            cross += sum(int((torch.floor(a) != torch.floor(c)).sum()) for a, c in zip(u0, ucoords(p2)))
         fd = (vals[0] - vals[1]) / (2 * eps)
         errs.append(abs(float((gb * d).sum()) - fd) / abs(fd))
+        steps.append(eps)
+        crossings.append(cross)
     return {"loss": "sum_{|k|<0.5 h/Mpc} |FFT(delta_r) - FFT(delta_L seed)|^2, delta_r FP64",
-            "gradient_seconds": t_grad, "fd_directions": directions, "fd_step": eps,
-            "fd_max_rel_error": max(errs)}
+            "gradient_seconds": t_grad, "fd_directions": directions,
+            "fd_step": "per direction eps_safe / 2 (no q crosses a CIC cell face)",
+            "fd_steps_min_median_max": [min(steps), statistics.median(steps), max(steps)],
+            "min_face_distance_cells": min(float(x.min()) for x in dist),
+            "face_crossings": sum(crossings), "fd_solve_rel_residual_max": max(resid),
+            "fd_max_rel_error": max(errs), "fd_median_rel_error": statistics.median(errs)}
 
 
 def _time_launches(torch, stream, fn, reps):

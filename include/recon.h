@@ -246,8 +246,9 @@ recon_status recon_smooth_density(recon_handle *h, const double *rho, double R, 
  *     out_i = mean + std * Phi^-1((rank_i + 1/2) / N^3),
  * rank_i the position of field_i in ascending order with ties broken by
  * position (-0 equals +0), mean and std (population) of field.  field, out:
- * device N^3, distinct; field must be finite.  The quantile is evaluated
- * in FP32 (out carries ~1e-6 relative rounding).  The first call allocates
+ * device N^3, distinct; field must be finite.  The probability and the
+ * quantile are FP64 (distinct ranks give distinct outputs at any size up to
+ * 1024^3).  The first call allocates
  * 24 N^3 bytes of workspace, held by the handle until recon_destroy.
  * Errors: RECON_E_INVALID, RECON_E_OOM, RECON_E_CUDA. */
 recon_status recon_gaussianise(recon_handle *h, const double *field, double *out);

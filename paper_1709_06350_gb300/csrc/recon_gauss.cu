@@ -211,7 +211,11 @@ k_radix_scatter(const unsigned long long *__restrict__ kin, const unsigned *__re
     }
 }
 
-// g[idx[r]] = mean + std * Phi^-1((r + 1/2) / n)
+// g[idx[r]] = mean + std * Phi^-1((r + 1/2) / n).  The probability and the
+// quantile are FP64: above 2^24 cells adjacent ranks would round to the same
+// FP32 probability and distinct inputs would get equal outputs.  The quantile
+// is taken of the smaller tail probability and mirrored, so the two halves
+// are exactly antisymmetric.
 __global__ void __launch_bounds__(kThreads)
 k_gauss_out(const unsigned *__restrict__ idx, size_t n, const double *__restrict__ scal,
             double *__restrict__ g)
@@ -220,9 +224,9 @@ k_gauss_out(const unsigned *__restrict__ idx, size_t n, const double *__restrict
     for (size_t r = (size_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
          r += (size_t)gridDim.x * blockDim.x) {
         const size_t lo = r < n - 1 - r ? r : n - 1 - r;
-        const float q = (float)((double)lo + 0.5) / (float)n;   // smaller tail probability
-        const float z = normcdfinvf(q);
-        g[idx[r]] = m + sd * (double)(r == lo ? z : -z);
+        const double q = ((double)lo + 0.5) / (double)n;   // smaller tail probability
+        const double z = normcdfinv(q);
+        g[idx[r]] = m + sd * (r == lo ? z : -z);
     }
 }
 
