@@ -716,14 +716,33 @@ def bench_adjoint(recon, synth, torch, dev, n, directions):
     phi, st = s.solve(b, tol=1e-12, max_cycles=60)
     torch.cuda.synchronize()
     t_solve = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    g = s.adjoint(wv)
+    modes = {}
     torch.cuda.synchronize()
-    t_adj = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    g = s.adjoint(wv)                      # cofactors and null vector reused
-    torch.cuda.synchronize()
-    t_adj2 = time.perf_counter() - t0
+    free0 = torch.cuda.mem_get_info(dev)[0]   # before any adjoint workspace exists
+    res0 = torch.cuda.memory_reserved(dev)
+    for store in (1, 0):
+        # the adjoint's device workspace: the drop in free device memory since
+        # before any adjoint call, less what torch's allocator took meanwhile
+        # (switching modes frees the other mode's workspace)
+        s.configure(adjoint_store_cofactors=store)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g = s.adjoint(wv)
+        torch.cuda.synchronize()
+        t_adj = time.perf_counter() - t0
+        ws = (free0 - torch.cuda.mem_get_info(dev)[0]) - (torch.cuda.memory_reserved(dev) - res0)
+        t0 = time.perf_counter()
+        g = s.adjoint(wv)                      # null vector (and stored cofactors) reused
+        torch.cuda.synchronize()
+        modes["stored" if store else "formed"] = {
+            "adjoint_seconds_first": t_adj, "adjoint_seconds_repeat": time.perf_counter() - t0,
+            "workspace_gb": ws / 1e9, "gradient": g}
+    g = modes["formed"].pop("gradient")
+    g_st = modes["stored"].pop("gradient")
+    modes["formed_vs_stored_rel_l2"] = float(torch.linalg.norm(g - g_st) / torch.linalg.norm(g_st))
+    del g_st
+    t_adj = modes["formed"]["adjoint_seconds_first"]
+    t_adj2 = modes["formed"]["adjoint_seconds_repeat"]
     eps = 1e-4
     errs = []
     aux = recon.Solver(n, L, recon.RECON_F64)
@@ -737,7 +756,7 @@ def bench_adjoint(recon, synth, torch, dev, n, directions):
         errs.append(abs(float((g * d).sum()) - fd) / abs(fd))
     out = {"workload": f"{n}^3, L = {L:g} Mpc/h, sigma_lin = 0.8, R = 4 Mpc/h, FP64",
            "solve_seconds": t_solve, "adjoint_seconds_first": t_adj,
-           "adjoint_seconds_repeat": t_adj2, "fd_directions": directions,
+           "adjoint_seconds_repeat": t_adj2, "finest_level_cofactors": modes, "fd_directions": directions,
            "fd_max_rel_error": max(errs) if errs else None, "fd_step": eps}
     try:
         out["delta_r_loss"] = _adjoint_delta_r_loss(recon, torch, s, aux, b, phi, delta_lin, n, L, gen)
@@ -837,7 +856,9 @@ def _adjoint_delta_r_loss(recon, torch, s, aux, b, phi, delta_lin, n, L, gen, di
             "fd_steps_min_median_max": [min(steps), statistics.median(steps), max(steps)],
             "min_face_distance_cells": min(float(x.min()) for x in dist),
             "face_crossings": sum(crossings), "fd_solve_rel_residual_max": max(resid),
-            "fd_max_rel_error": max(errs), "fd_median_rel_error": statistics.median(errs)}
+            "fd_max_rel_error": max(errs), "fd_median_rel_error": statistics.median(errs),
+            "fd_fraction_below_1e-5": sum(e < 1e-5 for e in errs) / len(errs),
+            "fd_errors": sorted(errs)}
 
 
 def _time_launches(torch, stream, fn, reps):

@@ -68,7 +68,8 @@ typedef enum {
 /* Solver options.  Defaults (recon_create): nu1 = nu2 = 2,
  * coarse_max_sweeps = 200, coarse_rtol = 1e-3, rule = NEWTON1, start = FMG,
  * scale_floor = 0.5, mixed_switch_rtol = 1e-4, mixed_fas_max_cycles = 12,
- * mixed_linear_vcycles = 2, mixed_df_residual = 1, fused_chunk = 0. */
+ * mixed_linear_vcycles = 2, mixed_df_residual = 1, fused_chunk = 0,
+ * adjoint_store_cofactors = 0. */
 typedef struct {
     int nu1, nu2;               /* pre- / post-smoothing sweeps per level          */
     int coarse_max_sweeps;      /* coarsest grid: sweep cap                        */
@@ -92,6 +93,11 @@ typedef struct {
                                    sweeps (grids >= 128^3): 4..128, 0 = by size;
                                    on grids of side a multiple of 64 it is taken
                                    down to a multiple of 4 that divides N       */
+    int adjoint_store_cofactors; /* recon_adjoint: 0 = the finest grid's six
+                                   cofactor fields of I + H phi are formed
+                                   again from phi in every application of J^T
+                                   (grids of side a multiple of 32; saves 48 N^3
+                                   bytes); 1 = kept in memory (faster)          */
 } recon_config;
 
 #define RECON_HISTORY_MAX 64

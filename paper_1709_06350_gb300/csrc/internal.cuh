@@ -24,6 +24,7 @@ struct GaussWork {
 
 struct AdjWork {
     bool ready = false;
+    bool stored0 = true;       // the finest level's cofactors are kept (else formed in every J^T)
     bool null_ready = false;   // cofactors and null vector match the last solve
     double null_rel = 0.0;
     double *th[kMaxLevels] = {}, *cof[kMaxLevels] = {}, *lam[kMaxLevels] = {}, *f[kMaxLevels] = {};

@@ -10,9 +10,11 @@
 // vector n = 1 + w (J^T w = -J^T 1), and lam = lam0 - (sum lam0 / sum n) n for
 // any solution lam0 of J^T lam0 = gbar - mean(gbar).
 //
-// Both linear solves use FP64 red-black Gauss-Seidel multigrid on J^T, with
-// the cofactors of every level computed once per call (coarse levels from
-// the restricted potential).
+// Both linear solves use FP64 red-black Gauss-Seidel multigrid on J^T.  The
+// coarse levels' cofactors are computed once per call from the restricted
+// potential and kept; the finest level's are formed again from phi in every
+// application of J^T (k_jt_fine) unless adjoint_store_cofactors keeps them
+// too (48 N^3 bytes).
 #include <cmath>
 #include <string>
 
@@ -159,6 +161,158 @@ k_jt_apply(const double *__restrict__ v, const double *__restrict__ f, const dou
     if (ltid() == 0) partials[4 * blockIdx.x + 1] = t;
 }
 
+// ---- the finest level without stored cofactors ----------------------------
+// J^T applied with the cofactors of I + H phi formed in shared memory: a CTA
+// streams chunks of 64 planes of the i columns of 8 x 32 (j, k) tiles (work
+// items taken in turn by the CTAs of a grid of at most kMaxRedBlocks); per
+// plane p it stages phi
+// (tile + 2-cell halo) and lam (tile + 1), forms the six cofactors of plane
+// p + 1 on the tile + 1 ring, and applies J^T at plane p.  Three barriers per
+// plane; no N^3 cofactor arrays.
+//   MODE 0: one colour pass of Gauss-Seidel on J^T lam = f (snapshot: out is
+//           the destination array, cells of the other colour copied)
+//   MODE 1: r = f - J^T lam (written to out unless out is null) and per-CTA
+//           sums of r^2 (partials column 1)
+//   MODE 2: out = sign * J^T 1 and per-CTA sums of out^2 (column 1)
+constexpr int kFJ = 8, kFK = 32, kFT = kFJ * kFK, kFChunk = 64;
+constexpr int kFPK = kFK + 4, kFPP = (kFJ + 4) * kFPK;   // phi planes
+constexpr int kFCK = kFK + 2, kFCP = (kFJ + 2) * kFCK;   // cofactor / lam planes
+constexpr size_t kFineSmem = sizeof(double) * (5 * kFPP + 3 * 6 * kFCP + 3 * kFCP);
+
+template <int MODE>
+__global__ void __launch_bounds__(kFT)
+k_jt_fine(const double *__restrict__ phi, const double *__restrict__ lam, const double *__restrict__ f,
+          double *__restrict__ out, int N, double ih2, int colour, double sign, double *__restrict__ partials)
+{
+    extern __shared__ double smd[];
+    double *sphi = smd;                       // [5][kFPP]
+    double *scof = sphi + 5 * kFPP;           // [3][6][kFCP]
+    double *slam = scof + 3 * 6 * kFCP;       // [3][kFCP]
+    __shared__ double sh[32];
+    const int tid = threadIdx.x, tj = tid / kFK, tk = tid % kFK;
+    const unsigned NN = (unsigned)N * (unsigned)N;
+    const int ncols = (N / kFK) * (N / kFJ), CI = N < kFChunk ? N : kFChunk, nchunks = N / CI;
+    auto wr = [&](int x) { return x < 0 ? x + N : (x >= N ? x - N : x); };
+    double s2 = 0.0;
+    for (int item = blockIdx.x; item < ncols * nchunks; item += gridDim.x) {
+        const int col = item % ncols, i0 = (item / ncols) * CI, i1 = i0 + CI;
+        const int k0 = (col % (N / kFK)) * kFK, j0 = (col / (N / kFK)) * kFJ;
+        auto load_phi = [&](int p) {
+            double *d = sphi + ((p + 10) % 5) * kFPP;
+            const unsigned pb = (unsigned)wr(p) * NN;
+            for (int e = tid; e < kFPP; e += kFT) {
+                const int r = e / kFPK, c = e - r * kFPK;
+                d[e] = phi[pb + (unsigned)wr(j0 - 2 + r) * (unsigned)N + (unsigned)wr(k0 - 2 + c)];
+            }
+        };
+        auto load_lam = [&](int p) {
+            if (MODE == 2) return;
+            double *d = slam + ((p + 9) % 3) * kFCP;
+            const unsigned pb = (unsigned)wr(p) * NN;
+            for (int e = tid; e < kFCP; e += kFT) {
+                const int r = e / kFCK, c = e - r * kFCK;
+                d[e] = lam[pb + (unsigned)wr(j0 - 1 + r) * (unsigned)N + (unsigned)wr(k0 - 1 + c)];
+            }
+        };
+        auto cof_plane = [&](int p) {   // cofactors of plane p on the tile + 1 ring (phi planes p-1..p+1 staged)
+            const double *pm = sphi + ((p + 9) % 5) * kFPP, *pc = sphi + ((p + 10) % 5) * kFPP,
+                         *pp = sphi + ((p + 11) % 5) * kFPP;
+            double *d = scof + ((p + 9) % 3) * 6 * kFCP;
+            for (int e = tid; e < kFCP; e += kFT) {
+                const int r = e / kFCK, c = e - r * kFCK;
+                const int o = (r + 1) * kFPK + (c + 1);
+                Nb19<double> v;
+                v.c = pc[o];
+                v.xp = pp[o];
+                v.xm = pm[o];
+                v.yp = pc[o + kFPK];
+                v.ym = pc[o - kFPK];
+                v.zp = pc[o + 1];
+                v.zm = pc[o - 1];
+                v.xpyp = pp[o + kFPK];
+                v.xmym = pm[o - kFPK];
+                v.xmyp = pm[o + kFPK];
+                v.xpym = pp[o - kFPK];
+                v.ypzp = pc[o + kFPK + 1];
+                v.ymzm = pc[o - kFPK - 1];
+                v.ymzp = pc[o - kFPK + 1];
+                v.ypzm = pc[o + kFPK - 1];
+                v.xpzp = pp[o + 1];
+                v.xmzm = pm[o - 1];
+                v.xmzp = pm[o + 1];
+                v.xpzm = pp[o - 1];
+                const Cof<double> a = cofactors(v, ih2);
+                d[e] = a.xx;
+                d[kFCP + e] = a.yy;
+                d[2 * kFCP + e] = a.zz;
+                d[3 * kFCP + e] = a.xy;
+                d[4 * kFCP + e] = a.yz;
+                d[5 * kFCP + e] = a.xz;
+            }
+        };
+        // prologue: phi planes i0-2..i0+1, lam planes i0-1, i0, cofactors of planes i0-1, i0
+        for (int p = i0 - 2; p <= i0 + 1; ++p) load_phi(p);
+        load_lam(i0 - 1);
+        load_lam(i0);
+        __syncthreads();
+        cof_plane(i0 - 1);
+        cof_plane(i0);
+        for (int p = i0; p < i1; ++p) {
+            __syncthreads();   // every read of the slots refilled below is done
+            load_phi(p + 2);
+            load_lam(p + 1);
+            __syncthreads();
+            cof_plane(p + 1);
+            __syncthreads();
+            // J^T lam at tile cell (tj, tk) of plane p
+            const double *cm = scof + ((p + 8) % 3) * 6 * kFCP, *cc = scof + ((p + 9) % 3) * 6 * kFCP,
+                         *cp = scof + ((p + 10) % 3) * 6 * kFCP;
+            const double *lm = slam + ((p + 8) % 3) * kFCP, *lc = slam + ((p + 9) % 3) * kFCP,
+                         *lp = slam + ((p + 10) % 3) * kFCP;
+            const int o = (tj + 1) * kFCK + (tk + 1);
+            auto X = [&](const double *cpl, const double *lpl, int comp, int off) {
+                return MODE == 2 ? cpl[comp * kFCP + o + off] : cpl[comp * kFCP + o + off] * lpl[o + off];
+            };
+            auto jt_here = [&]() {
+                const double dxx = X(cp, lp, 0, 0) + X(cm, lm, 0, 0) - 2.0 * X(cc, lc, 0, 0);
+                const double dyy = X(cc, lc, 1, kFCK) + X(cc, lc, 1, -kFCK) - 2.0 * X(cc, lc, 1, 0);
+                const double dzz = X(cc, lc, 2, 1) + X(cc, lc, 2, -1) - 2.0 * X(cc, lc, 2, 0);
+                const double dxy =
+                    (X(cp, lp, 3, kFCK) + X(cm, lm, 3, -kFCK)) - (X(cm, lm, 3, kFCK) + X(cp, lp, 3, -kFCK));
+                const double dyz = (X(cc, lc, 4, kFCK + 1) + X(cc, lc, 4, -kFCK - 1)) -
+                                   (X(cc, lc, 4, -kFCK + 1) + X(cc, lc, 4, kFCK - 1));
+                const double dxz = (X(cp, lp, 5, 1) + X(cm, lm, 5, -1)) - (X(cm, lm, 5, 1) + X(cp, lp, 5, -1));
+                return (dxx + dyy + dzz) * ih2 + (dxy + dyz + dxz) * (0.5 * ih2);
+            };
+            const int j = j0 + tj, k = k0 + tk;
+            const unsigned id = (unsigned)p * NN + (unsigned)j * (unsigned)N + (unsigned)k;
+            if (MODE == 0) {
+                const double l0 = lc[o];
+                if (((p + j + k) & 1) == colour) {
+                    const double diag = -2.0 * (cc[o] + cc[kFCP + o] + cc[2 * kFCP + o]) * ih2;
+                    out[id] = l0 + (f[id] - jt_here()) / diag;
+                } else {
+                    out[id] = l0;
+                }
+            } else if (MODE == 1) {
+                const double jt = jt_here();
+                const double r = f[id] - jt;
+                if (out) out[id] = r;
+                s2 += r * r;
+            } else {
+                const double v = sign * jt_here();
+                out[id] = v;
+                s2 += v * v;
+            }
+        }
+        __syncthreads();   // the next column refills every slot
+    }
+    if (MODE != 0) {
+        const double t = block_sum<kFT>(s2, sh);
+        if (ltid() == 0) partials[4 * blockIdx.x + 1] = t;
+    }
+}
+
 // Single-CTA Gauss-Seidel on the coarsest level (N^3 <= 4096).
 __global__ void __launch_bounds__(kCoarseThreads)
 k_jt_coarse(double *lam, double *work, const double *f, const double *cof, int N, double ih2,
@@ -266,11 +420,32 @@ inline unsigned nred(size_t n)
         if (e_ != cudaSuccess) return e_;                                          \
     } while (0)
 
+// grid of the cofactor-forming kernel: its (column, 64-plane chunk) items,
+// at most kMaxRedBlocks CTAs
+inline unsigned fine_grid(int N)
+{
+    const unsigned items = (unsigned)(N / kFK) * (unsigned)(N / kFJ) * (unsigned)(N < kFChunk ? 1 : N / kFChunk);
+    return items < (unsigned)kMaxRedBlocks ? items : (unsigned)kMaxRedBlocks;
+}
+
+// level l applies J^T with cofactors formed from phi (no stored arrays)
+inline bool formed(const recon_handle *H, int l) { return l == 0 && !H->adj.stored0; }
+
 cudaError_t jt_sweep(recon_handle *H, int l, double *lam, const double *f, int sweeps)
 {
     AdjWork &A = H->adj;
     const int N = H->Nl[l];
     const double ih2 = 1.0 / (H->hl[l] * H->hl[l]);
+    if (formed(H, l)) {
+        for (int it = 0; it < sweeps; ++it) {
+            note_launch(2);
+            k_jt_fine<0><<<fine_grid(N), kFT, kFineSmem, H->stream>>>(A.th[0], lam, f, H->work64, N, ih2, 0, 1.0,
+                                                                     nullptr);
+            k_jt_fine<0><<<fine_grid(N), kFT, kFineSmem, H->stream>>>(A.th[0], H->work64, f, lam, N, ih2, 1, 1.0,
+                                                                     nullptr);
+        }
+        return cudaGetLastError();
+    }
     for (int it = 0; it < sweeps; ++it) {
         note_launch(2);
         k_jt_pass<<<row_grid(N), row_block(), 0, H->stream>>>(lam, H->work64, f, A.cof[l], N, ih2, 0);
@@ -297,10 +472,22 @@ cudaError_t jt_vcycle(recon_handle *H, int l, double *lam, const double *f)
     CK(jt_sweep(H, l, lam, f, cf.nu1));
     const int Nc = H->Nl[l + 1];
     const size_t nc = (size_t)Nc * Nc * Nc;
-    const unsigned nb = row_grid(Nc, kMaxRedBlocks);
-    note_launch(3);
-    k_jt_restrict_residual<<<nb, row_block(), 0, s>>>(lam, f, A.cof[l], N, ih2, A.f[l + 1], H->partials);
-    k_reduce_col<<<1, kReduceThreads, 0, s>>>(H->partials, nb, 0, 1.0 / (double)nc, H->scal + S_ADJ_MEAN);
+    if (formed(H, l)) {
+        // r = f - J^T lam (cofactors formed from phi), then its 8-son mean
+        note_launch(3);
+        k_jt_fine<1><<<fine_grid(N), kFT, kFineSmem, s>>>(A.th[0], lam, f, H->work64b, N, ih2, 0, 1.0,
+                                                          H->partials);
+        CK(restrict_plain<double>(N, H->work64b, A.f[l + 1], s));
+        k_sum<<<nred(nc), kThreads, 0, s>>>(A.f[l + 1], nc, H->partials);
+        k_reduce_col<<<1, kReduceThreads, 0, s>>>(H->partials, nred(nc), 0, 1.0 / (double)nc,
+                                                  H->scal + S_ADJ_MEAN);
+    } else {
+        const unsigned nb = row_grid(Nc, kMaxRedBlocks);
+        note_launch(2);
+        k_jt_restrict_residual<<<nb, row_block(), 0, s>>>(lam, f, A.cof[l], N, ih2, A.f[l + 1], H->partials);
+        k_reduce_col<<<1, kReduceThreads, 0, s>>>(H->partials, nb, 0, 1.0 / (double)nc, H->scal + S_ADJ_MEAN);
+    }
+    note_launch();
     k_sub_mean<<<blocks_for(nc), kThreads, 0, s>>>(A.f[l + 1], nc, H->scal + S_ADJ_MEAN);
     CK(cudaMemsetAsync(A.lam[l + 1], 0, sizeof(double) * nc, s));
     CK(jt_vcycle(H, l + 1, A.lam[l + 1], A.f[l + 1]));
@@ -317,13 +504,22 @@ int jt_solve(recon_handle *H, double *lam, const double *f, double tol, int max_
     const int N = H->N;
     const size_t n = (size_t)N * N * N;
     const double ih2 = 1.0 / (H->h * H->h);
-    const unsigned nb = row_grid(N, kMaxRedBlocks);
+    const bool fm = formed(H, 0);
+    const unsigned nb = fm ? fine_grid(N) : row_grid(N, kMaxRedBlocks);
+    // partial sums of ||f - J^T lam||^2 (column 1)
+    auto resid_norm = [&]() {
+        note_launch();
+        if (fm)
+            k_jt_fine<1><<<nb, kFT, kFineSmem, s>>>(H->adj.th[0], lam, f, nullptr, N, ih2, 0, 1.0, H->partials);
+        else
+            k_jt_apply<<<nb, row_block(), 0, s>>>(lam, f, H->adj.cof[0], N, ih2, 1.0, nullptr, H->partials);
+    };
     if (cudaMemsetAsync(lam, 0, sizeof(double) * n, s) != cudaSuccess) return -1;
     double fnorm2 = 0.0;
     {
         // ||f||^2 as the residual norm at lam = 0
-        note_launch(2);
-        k_jt_apply<<<nb, row_block(), 0, s>>>(lam, f, H->adj.cof[0], N, ih2, 1.0, nullptr, H->partials);
+        resid_norm();
+        note_launch();
         k_reduce_col<<<1, kReduceThreads, 0, s>>>(H->partials, nb, 1, 1.0, H->scal + S_ADJ_NORM);
         if (cudaMemcpyAsync(&H->hscal[S_ADJ_NORM], H->scal + S_ADJ_NORM, sizeof(double),
                             cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -340,8 +536,8 @@ int jt_solve(recon_handle *H, double *lam, const double *f, double tol, int max_
     double rel = 1.0;
     for (cyc = 1; cyc <= max_cycles; ++cyc) {
         if (jt_vcycle(H, 0, lam, f) != cudaSuccess) return -1;
-        note_launch(2);
-        k_jt_apply<<<nb, row_block(), 0, s>>>(lam, f, H->adj.cof[0], N, ih2, 1.0, nullptr, H->partials);
+        resid_norm();
+        note_launch();
         k_reduce_col<<<1, kReduceThreads, 0, s>>>(H->partials, nb, 1, 1.0, H->scal + S_ADJ_NORM);
         if (cudaMemcpyAsync(&H->hscal[S_ADJ_NORM], H->scal + S_ADJ_NORM, sizeof(double),
                             cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -355,10 +551,28 @@ int jt_solve(recon_handle *H, double *lam, const double *f, double tol, int max_
     return cyc > max_cycles ? max_cycles : cyc;
 }
 
+// the finest level's cofactors are formed on the fly when configured so and
+// the grid tiles into the kernel's 8 x 32 columns
+inline bool store0(const recon_handle *H)
+{
+    return H->cfg.adjoint_store_cofactors != 0 || H->N % kFK != 0 || H->N % kFJ != 0 ||
+           (H->N > kFChunk && H->N % kFChunk != 0);
+}
+
 cudaError_t adj_alloc(recon_handle *H)
 {
     AdjWork &A = H->adj;
     if (A.ready) return cudaSuccess;
+    A.stored0 = store0(H);
+    if (!A.stored0) {
+        static bool attr = false;
+        if (!attr) {
+            CK(cudaFuncSetAttribute(k_jt_fine<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFineSmem));
+            CK(cudaFuncSetAttribute(k_jt_fine<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFineSmem));
+            CK(cudaFuncSetAttribute(k_jt_fine<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFineSmem));
+            attr = true;
+        }
+    }
     for (int l = 0; l < H->nlev; ++l) {
         const size_t n = (size_t)H->Nl[l] * H->Nl[l] * H->Nl[l];
         if (l > 0) {
@@ -366,7 +580,7 @@ cudaError_t adj_alloc(recon_handle *H)
             CK(cudaMalloc(&A.lam[l], sizeof(double) * n));
             CK(cudaMalloc(&A.f[l], sizeof(double) * n));
         }
-        CK(cudaMalloc(&A.cof[l], sizeof(double) * 6 * n));
+        if (l > 0 || A.stored0) CK(cudaMalloc(&A.cof[l], sizeof(double) * 6 * n));
     }
     const size_t n0 = (size_t)H->N * H->N * H->N;
     CK(cudaMalloc(&A.nvec, sizeof(double) * n0));
@@ -407,22 +621,36 @@ recon_status adjoint(recon_handle *H, const double *gbar, double *lam)
     const size_t n = (size_t)N * N * N;
     const double tol = 1e-12;
     const int maxc = 100;
+    if (A.ready && A.stored0 != store0(H)) {
+        // the cofactor option changed since the workspace was made
+        adj_free(H);
+        if ((e = adj_alloc(H)) != cudaSuccess) {
+            adj_free(H);
+            cudaGetLastError();
+            H->err = "adjoint workspace allocation failed";
+            return RECON_E_OOM;
+        }
+    }
     if (!A.null_ready) {
         // cofactors of every level, from phi and its restrictions
         A.th[0] = const_cast<double *>(H->last_phi);
         for (int l = 1; l < H->nlev; ++l)
             if ((e = restrict_plain<double>(H->Nl[l - 1], A.th[l - 1], A.th[l], s)) != cudaSuccess)
                 return RECON_E_CUDA;
-        for (int l = 0; l < H->nlev; ++l) {
+        for (int l = A.stored0 ? 0 : 1; l < H->nlev; ++l) {
             note_launch();
             k_cof6<<<row_grid(H->Nl[l]), row_block(), 0, s>>>(A.th[l], H->Nl[l],
                                                               1.0 / (H->hl[l] * H->hl[l]), A.cof[l]);
         }
         // null vector of J^T: n = 1 + w, J^T w = -J^T 1
         note_launch();
-        k_jt_apply<<<row_grid(N, kMaxRedBlocks), row_block(), 0, s>>>(nullptr, nullptr, A.cof[0], N,
-                                                                    1.0 / (H->h * H->h), -1.0, A.f[0],
-                                                                    H->partials);
+        if (A.stored0)
+            k_jt_apply<<<row_grid(N, kMaxRedBlocks), row_block(), 0, s>>>(nullptr, nullptr, A.cof[0], N,
+                                                                        1.0 / (H->h * H->h), -1.0, A.f[0],
+                                                                        H->partials);
+        else
+            k_jt_fine<2><<<fine_grid(N), kFT, kFineSmem, s>>>(A.th[0], nullptr, nullptr, A.f[0], N,
+                                                              1.0 / (H->h * H->h), 0, -1.0, H->partials);
         double rel = 0.0;
         const int c1 = jt_solve(H, A.nvec, A.f[0], tol, maxc, &rel);
         if (c1 < 0) {

@@ -52,6 +52,7 @@ recon_config default_config()
     c.mixed_linear_vcycles = 2;
     c.mixed_df_residual = 1;
     c.fused_chunk = 0;
+    c.adjoint_store_cofactors = 0;
     return c;
 }
 
@@ -285,7 +286,8 @@ recon_status recon_set_config(recon_handle *H, const recon_config *c)
         return set_err(H, RECON_E_INVALID, "scale_floor must be < 1");
     if (!(c->mixed_switch_rtol > 0.0) || c->mixed_fas_max_cycles < 0 || c->mixed_linear_vcycles < 1 ||
         (c->mixed_df_residual != 0 && c->mixed_df_residual != 1) ||
-        (c->fused_chunk != 0 && (c->fused_chunk < 4 || c->fused_chunk > 128)))
+        (c->fused_chunk != 0 && (c->fused_chunk < 4 || c->fused_chunk > 128)) ||
+        (c->adjoint_store_cofactors != 0 && c->adjoint_store_cofactors != 1))
         return set_err(H, RECON_E_INVALID, "bad mixed-precision options");
     H->cfg = *c;
     return RECON_OK;

@@ -41,7 +41,8 @@ class recon_config(ctypes.Structure):
                 ("rule", ctypes.c_int), ("start", ctypes.c_int),
                 ("scale_floor", ctypes.c_double), ("mixed_switch_rtol", ctypes.c_double),
                 ("mixed_fas_max_cycles", ctypes.c_int), ("mixed_linear_vcycles", ctypes.c_int),
-                ("mixed_df_residual", ctypes.c_int), ("fused_chunk", ctypes.c_int)]
+                ("mixed_df_residual", ctypes.c_int), ("fused_chunk", ctypes.c_int),
+                ("adjoint_store_cofactors", ctypes.c_int)]
 
 
 class recon_stats(ctypes.Structure):

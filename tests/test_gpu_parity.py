@@ -527,4 +527,6 @@ def test_gaussianise_keeps_strict_order_above_2_24_cells(R, O):
     order = np.argsort(v, axis=None, kind="stable")
     assert np.all(np.diff(g.ravel()[order]) > 0)
     g_ref, _ = O.gaussianise(v)
-    assert np.max(np.abs(g - g_ref)) < 1e-11 * v.std()
+    # the extreme ranks sit at |g| ~ 5.6 (p ~ 1.5e-8), where CUDA's
+    # normcdfinv and scipy's ndtri differ by a few 1e-10
+    assert np.max(np.abs(g - g_ref)) < 1e-9 * v.std()
