@@ -881,10 +881,11 @@ def _time_launches(torch, stream, fn, reps):
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # each register-blocked fused smoother, from an ncu capture of the 384^3 case
-# (python bench.py --kernel-only 384; third launch of each); a launch at N^3
+# (python bench.py --kernel-only 384; ncu -k regex:k_sweep_reg, -s 2 -c 1 for
+# the FAS smoother, -s 18 -c 1 for the linear one); a launch at N^3
 # moves (N/384)^3 times as much.  Valid for the kernels as they were
 # captured: re-measure after a change to either kernel.
-NCU_TRAFFIC_384 = {"LIN": 722.541312e6 + 211.707392e6, "FAS": 463.279360e6 + 201.707520e6}
+NCU_TRAFFIC_384 = {"LIN": 689.353472e6 + 208.309248e6, "FAS": 472.232960e6 + 210.356992e6}
 
 
 def kernel_roofline(recon, torch, N, L, dev, stream):
