@@ -223,7 +223,8 @@ recon_status recon_displace_fp64(recon_handle *h, const double *phi, const doubl
  * the output of a solve, pass gbar_phi on to recon_adjoint and add its
  * gbar_b to this one.  The first call allocates 9 N^3 doubles of workspace,
  * held by the handle until recon_destroy; also uses 2 N^3 doubles of the
- * handle workspace.  Outputs must not alias an input or each other.
+ * handle workspace.  Outputs must not overlap an input or each other
+ * (byte ranges: gbar_psi 3 N^3 doubles, every other array N^3).
  * Errors: RECON_E_INVALID, RECON_E_OOM, RECON_E_CUDA. */
 recon_status recon_displace_adjoint(recon_handle *h, const double *phi, const double *b,
                                     const double *gbar_psi, const double *gbar_deltaL,

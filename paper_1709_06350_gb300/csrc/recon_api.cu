@@ -1,6 +1,7 @@
 // recon_api.cu -- the C ABI of librecon (include/recon.h, include/recon_steps.h):
 // argument checks, workspace ownership, status codes and messages.
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <new>
 #include <string>
@@ -401,13 +402,21 @@ recon_status recon_displace_adjoint(recon_handle *H, const double *phi, const do
 {
     if (!H) return RECON_E_INVALID;
     if (!phi || !b || !gbar_phi || !gbar_b) return set_err(H, RECON_E_INVALID, "NULL pointer");
-    const void *ins[4] = {phi, b, gbar_psi, gbar_deltaL};
-    for (const void *q : ins)
-        if (q && (q == gbar_phi || q == gbar_b))
-            return set_err(H, RECON_E_INVALID, "gbar_phi and gbar_b must not alias an input");
-    if (gbar_phi == gbar_b) return set_err(H, RECON_E_INVALID, "gbar_phi and gbar_b must differ");
-    H->err.clear();
     const size_t n = (size_t)H->N * H->N * H->N;
+    // byte ranges: gbar_psi holds 3 N^3 doubles, every other array N^3; an
+    // output may not overlap any input or the other output
+    auto overlap = [](const void *a, size_t na, const void *b, size_t nb) {
+        if (!a || !b) return false;
+        const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+        return x < y + nb * sizeof(double) && y < x + na * sizeof(double);
+    };
+    const void *ins[4] = {phi, b, gbar_psi, gbar_deltaL};
+    const size_t nin[4] = {n, n, 3 * n, n};
+    for (int a = 0; a < 4; ++a)
+        if (overlap(ins[a], nin[a], gbar_phi, n) || overlap(ins[a], nin[a], gbar_b, n))
+            return set_err(H, RECON_E_INVALID, "gbar_phi and gbar_b must not overlap an input");
+    if (overlap(gbar_phi, n, gbar_b, n)) return set_err(H, RECON_E_INVALID, "gbar_phi and gbar_b must not overlap");
+    H->err.clear();
     if (!H->dadj && cudaMalloc(&H->dadj, sizeof(double) * 9 * n) != cudaSuccess) {
         cudaGetLastError();
         H->dadj = nullptr;

@@ -370,9 +370,11 @@ k_displace_finish(const float2 *__restrict__ acc, size_t n, double *__restrict__
 }
 
 // ---- the reconstruction output in plain FP64, and its adjoint ----------
-// Per cell c at x_c = (i + 1/2) h, evaluated with the operations of a plain
-// IEEE evaluation of the definition (explicit roundings, no fused
-// multiply-add), so that the CIC cells of q match any host's bit for bit:
+// Per cell c at x_c = (i + 1/2) h.  The CIC coordinate (the gradient, q and
+// u below) is evaluated with explicit IEEE roundings and no fused
+// multiply-add, so that the CIC cells of q match any host's bit for bit; the
+// rest (A, v, the weights) is ordinary FP64 arithmetic that the compiler may
+// contract into fused multiply-adds:
 //   g = central-difference gradient of phi,  psi = -g,
 //   q = x + g (mod L),  per axis u = q N/L - 1/2 (CIC cell and fraction),
 //   A = I + H phi (stencils of eq. discrete_examples),  v = 3 - tr(A^-1),

@@ -22,6 +22,10 @@ static __device__ __align__(256) double g_noalloc_scratch[kNoAllocCells];
 // name g_noalloc_scratch is only a host-side stand-in: passing it to a kernel
 // would fault (or, where the GPU can reach host memory, silently use the
 // wrong memory), so kernels get the address from cudaGetSymbolAddress.
+// The cached address belongs to the device's current context: after
+// cudaDeviceReset the module is loaded again at a new address, and calls made
+// after a reset are not supported (the cache is not invalidated; the
+// allocating recon_step_coarse_solve has no such limit).
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void *g_scratch_addr[kMaxDevices] = {};

@@ -95,4 +95,13 @@ def test_displace_adjoint_rejects_bad_arguments(R):
         R.recon_displace_adjoint(s.h, N, x, x, None, x, out, out)     # outputs alias
     with pytest.raises(R.ReconError):
         R.recon_displace_adjoint(s.h, N, x, x, None, out, out, torch.empty_like(x))   # output aliases input
+    # an output inside gbar_psi's 3 N^3 doubles (not at its base) overlaps it
+    psi = torch.zeros((3, N, N, N), dtype=torch.float64, device="cuda")
+    with pytest.raises(R.ReconError):
+        R.recon_displace_adjoint(s.h, N, x, x, psi, x, psi[1], torch.empty_like(x))
+    # two outputs that overlap without sharing a base address
+    big = torch.empty(2 * N ** 3, dtype=torch.float64, device="cuda")
+    with pytest.raises(R.ReconError):
+        R.recon_displace_adjoint(s.h, N, x, x, None, x, big[:N ** 3].view(N, N, N),
+                                 big[N ** 3 // 2: N ** 3 // 2 + N ** 3].view(N, N, N))
     s.close()
