@@ -67,6 +67,8 @@ def _load():
             "or_sweep": (None, [_P, _P, _D, _I, _D, _I, _I]),
             "or_residual": (None, [_P, _P, _D, _I, _D, _P]),
             "or_paper_eps": (_D, [_P, _P, _D, _I, _D]),
+            "or_paper_eps_planes": (None, [_P, _P, _D, _I, _D, _P]),
+            "or_plane_sums": (None, [_P, _I, _I, _D, _I, _P]),
             "or_restrict": (None, [_P, _I, _P]),
             "or_prolong_add": (None, [_P, _P, _I, _D, _P]),
             "or_defect_scale": (_D, [_P, _P, _L, _D]),
@@ -183,6 +185,26 @@ def paper_eps(theta, g, c, h) -> float:
     """The paper's epsilon = rms(lap theta - Sigma) (Sec. II.A.2)."""
     t, gg = _f64(theta), _f64(g)
     return _load().or_paper_eps(_ptr(t), _ptr(gg), float(c), _grid_n(t), float(h))
+
+
+def paper_eps_planes(theta, g, c, h) -> np.ndarray:
+    """Per-plane partial sums of L_h^2 (the terms of the paper's epsilon)."""
+    t, gg = _f64(theta), _f64(g)
+    out = np.empty(t.shape[0])
+    _load().or_paper_eps_planes(_ptr(t), _ptr(gg), float(c), _grid_n(t), float(h), _ptr(out))
+    return out
+
+
+def plane_sums(a, m=0.0, squared=False) -> np.ndarray:
+    """Per-plane sums of (a - m) or (a - m)^2 over a (planes, N, N) array, each
+    a running sum in memory order: the partial sums every grid sum of the
+    oracle is built from (added in plane order)."""
+    x = _f64(a)
+    if x.ndim != 3 or x.shape[1] != x.shape[2]:
+        raise ValueError("expected a (planes, N, N) array")
+    out = np.empty(x.shape[0])
+    _load().or_plane_sums(_ptr(x), x.shape[0], x.shape[1], float(m), int(bool(squared)), _ptr(out))
+    return out
 
 
 def restrict(fine) -> np.ndarray:

@@ -251,11 +251,12 @@ void or_residual(const double *t, const double *g, double c, int N, double h,
 /* eps = rms over cells of L_h = lap_h theta - Sigma, Sigma = root - 3   */
 /* (eq. discretisition), with rhs = g + c.  L_h is dimensionless, so its */
 /* value is the same in the paper's code units.                          */
-double or_paper_eps(const double *t, const double *g, double c, int N, double h)
+/* per-plane partial sums of L_h^2 (out[i] for plane i, N values) */
+void or_paper_eps_planes(const double *t, const double *g, double c, int N, double h,
+                         double *out)
 {
-    double acc = 0.0;
-    long n = (long)N * N * N;
-    for (int i = 0; i < N; ++i)
+    for (int i = 0; i < N; ++i) {
+        double acc = 0.0;
         for (int j = 0; j < N; ++j)
             for (int k = 0; k < N; ++k) {
                 double s, p, q;
@@ -263,7 +264,18 @@ double or_paper_eps(const double *t, const double *g, double c, int N, double h)
                 double L = (s - 3.0) - (or_largest_root(p, q) - 3.0);
                 acc += L * L;
             }
-    return sqrt(acc / (double)n);
+        out[i] = acc;
+    }
+}
+
+double or_paper_eps(const double *t, const double *g, double c, int N, double h)
+{
+    double *ps = (double *)malloc(sizeof(double) * N);
+    or_paper_eps_planes(t, g, c, N, h, ps);
+    double acc = 0.0;
+    for (int i = 0; i < N; ++i) acc += ps[i];
+    free(ps);
+    return sqrt(acc / ((double)N * N * N));
 }
 
 /* ------------------------------------------------------------------ */
@@ -318,20 +330,46 @@ void or_prolong_add(const double *cnew, const double *cold, int Nc, double scale
 }
 
 /* ------------------------------------------------------------------ */
-/* small helpers on whole grids                                          */
+/* Sums over a grid.  The paper fixes no summation order; here a sum over */
+/* an N^3 grid is the sum, in plane order, of per-plane partial sums      */
+/* (each a running sum over the N^2 values of plane i in memory order).  */
+/* A grid split into slabs of whole planes (several processes, one slab  */
+/* each) then gives the same sums from its slabs' plane partials.        */
 /* ------------------------------------------------------------------ */
-static double mean_of(const double *a, long n)
+/* partial sums of the planes of a (nplanes x N x N) array:               */
+/*   out[i] = sum over plane i of (a - m)       (sq = 0)                 */
+/*   out[i] = sum over plane i of (a - m)^2     (sq = 1)                 */
+void or_plane_sums(const double *a, int nplanes, int N, double m, int sq, double *out)
 {
-    double s = 0.0;
-    for (long x = 0; x < n; ++x) s += a[x];
-    return s / (double)n;
+    long pl = (long)N * N;
+    for (int i = 0; i < nplanes; ++i) {
+        double s = 0.0;
+        for (long x = 0; x < pl; ++x) {
+            double d = a[i * pl + x] - m;
+            s += sq ? d * d : d;
+        }
+        out[i] = s;
+    }
 }
 
-static double norm2_centered(const double *a, long n, double m)
+static double grid_sum(const double *a, int N, double m, int sq)
 {
+    double *ps = (double *)malloc(sizeof(double) * N);
+    or_plane_sums(a, N, N, m, sq, ps);
     double s = 0.0;
-    for (long x = 0; x < n; ++x) s += (a[x] - m) * (a[x] - m);
-    return sqrt(s);
+    for (int i = 0; i < N; ++i) s += ps[i];
+    free(ps);
+    return s;
+}
+
+static double mean_of(const double *a, int N)
+{
+    return grid_sum(a, N, 0.0, 0) / ((double)N * N * N);
+}
+
+static double norm2_centered(const double *a, int N, double m)
+{
+    return sqrt(grid_sum(a, N, m, 1));
 }
 
 void or_det_grid(const double *t, int N, double h, double *out);
@@ -387,10 +425,10 @@ typedef struct {
 } or_params;
 
 /* rms of (r - mean r) on one level */
-static double proj_rms(const double *r, long n)
+static double proj_rms(const double *r, int N)
 {
-    double m = mean_of(r, n);
-    return norm2_centered(r, n, m) / sqrt((double)n);
+    double m = mean_of(r, N);
+    return norm2_centered(r, N, m) / sqrt((double)N * N * N);
 }
 
 /* Coarsest-grid solve (Sec. II.A.3: the hierarchy ends at 4^3; the      */
@@ -405,14 +443,14 @@ int or_coarse_solve(double *t, const double *g, double c, int N, double h,
     long n = (long)N * N * N;
     double *r = (double *)malloc(sizeof(double) * n);
     or_residual(t, g, c, N, h, r);
-    double r0 = proj_rms(r, n);
+    double r0 = proj_rms(r, N);
     double prev = r0;
     int sw = 0;
     while (sw < P->coarse_max_sweeps) {
         or_sweep(t, g, c, N, h, P->ordering, P->rule);
         ++sw;
         or_residual(t, g, c, N, h, r);
-        double cur = proj_rms(r, n);
+        double cur = proj_rms(r, N);
         if (cur <= P->coarse_rtol * r0)
             break;
         if (P->coarse_rtol > 0.0 && cur >= prev)
@@ -497,7 +535,7 @@ static void vcycle(or_hier *Hh, int l, double c, const or_params *P)
     double *rr = (double *)malloc(sizeof(double) * nc);
     double *dH = (double *)malloc(sizeof(double) * nc);
     or_restrict(Hh->r[l], N, rr);
-    double m = mean_of(rr, nc);
+    double m = mean_of(rr, Nc);
     for (long x = 0; x < nc; ++x) rr[x] -= m;
     or_det_grid(Hh->t[l + 1], Nc, hc, dH);
     double sc = or_defect_scale(dH, rr, nc, P->scale_floor);
@@ -538,8 +576,8 @@ static void compat_and_gauge(or_hier *Hh, int l, double *c)
     int N = Hh->N[l];
     long n = (long)N * N * N;
     or_residual(Hh->t[l], Hh->g[l], *c, N, Hh->h[l], Hh->r[l]);
-    *c -= mean_of(Hh->r[l], n);
-    double mt = mean_of(Hh->t[l], n);
+    *c -= mean_of(Hh->r[l], N);
+    double mt = mean_of(Hh->t[l], N);
     for (long x = 0; x < n; ++x) Hh->t[l][x] -= mt;
 }
 
@@ -582,18 +620,18 @@ int or_solve(const double *b, int N, double L, double *theta, double *c_io,
         compat_and_gauge(&Hh, 0, &c);
     }
 
-    double denom = norm2_centered(b, n, 1.0);
+    double denom = norm2_centered(b, N, 1.0);
     if (denom == 0.0) denom = 1.0;
     double rel = 0.0;
     int cyc = 0, status = 3;
     for (cyc = 1; cyc <= max_cycles; ++cyc) {
         vcycle(&Hh, 0, c, P);
         or_residual(theta, b, c, N, h, Hh.r[0]);
-        double m = mean_of(Hh.r[0], n);
+        double m = mean_of(Hh.r[0], N);
         c -= m;
-        double mt = mean_of(theta, n);
+        double mt = mean_of(theta, N);
         for (long x = 0; x < n; ++x) theta[x] -= mt;
-        rel = norm2_centered(Hh.r[0], n, m) / denom;
+        rel = norm2_centered(Hh.r[0], N, m) / denom;
         if (stats) stats[4 + cyc - 1] = rel;
         if (!isfinite(rel)) { status = 4; break; }
         if (rel < tol) { status = 0; break; }
