@@ -20,7 +20,7 @@ OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "librecon.so")
 SOURCES = ["recon_mg.cu", "recon_sweep.cu", "recon_cic.cu", "recon_adjoint.cu", "recon_batch.cu",
            "recon_api.cu", "recon_noalloc.cu", "recon_gauss.cu", "recon_smooth.cu",
-           "recon_measure.cu"]
+           "recon_measure.cu", "recon_slab.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

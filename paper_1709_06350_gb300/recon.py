@@ -57,7 +57,14 @@ class recon_stats(ctypes.Structure):
                     seconds=self.seconds, history=list(self.history[:self.n_history]))
 
 
+class recon_slab(ctypes.Structure):
+    """A slab of planes of a periodic N^3 grid (include/recon_slab.h)."""
+    _fields_ = [("N", ctypes.c_int), ("planes", ctypes.c_int), ("first", ctypes.c_int),
+                ("lo", ctypes.c_int), ("hi", ctypes.c_int)]
+
+
 _P, _I, _D, _LL = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+_SP = ctypes.POINTER(recon_slab)
 _SIGS = {
     "recon_create": (_I, [_I, _D, _I, ctypes.POINTER(_P)]),
     "recon_destroy": (None, [_P]),
@@ -94,6 +101,16 @@ _SIGS = {
     "recon_step_jacobian_apply": (_I, [_I, _D, _P, _P, _P, _P]),
     "recon_step_linear_sweep": (_I, [_I, _D, _P, _P, _P, _I, _P, _P]),
     "recon_measure_fp64_fma": (_I, [_I, _I, _P, _P]),
+    "recon_slab_sweep": (_I, [_SP, _D, _I, _P, _P, _D, _P, _P]),
+    "recon_slab_residual": (_I, [_SP, _D, _P, _P, _D, _P, _P]),
+    "recon_slab_det": (_I, [_SP, _D, _P, _P, _P]),
+    "recon_slab_restrict": (_I, [_SP, _P, _SP, _P, _P]),
+    "recon_slab_prolong_add": (_I, [_SP, _P, _P, _D, _SP, _P, _P]),
+    "recon_slab_plane_sums": (_I, [_SP, _P, _D, _I, _P, _P]),
+    "recon_slab_eps_planes": (_I, [_SP, _D, _P, _P, _D, _P, _P]),
+    "recon_slab_defect_min": (_I, [_SP, _P, _P, _D, _P, _P]),
+    "recon_slab_form_rhs": (_I, [_SP, _P, _P, _D, _P, _P]),
+    "recon_slab_sub": (_I, [_SP, _P, _D, _P]),
 }
 EXPORTS = tuple(_SIGS)
 
@@ -553,3 +570,67 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------- slab steps
+def _slab(lay):
+    """recon_slab from any object with N, planes, first, lo, hi."""
+    return ctypes.byref(recon_slab(int(lay.N), int(lay.planes), int(lay.first), int(lay.lo), int(lay.hi)))
+
+
+def _slab_ptr(t, lay):
+    import torch
+    return _dev_ptr(t, torch.float64, lay.planes * lay.N * lay.N)
+
+
+def recon_slab_sweep(lay, h, rule, theta, g, c, work, stream=None):
+    _check(load().recon_slab_sweep(_slab(lay), float(h), int(rule), _slab_ptr(theta, lay), _slab_ptr(g, lay),
+                                   float(c), _slab_ptr(work, lay), _stream(stream)))
+
+
+def recon_slab_residual(lay, h, theta, g, c, r, stream=None):
+    _check(load().recon_slab_residual(_slab(lay), float(h), _slab_ptr(theta, lay), _slab_ptr(g, lay), float(c),
+                                      _slab_ptr(r, lay), _stream(stream)))
+
+
+def recon_slab_det(lay, h, theta, out, stream=None):
+    _check(load().recon_slab_det(_slab(lay), float(h), _slab_ptr(theta, lay), _slab_ptr(out, lay),
+                                 _stream(stream)))
+
+
+def recon_slab_restrict(lay_f, fine, lay_c, coarse, stream=None):
+    _check(load().recon_slab_restrict(_slab(lay_f), _slab_ptr(fine, lay_f), _slab(lay_c),
+                                      _slab_ptr(coarse, lay_c), _stream(stream)))
+
+
+def recon_slab_prolong_add(lay_c, cnew, cold, scale, lay_f, fine, stream=None):
+    _check(load().recon_slab_prolong_add(_slab(lay_c), _slab_ptr(cnew, lay_c),
+                                         _slab_ptr(cold, lay_c) if cold is not None else None, float(scale),
+                                         _slab(lay_f), _slab_ptr(fine, lay_f), _stream(stream)))
+
+
+def recon_slab_plane_sums(lay, a, m, squared, out, stream=None):
+    import torch
+    _check(load().recon_slab_plane_sums(_slab(lay), _slab_ptr(a, lay), float(m), int(bool(squared)),
+                                        _dev_ptr(out, torch.float64, lay.hi - lay.lo), _stream(stream)))
+
+
+def recon_slab_eps_planes(lay, h, theta, g, c, out, stream=None):
+    import torch
+    _check(load().recon_slab_eps_planes(_slab(lay), float(h), _slab_ptr(theta, lay), _slab_ptr(g, lay), float(c),
+                                        _dev_ptr(out, torch.float64, lay.hi - lay.lo), _stream(stream)))
+
+
+def recon_slab_defect_min(lay, dH, rr, floor, out, stream=None):
+    import torch
+    _check(load().recon_slab_defect_min(_slab(lay), _slab_ptr(dH, lay), _slab_ptr(rr, lay), float(floor),
+                                        _dev_ptr(out, torch.float64, lay.hi - lay.lo), _stream(stream)))
+
+
+def recon_slab_form_rhs(lay, dH, rr, scale, g, stream=None):
+    _check(load().recon_slab_form_rhs(_slab(lay), _slab_ptr(dH, lay), _slab_ptr(rr, lay), float(scale),
+                                      _slab_ptr(g, lay), _stream(stream)))
+
+
+def recon_slab_sub(lay, a, m, stream=None):
+    _check(load().recon_slab_sub(_slab(lay), _slab_ptr(a, lay), float(m), _stream(stream)))

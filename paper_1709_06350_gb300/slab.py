@@ -507,6 +507,80 @@ class SlabSolver:
         return out
 
 
+class GpuSlabBackend:
+    """The per-rank steps as the recon_slab_* kernels of librecon.so, on this
+    process's current CUDA device and stream (FP64)."""
+
+    def __init__(self, device=None):
+        import torch
+        from . import recon
+        recon.load()
+        self.R = recon
+        self.torch = torch
+        self.comm_device = torch.device(device) if device is not None else torch.device("cuda")
+        self._work = {}
+
+    def zeros(self, lay):
+        return self.torch.zeros((lay.planes, lay.N, lay.N), dtype=self.torch.float64, device=self.comm_device)
+
+    def fill(self, a, v):
+        a.fill_(v)
+
+    def copy(self, dst, src):
+        dst.copy_(src)
+
+    def _scratch(self, lay):
+        key = (lay.N, lay.planes)
+        if key not in self._work:
+            self._work[key] = self.zeros(lay)
+        return self._work[key]
+
+    def sweep(self, t, g, c, h, lay, rule):
+        self.R.recon_slab_sweep(lay, h, rule, t, g, c, self._scratch(lay))
+
+    def residual(self, t, g, c, h, lay, r):
+        self.R.recon_slab_residual(lay, h, t, g, c, r)
+
+    def det(self, t, h, lay, out):
+        self.R.recon_slab_det(lay, h, t, out)
+
+    def restrict(self, f, lay_f, out, lay_c):
+        self.R.recon_slab_restrict(lay_f, f, lay_c, out)
+
+    def prolong_add(self, cn, co, lay_c, scale, f, lay_f):
+        self.R.recon_slab_prolong_add(lay_c, cn, co, scale, lay_f, f)
+
+    def _per_plane(self, lay):
+        return self.torch.empty(lay.own, dtype=self.torch.float64, device=self.comm_device)
+
+    def plane_sums(self, a, lay, m, sq):
+        out = self._per_plane(lay)
+        self.R.recon_slab_plane_sums(lay, a, m, sq, out)
+        return out
+
+    def eps_planes(self, t, g, c, h, lay):
+        out = self._per_plane(lay)
+        self.R.recon_slab_eps_planes(lay, h, t, g, c, out)
+        return out
+
+    def defect_min(self, dH, rr, lay, floor):
+        if floor <= 0.0:
+            return 1.0
+        out = self._per_plane(lay)
+        self.R.recon_slab_defect_min(lay, dH, rr, floor, out)
+        s = min(out.tolist())
+        return 0.0 if s < 1e-3 else s
+
+    def form_rhs(self, dH, rr, s, lay, g):
+        self.R.recon_slab_form_rhs(lay, dH, rr, s, g)
+
+    def sub(self, a, m, lay):
+        self.R.recon_slab_sub(lay, a, m)
+
+    def coarse_solve(self, t, g, c, h, max_sweeps, rtol, rule):
+        self.R.recon_step_coarse_solve(t, g, c, h, max_sweeps, rtol, rule)
+
+
 def _ordered_sum(parts) -> float:
     """Add the plane partials of all ranks in plane order (rank order, then
     plane order within a rank), one IEEE addition at a time."""

@@ -76,3 +76,80 @@ class OracleSlabBackend:
         out, _ = self.O.coarse_solve(t.numpy(), g.numpy(), c, h, max_sweeps, rtol, "rb-snapshot",
                                      "newton1" if rule == 0 else "exact")
         t.copy_(torch.from_numpy(out))
+
+
+class ThreadGroup:
+    """P ranks as threads of one process: the collectives of slab.Comm done
+    through shared slots and a barrier (with a timeout, so a rank that
+    diverges fails the test instead of waiting forever).  Tensors are cloned
+    when posted, so on a GPU every copy is ordered on the shared stream after
+    the kernels that wrote its source."""
+
+    def __init__(self, P, timeout=120.0):
+        import threading
+        self.P = P
+        self.slots = [None] * P
+        self.barrier = threading.Barrier(P, timeout=timeout)
+
+
+class ThreadComm:
+    def __init__(self, group, rank):
+        self.g, self.rank, self.size = group, rank, group.P
+
+    def _post(self, obj):
+        self.g.slots[self.rank] = obj
+        self.g.barrier.wait()
+        vals = list(self.g.slots)
+        self.g.barrier.wait()
+        return vals
+
+    def exchange(self, send_lo, send_hi, recv_lo, recv_hi):
+        vals = self._post((send_lo.clone(), send_hi.clone()))
+        P = self.size
+        recv_lo.copy_(vals[(self.rank - 1) % P][1])
+        recv_hi.copy_(vals[(self.rank + 1) % P][0])
+
+    def all_gather(self, t):
+        return self._post(t.clone())
+
+    def gather0(self, t):
+        vals = self._post(t.clone())
+        return vals if self.rank == 0 else None
+
+    def scatter0(self, chunks, out):
+        vals = self._post([c.clone() for c in chunks] if self.rank == 0 else None)
+        out.copy_(vals[0][self.rank])
+
+    def broadcast0(self, t):
+        vals = self._post(t.clone() if self.rank == 0 else None)
+        t.copy_(vals[0])
+        return t
+
+    def min(self, t):
+        vals = self._post(t.clone())
+        t.copy_(torch.stack(vals).min(0).values)
+        return t
+
+
+def run_threads(P, fn):
+    """fn(rank, comm) on P threads; returns the results in rank order (an
+    exception in any rank is raised here)."""
+    import threading
+    grp = ThreadGroup(P)
+    out, err = [None] * P, []
+
+    def body(r):
+        try:
+            out[r] = fn(r, ThreadComm(grp, r))
+        except BaseException as e:          # noqa: BLE001 - reported below
+            err.append(e)
+            grp.barrier.abort()
+
+    th = [threading.Thread(target=body, args=(r,)) for r in range(P)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    if err:
+        raise err[0]
+    return out

@@ -72,3 +72,33 @@ def test_binding_refuses_cpu_tensors():
     from paper_1709_06350_gb300 import recon
     with pytest.raises(TypeError):
         recon._dev_ptr(torch.zeros(4))
+
+
+def test_slab_layouts_rejected_before_launch():
+    """Bad slab layouts come back RECON_E_INVALID without touching a GPU."""
+    import ctypes
+    from paper_1709_06350_gb300 import recon
+    from paper_1709_06350_gb300 import build
+    build.build()
+    lib = recon.load()
+    fake = ctypes.c_void_p(256)
+
+    def lay(N, planes, first, lo, hi):
+        return ctypes.byref(recon.recon_slab(N, planes, first, lo, hi))
+
+    bad = [lay(7, 7, 0, 0, 7),          # odd N
+           lay(2048, 2048, 0, 0, 2048),  # beyond the 32-bit offset range
+           lay(16, 12, -2, 1, 11),       # sweep needs two halo planes each side
+           lay(16, 12, -2, 2, 11),
+           lay(16, 20, -2, 2, 18),       # a slab holding a plane twice
+           lay(16, 8, 0, 4, 4)]          # no own planes
+    for L in bad:
+        assert lib.recon_slab_sweep(L, 1.0, 0, fake, fake, 0.0, fake, None) == 1
+    assert lib.recon_slab_residual(lay(16, 8, 0, 0, 8), 1.0, fake, fake, 0.0, fake, None) == 1
+    # restriction: the fine array must hold both sons of every own coarse plane
+    assert lib.recon_slab_restrict(lay(16, 8, 0, 0, 8), fake, lay(8, 5, 0, 0, 5), fake, None) == 1
+    # prolongation: the coarse array must hold the parents' neighbours
+    assert lib.recon_slab_prolong_add(lay(8, 4, 0, 0, 4), fake, None, 1.0, lay(16, 8, 0, 0, 8), fake,
+                                      None) == 1
+    assert lib.recon_slab_defect_min(lay(16, 16, 0, 0, 16), fake, fake, 0.0, fake, None) == 1
+    assert b"recon_slab" in lib.recon_last_error(None)

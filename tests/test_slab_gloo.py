@@ -154,3 +154,21 @@ def test_gloo_whole_grid_on_rank0(O):
     assert all(r[2] == [False, False] for r in res)
     b = _density(O, 8, 7)
     _same_as_oracle(O, b, np.concatenate([r[0] for r in res]), res[0][1], 1e-9, 10)
+
+
+def test_thread_ranks_equal_oracle(O):
+    """The same decomposition with ranks as threads of one process (the form
+    the GPU test uses on one GPU) also reproduces the oracle bit for bit."""
+    from tests.slab_backends import OracleSlabBackend, run_threads
+    N, tol, max_cycles = 32, 1e-9, 12
+    b = _density(O, N, 47)
+
+    def rank_fn(r, comm):
+        sv = slab.SlabSolver(N, L_BOX, OracleSlabBackend(O), comm, slab.SlabParams(**KW, min_planes=2))
+        n = N // 4
+        th, info = sv.solve(torch.from_numpy(np.ascontiguousarray(b[r * n:(r + 1) * n])), tol, max_cycles)
+        return th.numpy().copy(), info, sv.split
+
+    res = run_threads(4, rank_fn)
+    assert res[0][2] == [True, True, True, False]
+    _same_as_oracle(O, b, np.concatenate([r[0] for r in res]), res[0][1], tol, max_cycles)
