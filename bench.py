@@ -408,7 +408,23 @@ def main():
         fp64 = {"time_to_tol_s": a.elapsed_time(bev) / 1e3, "cycles": st64["cycles"],
                 "rel_residual": st64["rel_residual"], "mixed_vs_fp64_rel_l2": diff}
         s64.close()
-        del p64
+        # the mixed path with its fine-grid residual in plain FP64 (the literal
+        # form) beside the double-float default: same schedule, same density
+        solver.configure(mixed_df_residual=0)
+        pr = torch.zeros_like(b)
+        solver.solve(b, phi=pr, tol=tol, max_cycles=40)
+        torch.cuda.synchronize()
+        a.record(stream)
+        _, str64 = solver.solve(b, phi=pr, tol=tol, max_cycles=40)
+        bev.record(stream)
+        torch.cuda.synchronize()
+        fp64["mixed_fp64_residual"] = {
+            "time_to_tol_s": a.elapsed_time(bev) / 1e3, "fas_cycles": str64["cycles"],
+            "outer_iterations": str64["outer_iterations"], "rel_residual": str64["rel_residual"],
+            "vs_fp64_rel_l2": float(torch.linalg.norm(pr - p64) / torch.linalg.norm(p64)),
+            "vs_double_float_rel_l2": float(torch.linalg.norm(pr - phi) / torch.linalg.norm(phi))}
+        solver.configure(mixed_df_residual=1)
+        del p64, pr
 
     # ---- rooflines of the two FP32 smoothers, timed in isolation at N^3
     kern = kernel_roofline(recon, torch, N, L, dev, stream)
