@@ -54,6 +54,9 @@ def parse():
     p.add_argument("--fd-directions", type=int, default=32)
     p.add_argument("--kernel-only", type=int, default=0, metavar="N",
                    help="only time the roofline kernel at N^3 (small case for profilers)")
+    p.add_argument("--profile-solve", type=int, default=0, metavar="N",
+                   help="only run two whole mixed reconstructions of an N^3 field of the "
+                        "workload's recipe (a small case for profilers); prints their times")
     return p.parse_args()
 
 
@@ -229,6 +232,11 @@ def main():
                                torch.cuda.current_stream())
         print(json.dumps({"kernel_only": n, "kernels": roof}), flush=True)
         return 0
+
+    if args.profile_solve:
+        pbuild.build()
+        torch.cuda.set_device(0)
+        return profile_solve(recon, synth, torch, args.profile_solve, synth.WORKLOADS[args.workload])
 
     from paper_1709_06350_gb300 import replicas
     world, rank, local = replicas.world()
@@ -902,6 +910,38 @@ def _time_launches(torch, stream, fn, reps):
 # moves (N/384)^3 times as much.  Valid for the kernels as they were
 # captured: re-measure after a change to either kernel.
 NCU_TRAFFIC_384 = {"LIN": 689.353472e6 + 208.309248e6, "FAS": 472.232960e6 + 210.356992e6}
+
+
+def profile_solve(recon, synth, torch, N, W):
+    """Two whole mixed reconstructions (CIC, density preparation, solve,
+    displacement) of an N^3 field of W's recipe at W's cell size (L = W.L N /
+    W.N), with the autotuned schedule of W's grid: a small case that runs
+    every kernel of the step, for a profiler.  Prints the two solve times."""
+    from paper_1709_06350_gb300 import autotune
+    dev = torch.device("cuda", 0)
+    L = W.L * N / W.N
+    _, dh = synth.linear_field(N, L, W.sigma_lin, W.seed, backend="torch", device=dev)
+    pos = synth.zeldovich_positions(dh, N, L).contiguous()
+    del dh
+    solver = recon.Solver(N, L, recon.RECON_MIXED)
+    autotune.apply(solver, W.N, recon.RECON_MIXED)
+    phi = torch.zeros((N, N, N), dtype=torch.float64, device=dev)
+    out = []
+    for _ in range(2):
+        rho = solver.deposit_cic(pos)
+        b = solver.smooth_density(rho, W.R)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, st = solver.solve(b, phi=phi, tol=W.tol, max_cycles=40)
+        torch.cuda.synchronize()
+        out.append(time.perf_counter() - t0)
+        solver.displace(phi, b)
+    torch.cuda.synchronize()
+    solver.close()
+    print(json.dumps({"profile_solve": N, "L": L, "solve_seconds": out, "fas_cycles": st["cycles"],
+                      "outer_iterations": st["outer_iterations"], "rel_residual": st["rel_residual"]}),
+          flush=True)
+    return 0
 
 
 def kernel_roofline(recon, torch, N, L, dev, stream):

@@ -66,4 +66,69 @@ __host__ __device__ __forceinline__ df df_from_double(double x)
 
 __device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
 
+// The same split as df_from_double, from the bit pattern with integer
+// operations only (FP64 instructions, conversions included, issue at 1/64 of
+// the FP32 rate; a split kernel spent its time waiting on them).  For
+// 2^-40 <= |x| < 2^126: hi rounds the 52-bit fraction to 23 bits (nearest,
+// ties to even; a carry into the exponent falls out of the integer addition),
+// and x - hi = (r - inc 2^29) 2^(e - 1075) exactly, r the 29 dropped bits and
+// inc the rounding increment, so lo is that integer rounded to a float once
+// and scaled by a power of two (exact).  Bit-identical to df_from_double in
+// that range; other x (zero, tiny, huge, non-finite) take df_from_double.
+__host__ __device__ __forceinline__ unsigned long long df_dbits(double x)
+{
+#ifdef __CUDA_ARCH__
+    return (unsigned long long)__double_as_longlong(x);
+#else
+    unsigned long long u;
+    __builtin_memcpy(&u, &x, sizeof u);
+    return u;
+#endif
+}
+__host__ __device__ __forceinline__ float df_fbits(unsigned u)
+{
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(u);
+#else
+    float f;
+    __builtin_memcpy(&f, &u, sizeof f);
+    return f;
+#endif
+}
+// RN(d) for |d| <= 2^29 on the FP32 pipes (no integer-to-float conversion
+// instruction): d = dh 2^14 + dl with 0 <= dl < 2^14; both parts are exact
+// floats by the 1.5 * 2^23 bias trick, and one fma rounds their exact sum.
+__host__ __device__ __forceinline__ float df_i2f(int d)
+{
+    const int dh = d >> 14, dl = d - dh * 16384;
+    const float fh = df_fbits(0x4B400000u + (unsigned)dh) - 12582912.0f;
+    const float fl = df_fbits(0x4B400000u + (unsigned)dl) - 12582912.0f;
+    return fmaf(fh, 16384.0f, fl);
+}
+
+// the FP64 split, out of line on the device so that the rare inputs outside
+// the integer path's range take a real branch (an inlined copy was evaluated
+// for every element and kept the FP64 pipe busy)
+#ifdef __CUDA_ARCH__
+__device__ __noinline__ df df_from_double_ool(double x) { return df_from_double(x); }
+#else
+inline df df_from_double_ool(double x) { return df_from_double(x); }
+#endif
+__host__ __device__ __forceinline__ df df_from_double_bits(double x)
+{
+    const unsigned long long u = df_dbits(x);
+    const unsigned e = (unsigned)(u >> 52) & 0x7FFu;
+    if (e < 1023u - 40u || e > 1023u + 125u) return df_from_double_ool(x);
+    const unsigned sign = (unsigned)(u >> 63) << 31;
+    const unsigned long long m = u & 0xFFFFFFFFFFFFFull;
+    const unsigned r = (unsigned)(m & 0x1FFFFFFFull);      // the 29 dropped bits
+    const unsigned keep = (unsigned)(m >> 29);              // the 23 kept bits
+    const unsigned inc = (r > 0x10000000u || (r == 0x10000000u && (keep & 1u))) ? 1u : 0u;
+    const unsigned hbits = (((e - 1023u + 127u) << 23) | keep) + inc;
+    const int d = (int)r - (int)(inc << 29);                 // |d| <= 2^28
+    const float scale = df_fbits((e - 1075u + 127u) << 23);  // 2^(e - 1075), a normal float here
+    // signed remainder (a zero remainder gives +0, as x - hi does in FP64)
+    return {df_fbits(sign | hbits), df_i2f(sign ? -d : d) * scale};
+}
+
 }  // namespace recon

@@ -671,6 +671,18 @@ k_gauge(T *__restrict__ t, size_t n, const double *__restrict__ scal)
 // children (2I+a, 2J+b, 2K+c) of coarse cell (I, J, K) lies in the fine block
 // i, j, k in 2I-1 .. 2I+2 (etc.) without the corners of its two outer
 // planes: 56 loads instead of 8 x 19.  Window index 1 + a is child a.
+// CTAs per SM the windowed kernels are compiled for (their 56-value windows
+// need ~120 registers at 2; the FP32 residual/restriction and norm kernels
+// also fit at 3)
+#ifndef RECON_WIN_CTAS
+#define RECON_WIN_CTAS 2
+#endif
+#ifndef RECON_RR_CTAS_F
+#define RECON_RR_CTAS_F 2
+#endif
+#ifndef RECON_NW_CTAS_F
+#define RECON_NW_CTAS_F 2
+#endif
 struct Win {
     unsigned pl[4], row[4], col[4];
     __device__ __forceinline__ Win(int Nf, int I, int J, int K)
@@ -728,7 +740,7 @@ __device__ __forceinline__ Nb19<T> win_nb(const T (&Pm)[4][4], const T (&Pc)[4][
 // Residual norms of an even grid from the fine windows of its 2 x 2 x 2
 // blocks (7 loads per cell instead of 19); same outputs as k_residual_norms.
 template <typename T>
-__global__ void __launch_bounds__(kRowThreads, 2)
+__global__ void __launch_bounds__(kRowThreads, sizeof(T) == 4 ? RECON_NW_CTAS_F : RECON_WIN_CTAS)
 k_residual_norms_win(const T *__restrict__ t, const T *__restrict__ g,
                      const double *__restrict__ cptr, int N, T ih2, double *__restrict__ partials,
                      float *__restrict__ f32out, float *__restrict__ t32out)
@@ -789,7 +801,7 @@ static unsigned launch_residual_norms(const T *t, const T *g, const double *cptr
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kRowThreads, 2)
+__global__ void __launch_bounds__(kRowThreads, sizeof(T) == 4 ? RECON_RR_CTAS_F : RECON_WIN_CTAS)
 k_restrict_residual(const T *__restrict__ t, const T *__restrict__ g,
                     const double *__restrict__ cptr, int Nf, T ih2, T *__restrict__ tH,
                     T *__restrict__ toldH, T *__restrict__ rrH, double *__restrict__ partials)
@@ -927,31 +939,87 @@ k_form_rhs(T *__restrict__ gH, const T *__restrict__ dH, size_t nc,
 // fine += scale * P(cnew - cold), P cell-centred trilinear: per axis the
 // parent weighs 3/4 and the coarse neighbour on the fine cell's side 1/4.
 // scale = *pscale when pscale is given (0 = no correction), else `scale`.
+// A thread takes one coarse cell (threads along K, rows (I, J) grid-stride)
+// and its 2 x 2 x 2 children: the 27 coarse differences d = cnew - cold
+// around the parent are formed once and interpolated axis by axis (i, then
+// j, then k; the product weights of the trilinear form factorise), and each
+// child pair along k is read and written as one vector when `fine` is
+// aligned to a pair.
+template <typename T>
+struct Vec2;
+template <>
+struct Vec2<float> {
+    using type = float2;
+};
+template <>
+struct Vec2<double> {
+    using type = double2;
+};
+
 template <typename T>
 __global__ void __launch_bounds__(kRowThreads)
 k_prolong_add(const T *__restrict__ cnew, const T *__restrict__ cold, int Nc,
-              const double *__restrict__ pscale, double scale, T *__restrict__ fine)
+              const double *__restrict__ pscale, double scale, T *__restrict__ fine, int pairs)
 {
+    using V2 = typename Vec2<T>::type;
     const double sc = pscale ? *pscale : scale;
     if (sc == 0.0) return;
+    const T s = (T)sc, w0 = T(0.75), w1 = T(0.25);
     const int Nf = 2 * Nc;
-    FOR_ROWS(Nf, i, j)
+    FOR_ROWS(Nc, I, J)
     {
-        const int I = i >> 1, J = j >> 1;
-        const int I1 = (i & 1) ? (I + 1 == Nc ? 0 : I + 1) : (I == 0 ? Nc - 1 : I - 1);
-        const int J1 = (j & 1) ? (J + 1 == Nc ? 0 : J + 1) : (J == 0 ? Nc - 1 : J - 1);
-        for (int k = threadIdx.x; k < Nf; k += kRowX) {
-            const int K = k >> 1;
-            const int K1 = (k & 1) ? (K + 1 == Nc ? 0 : K + 1) : (K == 0 ? Nc - 1 : K - 1);
-            T acc = T(0);
-            for (int a = 0; a < 2; ++a)
-                for (int b = 0; b < 2; ++b)
-                    for (int cc = 0; cc < 2; ++cc) {
-                        const T w = (a ? T(0.25) : T(0.75)) * (b ? T(0.25) : T(0.75)) * (cc ? T(0.25) : T(0.75));
-                        const unsigned o = offs(Nc, a ? I1 : I, b ? J1 : J, cc ? K1 : K);
-                        acc += w * (cold ? cnew[o] - cold[o] : cnew[o]);
+        const int Ip[3] = {I == 0 ? Nc - 1 : I - 1, I, I + 1 == Nc ? 0 : I + 1};
+        const int Jp[3] = {J == 0 ? Nc - 1 : J - 1, J, J + 1 == Nc ? 0 : J + 1};
+        for (int K = threadIdx.x; K < Nc; K += kRowX) {
+            const int Kp[3] = {K == 0 ? Nc - 1 : K - 1, K, K + 1 == Nc ? 0 : K + 1};
+            // the four fine pairs first: their DRAM reads overlap the coarse loads
+            unsigned fo[2][2];
+            V2 fv[2][2];
+#pragma unroll
+            for (int ei = 0; ei < 2; ++ei)
+#pragma unroll
+                for (int ej = 0; ej < 2; ++ej) {
+                    fo[ei][ej] = offs(Nf, 2 * I + ei, 2 * J + ej, 2 * K);
+                    if (pairs) {
+                        fv[ei][ej] = *reinterpret_cast<const V2 *>(fine + fo[ei][ej]);
+                    } else {
+                        fv[ei][ej].x = fine[fo[ei][ej]];
+                        fv[ei][ej].y = fine[fo[ei][ej] + 1];
                     }
-            fine[offs(Nf, i, j, k)] += (T)sc * acc;
+                }
+            T d[3][3][3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const unsigned o = offs(Nc, Ip[a], Jp[b], Kp[c]);
+                        d[a][b][c] = cold ? cnew[o] - cold[o] : cnew[o];
+                    }
+#pragma unroll
+            for (int ei = 0; ei < 2; ++ei) {
+                T u[3][3];   // along i: child ei takes the neighbour 2 (ei = 1) or 0
+#pragma unroll
+                for (int b = 0; b < 3; ++b)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) u[b][c] = w0 * d[1][b][c] + w1 * d[ei ? 2 : 0][b][c];
+#pragma unroll
+                for (int ej = 0; ej < 2; ++ej) {
+                    T v[3];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) v[c] = w0 * u[1][c] + w1 * u[ej ? 2 : 0][c];
+                    V2 x = fv[ei][ej];
+                    x.x += s * (w0 * v[1] + w1 * v[0]);
+                    x.y += s * (w0 * v[1] + w1 * v[2]);
+                    if (pairs) {
+                        *reinterpret_cast<V2 *>(fine + fo[ei][ej]) = x;
+                    } else {
+                        fine[fo[ei][ej]] = x.x;
+                        fine[fo[ei][ej] + 1] = x.y;
+                    }
+                }
+            }
         }
     }
 }
@@ -961,7 +1029,8 @@ cudaError_t prolong_add(int Nc, const T *cnew, const T *cold, const double *psca
                         double scale, T *fine, cudaStream_t s)
 {
     note_launch();
-    k_prolong_add<T><<<row_grid(2 * Nc), row_block(), 0, s>>>(cnew, cold, Nc, pscale, scale, fine);
+    const int pairs = ((uintptr_t)fine % (2 * sizeof(T))) == 0;
+    k_prolong_add<T><<<row_grid(Nc), row_block(), 0, s>>>(cnew, cold, Nc, pscale, scale, fine, pairs);
     return cudaGetLastError();
 }
 template cudaError_t prolong_add<double>(int, const double *, const double *, const double *, double, double *, cudaStream_t);
@@ -1239,7 +1308,7 @@ k_split_df(const double *__restrict__ a, float *__restrict__ hi, float *__restri
 {
     const size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (id < n) {
-        const df v = df_from_double(a[id]);
+        const df v = df_from_double_bits(a[id]);
         hi[id] = v.hi;
         lo[id] = v.lo;
     }
@@ -1395,7 +1464,7 @@ cudaError_t linear_sweep(int N, double h, float *e, const float *f, const float 
 // fine windows of e and (FROM_TH) theta; otherwise the cofactors come from
 // the colour-split arrays cof.
 template <bool FROM_TH>
-__global__ void __launch_bounds__(kRowThreads, 2)
+__global__ void __launch_bounds__(kRowThreads, RECON_WIN_CTAS)
 k_lin_restrict_residual(const float *__restrict__ e, const float *__restrict__ f,
                         const float *__restrict__ cof, const float *__restrict__ th, int Nf,
                         float ih2, float *__restrict__ fH, double *__restrict__ partials)
