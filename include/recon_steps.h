@@ -50,7 +50,8 @@ recon_status recon_step_prolong_add(int Nc, int prec, const void *cnew,
 /* Coarsest-grid solve: sweeps of recon_step_sweep until the mean-free rms
  * residual falls below rtol times its start, or (when rtol > 0) a sweep no
  * longer lowers it, or max_sweeps sweeps ran; one thread block,
- * N^3 <= 4096.  sweeps_done: device int (nullable). */
+ * N^3 <= 4096, relaxed in the block's shared memory (work is reserved: the
+ * current kernel does not touch it).  sweeps_done: device int (nullable). */
 recon_status recon_step_coarse_solve(int N, double h, int prec, int rule, void *theta,
                                      const void *g, double c, int max_sweeps,
                                      double rtol, void *work, int *sweeps_done,

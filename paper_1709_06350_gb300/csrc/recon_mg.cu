@@ -481,6 +481,7 @@ static cudaError_t fused_attr()
 }
 
 static bool g_kernels_ready = false;
+static cudaError_t coarse_attrs();   // shared-memory limits of the coarsest solves
 // planes per CTA of the fused sweeps for the solve being enqueued on this
 // host thread (recon_config.fused_chunk; 0 = by grid size)
 static thread_local int g_fused_chunk = 0;
@@ -492,6 +493,7 @@ cudaError_t prepare_kernels()
     if (e == cudaSuccess) e = fused_attr<double, false>();
     if (e == cudaSuccess) e = fused_attr<float, true>();
     if (e == cudaSuccess) e = prepare_reg_sweeps();
+    if (e == cudaSuccess) e = coarse_attrs();
     if (e == cudaSuccess) g_kernels_ready = true;
     return e;
 }
@@ -1077,18 +1079,29 @@ __global__ void __launch_bounds__(kCoarseThreads)
 k_coarse_solve(T *t, T *work, const T *g, const double *cptr, double cval, int N, T ih2, T h2_6,
                int rule, int max_sweeps, double rtol, int *sweeps_out)
 {
+    // the grid (<= 16^3) is relaxed in shared memory: theta, the colour
+    // pass's scratch and g are staged once and theta is written back at the
+    // end (the global scratch `work` is not touched)
+    extern __shared__ __align__(16) unsigned char coarse_smem[];
     __shared__ double sh[32];
     __shared__ double sval;
+    const int n = N * N * N;
+    T *ts = reinterpret_cast<T *>(coarse_smem), *ws = ts + n, *gs = ws + n;
+    for (int id = threadIdx.x; id < n; id += blockDim.x) {
+        ts[id] = t[id];
+        gs[id] = g[id];
+    }
+    __syncthreads();
     const T c = (T)(cptr ? *cptr : cval);
     const int half = N >> 1;
     const int npairs = N * N * half;
-    const double r0 = coarse_proj_rms<T>(t, work, g, c, N, ih2, sh, &sval);
+    const double r0 = coarse_proj_rms<T>(ts, ws, gs, c, N, ih2, sh, &sval);
     double prev = r0;
     int sw = 0;
     while (sw < max_sweeps) {
         for (int colour = 0; colour < 2; ++colour) {
-            const T *src = colour == 0 ? t : work;
-            T *dst = colour == 0 ? work : t;
+            const T *src = colour == 0 ? ts : ws;
+            T *dst = colour == 0 ? ws : ts;
             for (int pi = threadIdx.x; pi < npairs; pi += blockDim.x) {
                 const int m = pi % half, r = pi / half;
                 const int j = r % N, i = r / N;
@@ -1096,7 +1109,7 @@ k_coarse_solve(T *t, T *work, const T *g, const double *cptr, double cval, int N
                 const int ka = 2 * m + par, kb = 2 * m + 1 - par;
                 const Nb19<T> nb = load19<T>(src, N, i, j, ka);
                 T s, p, q;
-                cubic_coeffs(nb, ih2, g[offs(N, i, j, ka)] + c, s, p, q);
+                cubic_coeffs(nb, ih2, gs[offs(N, i, j, ka)] + c, s, p, q);
                 const T vnew = point_update(nb.c, h2_6, s, p, q, rule);
                 const T vcopy = src[offs(N, i, j, kb)];
                 dst[offs(N, i, j, ka)] = vnew;
@@ -1105,11 +1118,12 @@ k_coarse_solve(T *t, T *work, const T *g, const double *cptr, double cval, int N
             __syncthreads();
         }
         ++sw;
-        const double cur = coarse_proj_rms<T>(t, work, g, c, N, ih2, sh, &sval);
+        const double cur = coarse_proj_rms<T>(ts, ws, gs, c, N, ih2, sh, &sval);
         if (cur <= rtol * r0) break;
         if (rtol > 0.0 && cur >= prev) break;   // no progress: round-off floor
         prev = cur;
     }
+    for (int id = threadIdx.x; id < n; id += blockDim.x) t[id] = ts[id];
     if (ltid() == 0 && sweeps_out) *sweeps_out = sw;
 }
 
@@ -1119,9 +1133,14 @@ cudaError_t coarse_solve(int N, double h, int rule, T *t, const T *g, const doub
                          cudaStream_t s)
 {
     const T ih2 = (T)(1.0 / (h * h)), h2_6 = (T)(h * h / 6.0);
+    if ((long)N * N * N > kMaxCoarseCells) return cudaErrorInvalidValue;
+    if (!g_kernels_ready) {
+        const cudaError_t e = prepare_kernels();
+        if (e != cudaSuccess) return e;
+    }
     note_launch();
-    k_coarse_solve<T><<<1, kCoarseThreads, 0, s>>>(t, work, g, cptr, cval, N, ih2, h2_6, rule,
-                                                   max_sweeps, rtol, sweeps_out);
+    k_coarse_solve<T><<<1, kCoarseThreads, 3 * sizeof(T) * (size_t)N * N * N, s>>>(
+        t, work, g, cptr, cval, N, ih2, h2_6, rule, max_sweeps, rtol, sweeps_out);
     return cudaGetLastError();
 }
 template cudaError_t coarse_solve<double>(int, double, int, double *, const double *, const double *, double, int, double, double *, int *, cudaStream_t);
@@ -1518,16 +1537,26 @@ __global__ void __launch_bounds__(kCoarseThreads)
 k_lin_coarse(float *e, float *work, const float *f, const float *cof, int N, float ih2,
              int max_sweeps, double rtol)
 {
+    // relaxed in shared memory: e, the colour pass's scratch, f and the six
+    // cofactor arrays are staged once, e is written back at the end
+    extern __shared__ __align__(16) unsigned char coarse_smem[];
     const size_t ncof = (size_t)N * N * N;
     __shared__ double sh[32];
     __shared__ double sval;
     const int n = N * N * N, half = N >> 1, npairs = N * N * half;
+    float *es = reinterpret_cast<float *>(coarse_smem), *ws = es + n, *fs = ws + n, *cs = fs + n;
+    for (int id = threadIdx.x; id < n; id += blockDim.x) {
+        es[id] = e[id];
+        fs[id] = f[id];
+    }
+    for (int id = threadIdx.x; id < 6 * n; id += blockDim.x) cs[id] = cof[id];
+    __syncthreads();
     auto proj_rms = [&]() -> double {
         double sr = 0.0;
         for (int id = threadIdx.x; id < n; id += blockDim.x) {
             const int k = id % N, j = (id / N) % N, i = id / (N * N);
-            const float r = f[id] - jac_apply(cof_at(cof, ncof, cof_slot(N, i, j, k)), load19<float>(e, N, i, j, k), ih2);
-            work[id] = r;
+            const float r = fs[id] - jac_apply(cof_at(cs, ncof, cof_slot(N, i, j, k)), load19<float>(es, N, i, j, k), ih2);
+            ws[id] = r;
             sr += (double)r;
         }
         double tot = block_sum<kCoarseThreads>(sr, sh);
@@ -1536,7 +1565,7 @@ k_lin_coarse(float *e, float *work, const float *f, const float *cof, int N, flo
         const double m = sval;
         double s2 = 0.0;
         for (int id = threadIdx.x; id < n; id += blockDim.x) {
-            const double d = (double)work[id] - m;
+            const double d = (double)ws[id] - m;
             s2 += d * d;
         }
         tot = block_sum<kCoarseThreads>(s2, sh);
@@ -1550,18 +1579,18 @@ k_lin_coarse(float *e, float *work, const float *f, const float *cof, int N, flo
     double prev = r0;
     for (int sw = 0; sw < max_sweeps; ++sw) {
         for (int colour = 0; colour < 2; ++colour) {
-            const float *src = colour == 0 ? e : work;
-            float *dst = colour == 0 ? work : e;
+            const float *src = colour == 0 ? es : ws;
+            float *dst = colour == 0 ? ws : es;
             for (int pi = threadIdx.x; pi < npairs; pi += blockDim.x) {
                 const int m = pi % half, r = pi / half;
                 const int j = r % N, i = r / N;
                 const int par = (colour + i + j) & 1;
                 const int ka = 2 * m + par, kb = 2 * m + 1 - par;
-                const Cof<float> a = cof_at(cof, ncof, cof_slot(N, i, j, ka));
+                const Cof<float> a = cof_at(cs, ncof, cof_slot(N, i, j, ka));
                 const Nb19<float> ev = load19<float>(src, N, i, j, ka);
                 const float Je = jac_apply(a, ev, ih2);
                 const float diag = -2.0f * (a.xx + a.yy + a.zz) * ih2;
-                const float vnew = ev.c + (f[offs(N, i, j, ka)] - Je) / diag;
+                const float vnew = ev.c + (fs[offs(N, i, j, ka)] - Je) / diag;
                 const float vcopy = src[offs(N, i, j, kb)];
                 dst[offs(N, i, j, ka)] = vnew;
                 dst[offs(N, i, j, kb)] = vcopy;
@@ -1573,6 +1602,20 @@ k_lin_coarse(float *e, float *work, const float *f, const float *cof, int N, flo
         if (rtol > 0.0 && cur >= prev) break;   // no progress: round-off floor
         prev = cur;
     }
+    for (int id = threadIdx.x; id < n; id += blockDim.x) e[id] = es[id];
+}
+
+static cudaError_t coarse_attrs()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_coarse_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(3 * sizeof(double) * kMaxCoarseCells));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_coarse_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(3 * sizeof(float) * kMaxCoarseCells));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_lin_coarse, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(9 * sizeof(float) * kMaxCoarseCells));
+    return e;
 }
 
 
@@ -1804,7 +1847,7 @@ cudaError_t lin_vcycle(recon_handle *H, int l)
     const float ih2 = (float)(1.0 / (h * h));
     if (l == H->nlev - 1) {
         note_launch();
-        k_lin_coarse<<<1, kCoarseThreads, 0, s>>>(H->e32[l], H->work32, H->f32[l], H->cof32[l], N,
+        k_lin_coarse<<<1, kCoarseThreads, 9 * sizeof(float) * ncell(N), s>>>(H->e32[l], H->work32, H->f32[l], H->cof32[l], N,
                                                   ih2, cf.coarse_max_sweeps, cf.coarse_rtol);
         return cudaGetLastError();
     }
