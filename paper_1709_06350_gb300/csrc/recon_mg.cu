@@ -1045,7 +1045,7 @@ template cudaError_t prolong_add<float>(int, const float *, const float *, const
 // t and work are read and written by different threads of the block across
 // __syncthreads(), so they are plain (not read-only) pointers.
 // ======================================================================
-template <typename T>
+template <typename T, int NT>
 __device__ double coarse_proj_rms(const T *t, T *work, const T *g, T c, int N, T ih2,
                                   double *sh, double *sval)
 {
@@ -1057,7 +1057,7 @@ __device__ double coarse_proj_rms(const T *t, T *work, const T *g, T c, int N, T
         work[id] = r;
         sr += (double)r;
     }
-    double tot = block_sum<kCoarseThreads>(sr, sh);
+    double tot = block_sum<NT>(sr, sh);
     if (ltid() == 0) *sval = tot / n;
     __syncthreads();
     const double m = *sval;
@@ -1066,7 +1066,7 @@ __device__ double coarse_proj_rms(const T *t, T *work, const T *g, T c, int N, T
         const double d = (double)work[id] - m;
         s2 += d * d;
     }
-    tot = block_sum<kCoarseThreads>(s2, sh);
+    tot = block_sum<NT>(s2, sh);
     if (ltid() == 0) *sval = sqrt(tot / n);
     __syncthreads();
     const double v = *sval;
@@ -1074,8 +1074,8 @@ __device__ double coarse_proj_rms(const T *t, T *work, const T *g, T c, int N, T
     return v;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kCoarseThreads)
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT)
 k_coarse_solve(T *t, T *work, const T *g, const double *cptr, double cval, int N, T ih2, T h2_6,
                int rule, int max_sweeps, double rtol, int *sweeps_out)
 {
@@ -1095,7 +1095,7 @@ k_coarse_solve(T *t, T *work, const T *g, const double *cptr, double cval, int N
     const T c = (T)(cptr ? *cptr : cval);
     const int half = N >> 1;
     const int npairs = N * N * half;
-    const double r0 = coarse_proj_rms<T>(ts, ws, gs, c, N, ih2, sh, &sval);
+    const double r0 = coarse_proj_rms<T, NT>(ts, ws, gs, c, N, ih2, sh, &sval);
     double prev = r0;
     int sw = 0;
     while (sw < max_sweeps) {
@@ -1118,7 +1118,7 @@ k_coarse_solve(T *t, T *work, const T *g, const double *cptr, double cval, int N
             __syncthreads();
         }
         ++sw;
-        const double cur = coarse_proj_rms<T>(ts, ws, gs, c, N, ih2, sh, &sval);
+        const double cur = coarse_proj_rms<T, NT>(ts, ws, gs, c, N, ih2, sh, &sval);
         if (cur <= rtol * r0) break;
         if (rtol > 0.0 && cur >= prev) break;   // no progress: round-off floor
         prev = cur;
@@ -1139,8 +1139,19 @@ cudaError_t coarse_solve(int N, double h, int rule, T *t, const T *g, const doub
         if (e != cudaSuccess) return e;
     }
     note_launch();
-    k_coarse_solve<T><<<1, kCoarseThreads, 3 * sizeof(T) * (size_t)N * N * N, s>>>(
-        t, work, g, cptr, cval, N, ih2, h2_6, rule, max_sweeps, rtol, sweeps_out);
+    // one thread per cell pair up to 128 pairs (the block-wide sums and
+    // barriers of every sweep are cheaper with fewer warps), 512 beyond
+    const size_t smem = 3 * sizeof(T) * (size_t)N * N * N;
+    const int pairs = N * N * N / 2;
+    if (pairs <= 64)
+        k_coarse_solve<T, 64><<<1, 64, smem, s>>>(t, work, g, cptr, cval, N, ih2, h2_6, rule, max_sweeps, rtol,
+                                                  sweeps_out);
+    else if (pairs <= 128)
+        k_coarse_solve<T, 128><<<1, 128, smem, s>>>(t, work, g, cptr, cval, N, ih2, h2_6, rule, max_sweeps,
+                                                    rtol, sweeps_out);
+    else
+        k_coarse_solve<T, kCoarseThreads><<<1, kCoarseThreads, smem, s>>>(t, work, g, cptr, cval, N, ih2, h2_6,
+                                                                          rule, max_sweeps, rtol, sweeps_out);
     return cudaGetLastError();
 }
 template cudaError_t coarse_solve<double>(int, double, int, double *, const double *, const double *, double, int, double, double *, int *, cudaStream_t);
@@ -1533,7 +1544,8 @@ k_lin_restrict_residual(const float *__restrict__ e, const float *__restrict__ f
     if (ltid() == 0) partials[4 * blockIdx.x + 0] = v;
 }
 
-__global__ void __launch_bounds__(kCoarseThreads)
+template <int NT>
+__global__ void __launch_bounds__(NT)
 k_lin_coarse(float *e, float *work, const float *f, const float *cof, int N, float ih2,
              int max_sweeps, double rtol)
 {
@@ -1559,7 +1571,7 @@ k_lin_coarse(float *e, float *work, const float *f, const float *cof, int N, flo
             ws[id] = r;
             sr += (double)r;
         }
-        double tot = block_sum<kCoarseThreads>(sr, sh);
+        double tot = block_sum<NT>(sr, sh);
         if (ltid() == 0) sval = tot / n;
         __syncthreads();
         const double m = sval;
@@ -1568,7 +1580,7 @@ k_lin_coarse(float *e, float *work, const float *f, const float *cof, int N, flo
             const double d = (double)ws[id] - m;
             s2 += d * d;
         }
-        tot = block_sum<kCoarseThreads>(s2, sh);
+        tot = block_sum<NT>(s2, sh);
         if (ltid() == 0) sval = sqrt(tot / n);
         __syncthreads();
         const double v = sval;
@@ -1605,16 +1617,29 @@ k_lin_coarse(float *e, float *work, const float *f, const float *cof, int N, flo
     for (int id = threadIdx.x; id < n; id += blockDim.x) e[id] = es[id];
 }
 
+template <typename T, int NT>
+static cudaError_t coarse_attr()
+{
+    return cudaFuncSetAttribute(k_coarse_solve<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(3 * sizeof(T) * kMaxCoarseCells));
+}
+template <int NT>
+static cudaError_t lin_coarse_attr()
+{
+    return cudaFuncSetAttribute(k_lin_coarse<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(9 * sizeof(float) * kMaxCoarseCells));
+}
 static cudaError_t coarse_attrs()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_coarse_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(3 * sizeof(double) * kMaxCoarseCells));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_coarse_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(3 * sizeof(float) * kMaxCoarseCells));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_lin_coarse, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(9 * sizeof(float) * kMaxCoarseCells));
+    cudaError_t e = coarse_attr<double, 64>();
+    if (e == cudaSuccess) e = coarse_attr<double, 128>();
+    if (e == cudaSuccess) e = coarse_attr<double, kCoarseThreads>();
+    if (e == cudaSuccess) e = coarse_attr<float, 64>();
+    if (e == cudaSuccess) e = coarse_attr<float, 128>();
+    if (e == cudaSuccess) e = coarse_attr<float, kCoarseThreads>();
+    if (e == cudaSuccess) e = lin_coarse_attr<64>();
+    if (e == cudaSuccess) e = lin_coarse_attr<128>();
+    if (e == cudaSuccess) e = lin_coarse_attr<kCoarseThreads>();
     return e;
 }
 
@@ -1847,8 +1872,18 @@ cudaError_t lin_vcycle(recon_handle *H, int l)
     const float ih2 = (float)(1.0 / (h * h));
     if (l == H->nlev - 1) {
         note_launch();
-        k_lin_coarse<<<1, kCoarseThreads, 9 * sizeof(float) * ncell(N), s>>>(H->e32[l], H->work32, H->f32[l], H->cof32[l], N,
-                                                  ih2, cf.coarse_max_sweeps, cf.coarse_rtol);
+        const size_t smem = 9 * sizeof(float) * ncell(N);
+        const int pairs = (int)(ncell(N) / 2);
+        if (pairs <= 64)
+            k_lin_coarse<64><<<1, 64, smem, s>>>(H->e32[l], H->work32, H->f32[l], H->cof32[l], N, ih2,
+                                                 cf.coarse_max_sweeps, cf.coarse_rtol);
+        else if (pairs <= 128)
+            k_lin_coarse<128><<<1, 128, smem, s>>>(H->e32[l], H->work32, H->f32[l], H->cof32[l], N, ih2,
+                                                   cf.coarse_max_sweeps, cf.coarse_rtol);
+        else
+            k_lin_coarse<kCoarseThreads><<<1, kCoarseThreads, smem, s>>>(H->e32[l], H->work32, H->f32[l],
+                                                                         H->cof32[l], N, ih2, cf.coarse_max_sweeps,
+                                                                         cf.coarse_rtol);
         return cudaGetLastError();
     }
     CK(lin_sweep(N, h, H->e32[l], H->f32[l], H->cof32[l], H->t32[l], cf.nu1, H->work32, s));
