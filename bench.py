@@ -323,6 +323,11 @@ def main():
     st = last["st"]
     # the solve alone, nothing else on the GPU (time to tolerance)
     ref_b, ref_dl = last["b"].clone(), last["dl"]
+    # the paper's own convergence measure of the same solve (untimed: one FP64
+    # pass with the cubic's largest root per cell)
+    solver.configure(report_paper_eps=1)
+    _, st_eps = solver.solve(ref_b, phi=phi, tol=tol, max_cycles=40)
+    solver.configure(report_paper_eps=0)
     solve_times = []
     torch.cuda.synchronize()
     for _ in range(3):
@@ -517,7 +522,7 @@ def main():
                               "mixed_inside_step": solve_in_step_ms / 1e3},
             "solve": {"fas_cycles": st["cycles"], "outer_iterations": st["outer_iterations"],
                       "rel_residual": st["rel_residual"], "compat_c": st["compat_c"],
-                      "history": st["history"]},
+                      "paper_eps": st_eps["paper_eps"], "history": st["history"]},
             "fp64_path": fp64,
             "r_k": {"k_h_per_Mpc": list(rk.keys()), "r": list(rk.values()),
                     "fields": "delta_r (displacement output, Lagrangian grid) vs the seeded "

@@ -69,7 +69,7 @@ typedef enum {
  * coarse_max_sweeps = 200, coarse_rtol = 1e-3, rule = NEWTON1, start = FMG,
  * scale_floor = 0.5, mixed_switch_rtol = 1e-4, mixed_fas_max_cycles = 12,
  * mixed_linear_vcycles = 2, mixed_df_residual = 1, fused_chunk = 0,
- * adjoint_store_cofactors = 0. */
+ * adjoint_store_cofactors = 0, report_paper_eps = 0. */
 typedef struct {
     int nu1, nu2;               /* pre- / post-smoothing sweeps per level          */
     int coarse_max_sweeps;      /* coarsest grid: sweep cap                        */
@@ -98,6 +98,9 @@ typedef struct {
                                    again from phi in every application of J^T
                                    (grids of side a multiple of 32; saves 48 N^3
                                    bytes); 1 = kept in memory (faster)          */
+    int report_paper_eps;       /* recon_solve: 1 = fill recon_stats.paper_eps
+                                   (one FP64 pass with the cubic's largest root
+                                   per cell: ~0.3 s at 512^3); 0 = NaN         */
 } recon_config;
 
 #define RECON_HISTORY_MAX 64
@@ -109,6 +112,11 @@ typedef struct {
     double rel_residual;        /* ||r - mean r||_2 / ||b - 1||_2 at exit, r the
                                    FP64 residual b + c - det(I + H phi)            */
     double compat_c;            /* the scalar c of (*)                             */
+    double paper_eps;           /* the paper's convergence measure (Sec. II.A.2):
+                                   rms over cells of L_h = lap_h phi - Sigma with
+                                   Sigma = largest root of the cell cubic (eq.
+                                   root) - 3, rhs = b + c; FP64, at exit; NaN
+                                   unless report_paper_eps = 1                  */
     double seconds;             /* wall time of the call                           */
     int n_history;              /* entries of history[] that are set               */
     double history[RECON_HISTORY_MAX]; /* relative residual after each cycle /

@@ -98,6 +98,10 @@ void set_fused_chunk(int c);
 
 // Message returned by recon_last_error(NULL) on this thread.
 void set_thread_error(const char *msg);
+// per-plane sums of L_h^2 (the paper's epsilon) over a whole N^3 grid, N
+// doubles into out (recon_slab.cu)
+cudaError_t paper_eps_planes(int N, double h, const double *theta, const double *g, double c, double *out,
+                             cudaStream_t s);
 
 // ---- multigrid launchers (recon_mg.cu); all asynchronous on `s`.
 template <typename T>

@@ -5,6 +5,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -54,6 +55,7 @@ recon_config default_config()
     c.mixed_df_residual = 1;
     c.fused_chunk = 0;
     c.adjoint_store_cofactors = 0;
+    c.report_paper_eps = 0;
     return c;
 }
 
@@ -288,7 +290,8 @@ recon_status recon_set_config(recon_handle *H, const recon_config *c)
     if (!(c->mixed_switch_rtol > 0.0) || c->mixed_fas_max_cycles < 0 || c->mixed_linear_vcycles < 1 ||
         (c->mixed_df_residual != 0 && c->mixed_df_residual != 1) ||
         (c->fused_chunk != 0 && (c->fused_chunk < 4 || c->fused_chunk > 128)) ||
-        (c->adjoint_store_cofactors != 0 && c->adjoint_store_cofactors != 1))
+        (c->adjoint_store_cofactors != 0 && c->adjoint_store_cofactors != 1) ||
+        (c->report_paper_eps != 0 && c->report_paper_eps != 1))
         return set_err(H, RECON_E_INVALID, "bad mixed-precision options");
     H->cfg = *c;
     return RECON_OK;
@@ -347,6 +350,20 @@ recon_status recon_solve(recon_handle *H, const double *b, double *phi, double t
     if (s != RECON_OK) return s;
     s = H->dtype == RECON_F64 ? solve_f64(H, b, phi, tol, max_cycles, stats)
                               : solve_mixed(H, b, phi, tol, max_cycles, stats);
+    if (stats) stats->paper_eps = std::nan("");
+    if (stats && H->cfg.report_paper_eps && (s == RECON_OK || s == RECON_E_NOCONV)) {
+        // per-plane sums of L_h^2 on the device, added here in plane order
+        const int N = H->N;
+        cudaError_t e = paper_eps_planes(N, H->L / N, phi, b, stats->compat_c, H->partials, H->stream);
+        std::vector<double> planes((size_t)N);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(H->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(planes.data(), H->partials, sizeof(double) * N, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_status(H, e, "paper_eps");
+        double acc = 0.0;
+        for (int i = 0; i < N; ++i) acc += planes[i];
+        stats->paper_eps = std::sqrt(acc / ((double)N * N * N));
+    }
     if (s == RECON_OK) {
         H->last_phi = phi;
         H->last_b = b;

@@ -303,6 +303,7 @@ recon_status recon_batch_solve(recon_batch *B, const double *const *b, double *c
             stats[i].outer_iterations = outer[i];
             stats[i].rel_residual = stats[i].n_history ? stats[i].history[stats[i].n_history - 1] : 0.0;
             stats[i].compat_c = h->hscal[recon::S_C];
+            stats[i].paper_eps = std::nan("");   // not evaluated by batched solves
         }
         if (conv[i]) {
             h->last_phi = phi[i];

@@ -272,6 +272,16 @@ recon_status bad(const char *what)
 }
 
 }  // namespace
+
+cudaError_t paper_eps_planes(int N, double h, const double *theta, const double *g, double c, double *out,
+                             cudaStream_t s)
+{
+    const Slab S{N, N, 0, 0, N};
+    note_launch(1);
+    k_slab_planes<2><<<N, kPlaneThreads, 0, s>>>(theta, g, c, 1.0 / (h * h), S, out);
+    return cudaGetLastError();
+}
+
 }  // namespace recon
 
 using namespace recon;

@@ -42,18 +42,19 @@ class recon_config(ctypes.Structure):
                 ("scale_floor", ctypes.c_double), ("mixed_switch_rtol", ctypes.c_double),
                 ("mixed_fas_max_cycles", ctypes.c_int), ("mixed_linear_vcycles", ctypes.c_int),
                 ("mixed_df_residual", ctypes.c_int), ("fused_chunk", ctypes.c_int),
-                ("adjoint_store_cofactors", ctypes.c_int)]
+                ("adjoint_store_cofactors", ctypes.c_int), ("report_paper_eps", ctypes.c_int)]
 
 
 class recon_stats(ctypes.Structure):
     _fields_ = [("cycles", ctypes.c_int), ("outer_iterations", ctypes.c_int),
                 ("rel_residual", ctypes.c_double), ("compat_c", ctypes.c_double),
+                ("paper_eps", ctypes.c_double),
                 ("seconds", ctypes.c_double), ("n_history", ctypes.c_int),
                 ("history", ctypes.c_double * HISTORY_MAX)]
 
     def as_dict(self):
         return dict(cycles=self.cycles, outer_iterations=self.outer_iterations,
-                    rel_residual=self.rel_residual, compat_c=self.compat_c,
+                    rel_residual=self.rel_residual, compat_c=self.compat_c, paper_eps=self.paper_eps,
                     seconds=self.seconds, history=list(self.history[:self.n_history]))
 
 

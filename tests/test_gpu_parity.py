@@ -530,3 +530,22 @@ def test_gaussianise_keeps_strict_order_above_2_24_cells(R, O):
     # the extreme ranks sit at |g| ~ 5.6 (p ~ 1.5e-8), where CUDA's
     # normcdfinv and scipy's ndtri differ by a few 1e-10
     assert np.max(np.abs(g - g_ref)) < 1e-9 * v.std()
+
+
+@pytest.mark.parametrize("dtype", ["f64", "mixed"])
+def test_paper_eps_matches_oracle(R, O, dtype):
+    """recon_stats.paper_eps (Sec. II.A.2's convergence measure, on request)
+    equals the oracle's epsilon of the same phi, b and c; NaN when not asked."""
+    N, L = 32, 100.0
+    b, _, _ = zeldovich_density(O, N, L, 0.5, 5.0, 1032)
+    s = R.Solver(N, L, R.RECON_F64 if dtype == "f64" else R.RECON_MIXED)
+    _, st0 = s.solve(dev(b), tol=1e-10, max_cycles=40)
+    assert np.isnan(st0["paper_eps"])
+    s.configure(report_paper_eps=1)
+    phi, st = s.solve(dev(b), tol=1e-10, max_cycles=40)
+    want = O.paper_eps(host(phi), b, st["compat_c"], L / N)
+    # L_h = (s - 3) - (root - 3) is a difference of O(1) numbers: rounding
+    # moves each cell's value by ~1e-15, against epsilon ~1e-11 here
+    assert st["paper_eps"] == pytest.approx(want, rel=1e-3, abs=1e-14)
+    assert 0.0 < st["paper_eps"] < 1e-8
+    s.close()
