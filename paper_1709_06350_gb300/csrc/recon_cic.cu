@@ -65,6 +65,45 @@ __device__ __forceinline__ bool cic_fixed(double u, int N, int &i0, unsigned lon
     return true;
 }
 
+// Cell and fraction of u = x 2^k - 1/2 when N/L = 2^k (k = pow2): x 2^k is
+// exact, so floor(u) and u - floor(u) follow from the bits of x in 64-bit
+// fixed point with no FP64 instruction.  The FP64 evaluation of u rounds
+// x 2^k - 1/2 only when it is not representable, i.e. for 0 < x 2^k < 1/4 by
+// less than 2^-53: the same cell, a fraction within 2^-53.  Returns false for
+// x < 0 and x 2^k >= 2^31 (the caller then uses the FP64 form).
+constexpr int kNoPow2 = -100000;
+__device__ __forceinline__ bool cic_fixed_pow2(double x, int k, int N, int &i0, unsigned long long &f)
+{
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    if (bits >> 63) return false;
+    const int e = (int)((bits >> 52) & 0x7ff);
+    if (e == 0) {              // +0 or subnormal: u = -1/2 (+ a subnormal)
+        i0 = N - 1;
+        f = 1ull << 63;
+        return true;
+    }
+    const int sh = 1075 - (e + k);   // fractional bits of the 53-bit m at the exponent of x 2^k
+    if (sh <= 22) return false;      // x 2^k >= 2^31
+    const unsigned long long m = (bits & 0xfffffffffffffull) | (1ull << 52);
+    unsigned long long ip, fr;
+    if (sh < 64) {
+        ip = m >> sh;
+        fr = (m & ((1ull << sh) - 1)) << (64 - sh);
+    } else {
+        ip = 0;
+        fr = sh - 64 < 64 ? m >> (sh - 64) : 0;
+    }
+    if (fr >= (1ull << 63)) {        // u = X - 1/2 keeps the integer part
+        f = fr - (1ull << 63);
+        i0 = (int)(ip < (unsigned long long)N ? ip : ip % (unsigned long long)N);
+    } else {                         // borrows one
+        f = fr + (1ull << 63);
+        const unsigned long long im = ip == 0 ? (unsigned long long)N - 1 : ip - 1;
+        i0 = (int)(im < (unsigned long long)N ? im : im % (unsigned long long)N);
+    }
+    return true;
+}
+
 // (a b) / 2^63 for 63-bit fixed-point weights a, b in [0, 2^63]
 __device__ __forceinline__ unsigned long long mul63(unsigned long long a, unsigned long long b)
 {
@@ -79,6 +118,17 @@ __device__ __forceinline__ double fixed63_to_double(unsigned long long w)
     const int lz = __clzll((long long)w);
     const unsigned long long mant = (w << lz) >> 11;   // 53 bits, leading one at bit 52
     return __longlong_as_double((long long)(((unsigned long long)(1023 - lz) << 52) |
+                                            (mant & 0xfffffffffffffull)));
+}
+
+// a 62-bit fixed-point value w (w / 2^62 in [0, 2]) as a double (truncated
+// to 53 bits)
+__device__ __forceinline__ double fixed62_to_double(unsigned long long w)
+{
+    if (w == 0) return 0.0;
+    const int lz = __clzll((long long)w);
+    const unsigned long long mant = (w << lz) >> 11;
+    return __longlong_as_double((long long)(((unsigned long long)(1024 - lz) << 52) |
                                             (mant & 0xfffffffffffffull)));
 }
 
@@ -112,21 +162,42 @@ __device__ __forceinline__ void zpair_add(V *__restrict__ acc, unsigned t0, unsi
     }
 }
 
+// The merge for unit mass on 63-bit fixed-point corner weights: the two
+// weights of a shared corner are added as integers (halved to 62 bits, so the
+// sum cannot overflow) and converted to double once.
+__device__ __forceinline__ void zpair_add_fixed(double *__restrict__ acc, unsigned t0, unsigned t1,
+                                                unsigned long long w0, unsigned long long w1, bool active)
+{
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned up_t1 = __shfl_up_sync(0xffffffffu, t1, 1);
+    const unsigned dn_t0 = __shfl_down_sync(0xffffffffu, t0, 1);
+    const unsigned long long a0 = w0 >> 1, a1 = w1 >> 1;
+    const unsigned long long up_a1 = __shfl_up_sync(0xffffffffu, a1, 1);
+    const bool take = lane > 0 && up_t1 == t0;
+    const bool give = lane < 31 && dn_t0 == t1;
+    if (active) {
+        atomicAdd(acc + t0, fixed62_to_double(take ? a0 + up_a1 : a0));
+        if (!give) atomicAdd(acc + t1, fixed62_to_double(a1));
+    }
+}
+
 // Deposit `val` with CIC weights at position (x, y, z) (inactive lanes take
 // part in the merge with no targets).  u is formed in FP64 with the two
 // roundings of the definition; the fraction, the corner weights
 // (w_x w_y) w_z and their conversion to double are 64-bit fixed point,
 // within ~1e-16 of the FP64 products.  val == 1 needs no multiply.
 __device__ __forceinline__ void cic_scatter(bool active, const double xyz[3], double val, int N,
-                                            double inv_h, double *__restrict__ rho)
+                                            double inv_h, int pow2, bool unit, double *__restrict__ rho)
 {
     int i0[3] = {0, 0, 0}, i1[3] = {0, 0, 0};
     unsigned long long w[3][2] = {{0, 0}, {0, 0}, {0, 0}};
     if (active)
         for (int d = 0; d < 3; ++d) {
-            const double u = __dsub_rn(__dmul_rn(xyz[d], inv_h), 0.5);
             unsigned long long f;
-            if (!cic_fixed(u, N, i0[d], f)) {   // far outside [0, L): the FP64 form
+            if (pow2 != kNoPow2 && cic_fixed_pow2(xyz[d], pow2, N, i0[d], f)) {
+                // N/L = 2^pow2: no FP64 instruction
+            } else if (!cic_fixed(__dsub_rn(__dmul_rn(xyz[d], inv_h), 0.5), N, i0[d], f)) {
+                // far outside [0, L): the FP64 form
                 double ff;
                 cic_axis(xyz[d], N, inv_h, i0[d], ff);
                 f = ff >= 1.0 ? ~0ull : (unsigned long long)ldexp(ff, 64);
@@ -135,30 +206,34 @@ __device__ __forceinline__ void cic_scatter(bool active, const double xyz[3], do
             w[d][1] = f >> 1;
             w[d][0] = (1ull << 63) - w[d][1];
         }
-    const bool unit = val == 1.0;
 #pragma unroll
     for (int a = 0; a < 2; ++a)
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
             const unsigned long long wab = mul63(w[0][a], w[1][b]);
             const unsigned row = offs(N, a ? i1[0] : i0[0], b ? i1[1] : i0[1], 0);
+            if (unit) {
+                zpair_add_fixed(rho, active ? row + i0[2] : kNoCell0, active ? row + i1[2] : kNoCell,
+                                mul63(wab, w[2][0]), mul63(wab, w[2][1]), active);
+                continue;
+            }
             const double c0 = fixed63_to_double(mul63(wab, w[2][0]));
             const double c1 = fixed63_to_double(mul63(wab, w[2][1]));
             zpair_add<double>(rho, active ? row + i0[2] : kNoCell0, active ? row + i1[2] : kNoCell,
-                              unit ? c0 : __dmul_rn(val, c0), unit ? c1 : __dmul_rn(val, c1), active);
+                              __dmul_rn(val, c0), __dmul_rn(val, c1), active);
         }
 }
 
 __global__ void __launch_bounds__(kThreads)
-k_cic_deposit(const double *__restrict__ pos, long long n, int N, double inv_h, double mass,
-              double *__restrict__ rho)
+k_cic_deposit(const double *__restrict__ pos, long long n, int N, double inv_h, int pow2, int unit,
+              double mass, double *__restrict__ rho)
 {
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = p < n;
     double xyz[3] = {0.0, 0.0, 0.0};
     if (active)
         for (int d = 0; d < 3; ++d) xyz[d] = pos[3 * p + d];
-    cic_scatter(active, xyz, mass, N, inv_h, rho);
+    cic_scatter(active, xyz, mass, N, inv_h, pow2, unit != 0, rho);
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -184,7 +259,14 @@ cudaError_t cic_deposit(const double *pos, long long n, int N, double L, double 
 {
     if (n == 0) return cudaSuccess;
     note_launch();
-    k_cic_deposit<<<blocks_for((size_t)n), kThreads, 0, s>>>(pos, n, N, (double)N / L, mass, rho);
+    // N/L a power of two (h = 1 in the benchmark's boxes): the cell
+    // coordinate in fixed point; unit mass: the corner merge in fixed point
+    const double inv_h = (double)N / L;
+    int e2 = 0;
+    const double m2 = std::frexp(inv_h, &e2);
+    const int pow2 = (m2 == 0.5 && e2 - 1 >= -60 && e2 - 1 <= 60) ? e2 - 1 : kNoPow2;
+    k_cic_deposit<<<blocks_for((size_t)n), kThreads, 0, s>>>(pos, n, N, inv_h, pow2, mass == 1.0 ? 1 : 0, mass,
+                                                            rho);
     return cudaGetLastError();
 }
 

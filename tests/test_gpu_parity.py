@@ -201,7 +201,7 @@ def test_cic_cells_bit_exact(R, O):
     assert np.array_equal(frac.cpu().numpy(), frac_ref)
 
 
-@pytest.mark.parametrize("N,L", [(32, 100.0), (48, 96.0)])
+@pytest.mark.parametrize("N,L", [(32, 100.0), (48, 96.0), (32, 32.0), (64, 128.0), (32, 8.0)])
 def test_cic_deposit_parity(R, O, N, L):
     from paper_1709_06350_gb300 import synth
     _, dh = synth.linear_field(N, L, 1.0, 78)
@@ -212,6 +212,16 @@ def test_cic_deposit_parity(R, O, N, L):
     got = host(rho)
     assert np.max(np.abs(got - ref)) < 1e-12 * ref.max()
     assert abs(got.sum() - N ** 3) < 1e-8
+    # particles at the edges of the box and of cells (N/L a power of two takes
+    # the fixed-point coordinate): x = 0, tiny, half a cell, just below a
+    # cell centre, L - ulp, L, and slightly negative (the FP64 form)
+    h = L / N
+    edge = np.array([0.0, 1e-300, 1e-17, 0.5 * h, 0.5 * h - 1e-13, h, 3.5 * h,
+                     np.nextafter(L, 0.0), L, -1e-12, -0.3 * h])
+    pe = np.stack(np.meshgrid(edge, edge[:4], edge[4:8], indexing="ij"), -1).reshape(-1, 3)
+    ref_e = O.cic_deposit(pe, N, L, mass=1.0)
+    got_e = host(s.deposit_cic(dev(pe), mass=1.0))
+    assert np.max(np.abs(got_e - ref_e)) < 1e-12 * max(ref_e.max(), 1.0)
     # empty input deposits nothing
     empty = s.deposit_cic(torch.zeros((0, 3), dtype=torch.float64, device="cuda"))
     assert host(empty).sum() == 0.0
