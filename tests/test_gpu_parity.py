@@ -300,10 +300,12 @@ def test_solve_domain_and_limits(R):
 
 
 # ------------------------------------------------------------------ output
-@pytest.mark.parametrize("N,L,sig,Rs,seed", [(32, 64.0, 0.8, 4.0, 41), (64, 64.0, 1.0, 2.0, 3000)])
+@pytest.mark.parametrize("N,L,sig,Rs,seed", [(32, 64.0, 0.8, 4.0, 41), (64, 64.0, 1.0, 2.0, 3000),
+                                              (32, 100.0, 0.8, 5.0, 42)])
 def test_displace_parity(R, O, N, L, sig, Rs, seed):
     """64^3 at sigma 1, R = 2 h^-1 Mpc: the bench recipe's resolution, with
-    cells down to b ~ 0.14 where v = 3 - tr((I+H)^-1) is most sensitive."""
+    cells down to b ~ 0.14 where v = 3 - tr((I+H)^-1) is most sensitive.
+    h = 2 and 1 scale psi by moving the exponent; h = 100/32 multiplies."""
     b, _, _ = zeldovich_density(O, N, L, sig, Rs, seed)
     t, _ = O.solve(b, L, tol=1e-11, max_cycles=40)
     psi_ref, dl_ref = O.displace(t, b, L)
