@@ -482,6 +482,7 @@ static cudaError_t fused_attr()
 
 static bool g_kernels_ready = false;
 static cudaError_t coarse_attrs();   // shared-memory limits of the coarsest solves
+static cudaError_t tail_attrs();     // and of the single-block V-cycle tails
 // planes per CTA of the fused sweeps for the solve being enqueued on this
 // host thread (recon_config.fused_chunk; 0 = by grid size)
 static thread_local int g_fused_chunk = 0;
@@ -494,6 +495,7 @@ cudaError_t prepare_kernels()
     if (e == cudaSuccess) e = fused_attr<float, true>();
     if (e == cudaSuccess) e = prepare_reg_sweeps();
     if (e == cudaSuccess) e = coarse_attrs();
+    if (e == cudaSuccess) e = tail_attrs();
     if (e == cudaSuccess) g_kernels_ready = true;
     return e;
 }
@@ -1645,6 +1647,399 @@ static cudaError_t coarse_attrs()
 
 
 // ======================================================================
+// The V-cycle below 16^3 in one thread block.  On a hierarchy level whose
+// grid has at most kMaxCoarseCells cells, the rest of the FAS V-cycle (and
+// of the linear one) runs in one CTA on shared memory: every level's arrays
+// are staged once, each step of the multi-kernel cycle is one block-wide
+// loop separated by barriers, and only the top level's solution goes back
+// to global memory.  The steps and their arithmetic are those of the grid
+// kernels (k_rb_pass / k_lin_pass, k_restrict_residual, k_coarse_rhs with
+// k_finalize_scale, k_form_rhs, k_prolong_add, the coarsest solves); the sums
+// of the means and the minimum of the scale factor are taken in another
+// order.  One launch replaces about a dozen per level, which on small grids
+// are each a few microseconds of launch latency.
+// ======================================================================
+constexpr int kTailMaxLevels = 8;
+
+template <typename T>
+struct TailFas {
+    int nl;                          // levels in the tail (>= 2)
+    int N[kTailMaxLevels];
+    T ih2[kTailMaxLevels], h2_6[kTailMaxLevels];
+    T *t;                            // top level: theta (in/out) and g (global)
+    const T *g;
+    const double *cptr;              // c of the top level (coarser levels: 0)
+    int nu1, nu2, rule, cmax;
+    double floor_, crtol;
+};
+
+struct TailLin {
+    int nl;
+    int N[kTailMaxLevels];
+    float ih2[kTailMaxLevels];
+    float *e;                        // top level: e (in/out) and f (global)
+    const float *f;
+    const float *cof[kTailMaxLevels];  // every level's six colour-split cofactor arrays
+    int nu1, nu2, cmax;
+    double crtol;
+};
+
+// snapshot red-black sweeps of eq. update on a shared-memory grid (t -> w -> t)
+template <typename T, int NT>
+__device__ void tail_sweeps(T *t, T *w, const T *g, T c, int N, T ih2, T h2_6, int rule, int sweeps)
+{
+    const int half = N >> 1, npairs = N * N * half;
+    for (int it = 0; it < sweeps; ++it)
+        for (int colour = 0; colour < 2; ++colour) {
+            const T *src = colour == 0 ? t : w;
+            T *dst = colour == 0 ? w : t;
+            for (int pi = threadIdx.x; pi < npairs; pi += NT) {
+                const int m = pi % half, r = pi / half;
+                const int j = r % N, i = r / N;
+                const int par = (colour + i + j) & 1;
+                const int ka = 2 * m + par, kb = 2 * m + 1 - par;
+                const Nb19<T> nb = load19<T>(src, N, i, j, ka);
+                T s, p, q;
+                cubic_coeffs(nb, ih2, g[offs(N, i, j, ka)] + c, s, p, q);
+                dst[offs(N, i, j, ka)] = point_update(nb.c, h2_6, s, p, q, rule);
+                dst[offs(N, i, j, kb)] = src[offs(N, i, j, kb)];
+            }
+            __syncthreads();
+        }
+}
+
+// fine += scale P(cn - co) on shared-memory grids (co may be null), the
+// separable form of k_prolong_add
+template <typename T, int NT>
+__device__ void tail_prolong(const T *cn, const T *co, int Nc, T s, T *fine)
+{
+    const int Nf = 2 * Nc, ncc = Nc * Nc * Nc;
+    const T w0 = T(0.75), w1 = T(0.25);
+    for (int id = threadIdx.x; id < ncc; id += NT) {
+        const int K = id % Nc, J = (id / Nc) % Nc, I = id / (Nc * Nc);
+        const int Ip[3] = {I == 0 ? Nc - 1 : I - 1, I, I + 1 == Nc ? 0 : I + 1};
+        const int Jp[3] = {J == 0 ? Nc - 1 : J - 1, J, J + 1 == Nc ? 0 : J + 1};
+        const int Kp[3] = {K == 0 ? Nc - 1 : K - 1, K, K + 1 == Nc ? 0 : K + 1};
+        T d[3][3][3];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+                for (int c = 0; c < 3; ++c) {
+                    const unsigned o = offs(Nc, Ip[a], Jp[b], Kp[c]);
+                    d[a][b][c] = co ? cn[o] - co[o] : cn[o];
+                }
+        for (int ei = 0; ei < 2; ++ei) {
+            T u[3][3];
+            for (int b = 0; b < 3; ++b)
+                for (int c = 0; c < 3; ++c) u[b][c] = w0 * d[1][b][c] + w1 * d[ei ? 2 : 0][b][c];
+            for (int ej = 0; ej < 2; ++ej) {
+                T v[3];
+                for (int c = 0; c < 3; ++c) v[c] = w0 * u[1][c] + w1 * u[ej ? 2 : 0][c];
+                const unsigned f = offs(Nf, 2 * I + ei, 2 * J + ej, 2 * K);
+                fine[f] += s * (w0 * v[1] + w1 * v[0]);
+                fine[f + 1] += s * (w0 * v[1] + w1 * v[2]);
+            }
+        }
+    }
+    __syncthreads();
+}
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_fas_tail(TailFas<T> A)
+{
+    extern __shared__ __align__(16) unsigned char tail_smem[];
+    __shared__ double sh[32];
+    __shared__ double sval;
+    __shared__ double spscale[kTailMaxLevels];
+    T *tl[kTailMaxLevels], *gl[kTailMaxLevels], *ol[kTailMaxLevels], *wl[kTailMaxLevels];
+    {
+        T *p = reinterpret_cast<T *>(tail_smem);
+        for (int l = 0; l < A.nl; ++l) {
+            const int n = A.N[l] * A.N[l] * A.N[l];
+            tl[l] = p;
+            gl[l] = p + n;
+            ol[l] = p + 2 * n;
+            wl[l] = p + 3 * n;
+            p += 4 * n;
+        }
+    }
+    const int n0 = A.N[0] * A.N[0] * A.N[0];
+    for (int id = threadIdx.x; id < n0; id += NT) {
+        tl[0][id] = A.t[id];
+        gl[0][id] = A.g[id];
+    }
+    __syncthreads();
+    const T c0 = (T)(*A.cptr);
+    // down: pre-smoothing, residual + restriction, the coarse right side
+    for (int l = 0; l + 1 < A.nl; ++l) {
+        const T c = l == 0 ? c0 : T(0);
+        const int N = A.N[l], Nc = A.N[l + 1], nc = Nc * Nc * Nc;
+        tail_sweeps<T, NT>(tl[l], wl[l], gl[l], c, N, A.ih2[l], A.h2_6[l], A.rule, A.nu1);
+        double sr = 0.0;
+        for (int id = threadIdx.x; id < nc; id += NT) {
+            const int K = id % Nc, J = (id / Nc) % Nc, I = id / (Nc * Nc);
+            T at = T(0), ar = T(0);
+            for (int a = 0; a < 2; ++a)
+                for (int b = 0; b < 2; ++b)
+                    for (int cc = 0; cc < 2; ++cc) {
+                        const int i = 2 * I + a, j = 2 * J + b, k = 2 * K + cc;
+                        const Nb19<T> nb = load19<T>(tl[l], N, i, j, k);
+                        at += nb.c;
+                        ar += (gl[l][offs(N, i, j, k)] + c) - det_IH(nb, A.ih2[l]);
+                    }
+            const T vt = at * T(0.125), vr = ar * T(0.125);
+            tl[l + 1][id] = vt;
+            ol[l + 1][id] = vt;
+            gl[l + 1][id] = vr;
+            sr += (double)vr;
+        }
+        double tot = block_sum<NT>(sr, sh);
+        if (ltid() == 0) sval = tot / nc;
+        __syncthreads();
+        const T m = (T)sval;
+        const T fl = (T)A.floor_;
+        T mn = T(INFINITY);
+        for (int id = threadIdx.x; id < nc; id += NT) {
+            const int K = id % Nc, J = (id / Nc) % Nc, I = id / (Nc * Nc);
+            const T rr = gl[l + 1][id] - m;
+            const T d = det_IH(load19<T>(tl[l + 1], Nc, I, J, K), A.ih2[l + 1]);
+            gl[l + 1][id] = rr;
+            wl[l + 1][id] = d;
+            if (rr < T(0)) {
+                const T cand = fl * (d > T(0) ? d : T(0)) / (-rr);
+                mn = cand < mn ? cand : mn;
+            }
+        }
+        const double v = block_min<NT>((double)mn, sh);
+        if (ltid() == 0) {
+            double sc = A.floor_ <= 0.0 ? 1.0 : fmin(1.0, v);
+            if (sc < 1e-3) sc = 0.0;
+            sval = sc;
+            spscale[l + 1] = sc > 0.0 ? 1.0 / sc : 0.0;
+        }
+        __syncthreads();
+        const T sc = (T)sval;
+        for (int id = threadIdx.x; id < nc; id += NT) gl[l + 1][id] = wl[l + 1][id] + sc * gl[l + 1][id];
+        __syncthreads();
+    }
+    // bottom: the coarsest-grid solve (c = 0 below the top level)
+    {
+        const int lc = A.nl - 1, N = A.N[lc], half = N >> 1, npairs = N * N * half;
+        T *ts = tl[lc], *ws = wl[lc];
+        const T *gs = gl[lc];
+        const double r0 = coarse_proj_rms<T, NT>(ts, ws, gs, T(0), N, A.ih2[lc], sh, &sval);
+        double prev = r0;
+        for (int sw = 0; sw < A.cmax; ++sw) {
+            for (int colour = 0; colour < 2; ++colour) {
+                const T *src = colour == 0 ? ts : ws;
+                T *dst = colour == 0 ? ws : ts;
+                for (int pi = threadIdx.x; pi < npairs; pi += NT) {
+                    const int m = pi % half, r = pi / half;
+                    const int j = r % N, i = r / N;
+                    const int par = (colour + i + j) & 1;
+                    const int ka = 2 * m + par, kb = 2 * m + 1 - par;
+                    const Nb19<T> nb = load19<T>(src, N, i, j, ka);
+                    T s, p, q;
+                    cubic_coeffs(nb, A.ih2[lc], gs[offs(N, i, j, ka)], s, p, q);
+                    dst[offs(N, i, j, ka)] = point_update(nb.c, A.h2_6[lc], s, p, q, A.rule);
+                    dst[offs(N, i, j, kb)] = src[offs(N, i, j, kb)];
+                }
+                __syncthreads();
+            }
+            const double cur = coarse_proj_rms<T, NT>(ts, ws, gs, T(0), N, A.ih2[lc], sh, &sval);
+            if (cur <= A.crtol * r0) break;
+            if (A.crtol > 0.0 && cur >= prev) break;
+            prev = cur;
+        }
+    }
+    // up: the corrections and post-smoothing
+    for (int l = A.nl - 2; l >= 0; --l) {
+        const double ps = spscale[l + 1];
+        if (ps != 0.0) tail_prolong<T, NT>(tl[l + 1], ol[l + 1], A.N[l + 1], (T)ps, tl[l]);
+        tail_sweeps<T, NT>(tl[l], wl[l], gl[l], l == 0 ? c0 : T(0), A.N[l], A.ih2[l], A.h2_6[l], A.rule,
+                           A.nu2);
+    }
+    for (int id = threadIdx.x; id < n0; id += NT) A.t[id] = tl[0][id];
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) k_lin_tail(TailLin A)
+{
+    extern __shared__ __align__(16) unsigned char tail_smem[];
+    __shared__ double sh[32];
+    __shared__ double sval;
+    float *el[kTailMaxLevels], *fl[kTailMaxLevels], *cl[kTailMaxLevels], *wl[kTailMaxLevels];
+    int nl_[kTailMaxLevels];
+    {
+        float *p = reinterpret_cast<float *>(tail_smem);
+        for (int l = 0; l < A.nl; ++l) {
+            const int n = A.N[l] * A.N[l] * A.N[l];
+            nl_[l] = n;
+            el[l] = p;
+            fl[l] = p + n;
+            wl[l] = p + 2 * n;
+            cl[l] = p + 3 * n;
+            p += 9 * n;
+        }
+    }
+    for (int l = 0; l < A.nl; ++l)
+        for (int id = threadIdx.x; id < 6 * nl_[l]; id += NT) cl[l][id] = A.cof[l][id];
+    for (int id = threadIdx.x; id < nl_[0]; id += NT) {
+        el[0][id] = A.e[id];
+        fl[0][id] = A.f[id];
+    }
+    __syncthreads();
+    auto sweeps = [&](int l, int count) {
+        const int N = A.N[l], half = N >> 1, npairs = N * N * half;
+        const size_t n = (size_t)nl_[l];
+        for (int it = 0; it < count; ++it)
+            for (int colour = 0; colour < 2; ++colour) {
+                const float *src = colour == 0 ? el[l] : wl[l];
+                float *dst = colour == 0 ? wl[l] : el[l];
+                for (int pi = threadIdx.x; pi < npairs; pi += NT) {
+                    const int m = pi % half, r = pi / half;
+                    const int j = r % N, i = r / N;
+                    const int par = (colour + i + j) & 1;
+                    const int ka = 2 * m + par, kb = 2 * m + 1 - par;
+                    const Cof<float> a = cof_at(cl[l], n, cof_slot(N, i, j, ka));
+                    const Nb19<float> ev = load19<float>(src, N, i, j, ka);
+                    const float Je = jac_apply(a, ev, A.ih2[l]);
+                    const float diag = -2.0f * (a.xx + a.yy + a.zz) * A.ih2[l];
+                    dst[offs(N, i, j, ka)] = ev.c + (fl[l][offs(N, i, j, ka)] - Je) / diag;
+                    dst[offs(N, i, j, kb)] = src[offs(N, i, j, kb)];
+                }
+                __syncthreads();
+            }
+    };
+    for (int l = 0; l + 1 < A.nl; ++l) {
+        const int N = A.N[l], Nc = A.N[l + 1], nc = Nc * Nc * Nc;
+        const size_t nf = (size_t)nl_[l];
+        sweeps(l, A.nu1);
+        double sr = 0.0;
+        for (int id = threadIdx.x; id < nc; id += NT) {
+            const int K = id % Nc, J = (id / Nc) % Nc, I = id / (Nc * Nc);
+            float acc = 0.0f;
+            for (int a = 0; a < 2; ++a)
+                for (int b = 0; b < 2; ++b)
+                    for (int cc = 0; cc < 2; ++cc) {
+                        const int i = 2 * I + a, j = 2 * J + b, k = 2 * K + cc;
+                        const Cof<float> C = cof_at(cl[l], nf, cof_slot(N, i, j, k));
+                        acc += fl[l][offs(N, i, j, k)] - jac_apply(C, load19<float>(el[l], N, i, j, k), A.ih2[l]);
+                    }
+            const float v = acc * 0.125f;
+            fl[l + 1][id] = v;
+            el[l + 1][id] = 0.0f;
+            sr += (double)v;
+        }
+        const double tot = block_sum<NT>(sr, sh);
+        if (ltid() == 0) sval = tot / nc;
+        __syncthreads();
+        const float m = (float)sval;
+        for (int id = threadIdx.x; id < nc; id += NT) fl[l + 1][id] -= m;
+        __syncthreads();
+    }
+    {   // the coarsest grid
+        const int lc = A.nl - 1, N = A.N[lc], n = nl_[lc], half = N >> 1, npairs = N * N * half;
+        const size_t ncof = (size_t)n;
+        float *es = el[lc], *ws = wl[lc], *fs = fl[lc], *cs = cl[lc];
+        auto proj_rms = [&]() -> double {
+            double sr = 0.0;
+            for (int id = threadIdx.x; id < n; id += NT) {
+                const int k = id % N, j = (id / N) % N, i = id / (N * N);
+                const float r = fs[id] - jac_apply(cof_at(cs, ncof, cof_slot(N, i, j, k)),
+                                                   load19<float>(es, N, i, j, k), A.ih2[lc]);
+                ws[id] = r;
+                sr += (double)r;
+            }
+            double tt = block_sum<NT>(sr, sh);
+            if (ltid() == 0) sval = tt / n;
+            __syncthreads();
+            const double mm = sval;
+            double s2 = 0.0;
+            for (int id = threadIdx.x; id < n; id += NT) {
+                const double d = (double)ws[id] - mm;
+                s2 += d * d;
+            }
+            tt = block_sum<NT>(s2, sh);
+            if (ltid() == 0) sval = sqrt(tt / n);
+            __syncthreads();
+            const double vv = sval;
+            __syncthreads();
+            return vv;
+        };
+        const double r0 = proj_rms();
+        double prev = r0;
+        for (int sw = 0; sw < A.cmax; ++sw) {
+            for (int colour = 0; colour < 2; ++colour) {
+                const float *src = colour == 0 ? es : ws;
+                float *dst = colour == 0 ? ws : es;
+                for (int pi = threadIdx.x; pi < npairs; pi += NT) {
+                    const int m = pi % half, r = pi / half;
+                    const int j = r % N, i = r / N;
+                    const int par = (colour + i + j) & 1;
+                    const int ka = 2 * m + par, kb = 2 * m + 1 - par;
+                    const Cof<float> a = cof_at(cs, ncof, cof_slot(N, i, j, ka));
+                    const Nb19<float> ev = load19<float>(src, N, i, j, ka);
+                    const float Je = jac_apply(a, ev, A.ih2[lc]);
+                    const float diag = -2.0f * (a.xx + a.yy + a.zz) * A.ih2[lc];
+                    dst[offs(N, i, j, ka)] = ev.c + (fs[offs(N, i, j, ka)] - Je) / diag;
+                    dst[offs(N, i, j, kb)] = src[offs(N, i, j, kb)];
+                }
+                __syncthreads();
+            }
+            const double cur = proj_rms();
+            if (cur <= A.crtol * r0) break;
+            if (A.crtol > 0.0 && cur >= prev) break;
+            prev = cur;
+        }
+    }
+    for (int l = A.nl - 2; l >= 0; --l) {
+        tail_prolong<float, NT>(el[l + 1], nullptr, A.N[l + 1], 1.0f, el[l]);
+        sweeps(l, A.nu2);
+    }
+    for (int id = threadIdx.x; id < nl_[0]; id += NT) A.e[id] = el[0][id];
+}
+
+// shared memory of the tails: FAS 4 arrays per level, linear 9
+template <typename T>
+static size_t tail_fas_smem(const int *Nl, int nl)
+{
+    size_t c = 0;
+    for (int l = 0; l < nl; ++l) c += 4 * (size_t)Nl[l] * Nl[l] * Nl[l];
+    return c * sizeof(T);
+}
+static size_t tail_lin_smem(const int *Nl, int nl)
+{
+    size_t c = 0;
+    for (int l = 0; l < nl; ++l) c += 9 * (size_t)Nl[l] * Nl[l] * Nl[l];
+    return c * sizeof(float);
+}
+// the most any tail can need: a top level of kMaxCoarseCells cells, each
+// level below an eighth of the one above
+constexpr size_t kTailCells = kMaxCoarseCells + kMaxCoarseCells / 7 + 1;
+
+static cudaError_t tail_attrs()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_fas_tail<float, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(4 * kTailCells * sizeof(float)));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fas_tail<float, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(4 * kTailCells * sizeof(float)));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fas_tail<double, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(4 * kTailCells * sizeof(double)));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fas_tail<double, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(4 * kTailCells * sizeof(double)));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_lin_tail<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(9 * kTailCells * sizeof(float)));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_lin_tail<512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(9 * kTailCells * sizeof(float)));
+    return e;
+}
+
+// ======================================================================
 // drivers
 // ======================================================================
 namespace {
@@ -1672,6 +2067,42 @@ inline size_t ncell(int N) { return (size_t)N * N * N; }
         if (e_ != cudaSuccess) return e_;                                          \
     } while (0)
 
+// The rest of the FAS V-cycle from level l (at most kMaxCoarseCells cells)
+// in one thread block.
+template <typename T>
+cudaError_t fas_tail(recon_handle *H, const Hier<T> &Y, int l, const double *cptr)
+{
+    const recon_config &cf = H->cfg;
+    TailFas<T> A{};
+    A.nl = H->nlev - l;
+    for (int q = 0; q < A.nl; ++q) {
+        A.N[q] = H->Nl[l + q];
+        const double h = H->hl[l + q];
+        A.ih2[q] = (T)(1.0 / (h * h));
+        A.h2_6[q] = (T)(h * h / 6.0);
+    }
+    A.t = Y.t[l];
+    A.g = Y.g[l];
+    A.cptr = cptr;
+    A.nu1 = cf.nu1;
+    A.nu2 = cf.nu2;
+    A.rule = cf.rule;
+    A.cmax = cf.coarse_max_sweeps;
+    A.floor_ = cf.scale_floor;
+    A.crtol = cf.coarse_rtol;
+    if (!g_kernels_ready) {
+        const cudaError_t e = prepare_kernels();
+        if (e != cudaSuccess) return e;
+    }
+    const size_t smem = tail_fas_smem<T>(A.N, A.nl);
+    note_launch();
+    if (ncell(A.N[0]) / 2 <= 1024)
+        k_fas_tail<T, 256><<<1, 256, smem, H->stream>>>(A);
+    else
+        k_fas_tail<T, 512><<<1, 512, smem, H->stream>>>(A);
+    return cudaGetLastError();
+}
+
 // FAS V-cycle from level l (Sec. II.A.3).
 template <typename T>
 cudaError_t vcycle(recon_handle *H, const Hier<T> &Y, int l, const double *cptr)
@@ -1681,6 +2112,8 @@ cudaError_t vcycle(recon_handle *H, const Hier<T> &Y, int l, const double *cptr)
     set_fused_chunk(cf.fused_chunk);
     const int N = H->Nl[l];
     const double h = H->hl[l];
+    if (l < H->nlev - 1 && ncell(N) <= (size_t)kMaxCoarseCells && H->nlev - l <= kTailMaxLevels)
+        return fas_tail<T>(H, Y, l, cptr);
     if (l == H->nlev - 1)
         return coarse_solve<T>(N, h, cf.rule, Y.t[l], Y.g[l], cptr, 0.0, cf.coarse_max_sweeps,
                                cf.coarse_rtol, Y.work, nullptr, s);
@@ -1870,6 +2303,35 @@ cudaError_t lin_vcycle(recon_handle *H, int l)
     const int N = H->Nl[l];
     const double h = H->hl[l];
     const float ih2 = (float)(1.0 / (h * h));
+    if (l < H->nlev - 1 && ncell(N) <= (size_t)kMaxCoarseCells && H->nlev - l <= kTailMaxLevels &&
+        H->cof32[l]) {
+        // the rest of the linear V-cycle in one thread block
+        TailLin A{};
+        A.nl = H->nlev - l;
+        for (int q = 0; q < A.nl; ++q) {
+            A.N[q] = H->Nl[l + q];
+            const double hq = H->hl[l + q];
+            A.ih2[q] = (float)(1.0 / (hq * hq));
+            A.cof[q] = H->cof32[l + q];
+        }
+        A.e = H->e32[l];
+        A.f = H->f32[l];
+        A.nu1 = cf.nu1;
+        A.nu2 = cf.nu2;
+        A.cmax = cf.coarse_max_sweeps;
+        A.crtol = cf.coarse_rtol;
+        if (!g_kernels_ready) {
+            const cudaError_t e = prepare_kernels();
+            if (e != cudaSuccess) return e;
+        }
+        const size_t smem = tail_lin_smem(A.N, A.nl);
+        note_launch();
+        if (ncell(A.N[0]) / 2 <= 1024)
+            k_lin_tail<256><<<1, 256, smem, s>>>(A);
+        else
+            k_lin_tail<512><<<1, 512, smem, s>>>(A);
+        return cudaGetLastError();
+    }
     if (l == H->nlev - 1) {
         note_launch();
         const size_t smem = 9 * sizeof(float) * ncell(N);
