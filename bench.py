@@ -667,6 +667,19 @@ def bench_cubic(recon, synth, torch, dev, tol=1e-3):
                      "rel_residual": st["rel_residual"], "lap_centre": float(lap.mean()),
                      "lap_expected": expect,
                      "hbar_max_rel": max(float((H[a] - lap / 3).abs().max()) for a in range(3)) / expect}
+        if dtype == recon.RECON_F64:
+            # the scaled-defect factor of every coarse level, cycle by cycle
+            # (the nested-iteration start and one cycle, then resumed cycles)
+            trace, rel = [], []
+            phi.zero_()
+            s.configure(start=0)
+            for k in range(12):
+                _, stk = s.solve(b, phi=phi, tol=1e-30, max_cycles=1, raise_on_noconv=False)
+                trace.append(s.level_scales())
+                rel.append(stk["rel_residual"])
+                s.configure(start=1)
+            out[name]["level_scale_trace"] = {"levels": [N >> (l + 1) for l in range(len(trace[0]))],
+                                              "s_per_cycle": trace, "rel_residual_per_cycle": rel}
         s.close()
     return out
 

@@ -256,6 +256,16 @@ recon_status recon_displace_adjoint(recon_handle *h, const double *phi, const do
  * RECON_E_CUDA. */
 recon_status recon_smooth_density(recon_handle *h, const double *rho, double R, double floor, double *b);
 
+/* The scaled-defect factor s of each coarse level in the last FAS V-cycle
+ * the handle ran (Sec. II.A.3, the coarse right side det_H(R phi) + s R r
+ * with the correction divided by s): out[l - 1] for level l = 1 .. L - 1
+ * (level 0 the finest grid, L the number of levels), at most n values; 1 =
+ * no scaling, 0 = the coarse correction was skipped.  For RECON_MIXED the
+ * factors of the last FP32 FAS cycle.  Synchronizes the handle's stream.
+ * *levels (nullable) receives L - 1.
+ * Errors: RECON_E_INVALID (null handle or out with n > 0), RECON_E_CUDA. */
+recon_status recon_level_scales(recon_handle *h, double *out, int n, int *levels);
+
 /* 1-point Gaussianisation of an N^3 field (Sec. III: tried on delta_r),
  * read as the rank mapping
  *     out_i = mean + std * Phi^-1((rank_i + 1/2) / N^3),

@@ -394,6 +394,20 @@ recon_status recon_smooth_density(recon_handle *H, const double *rho, double R, 
                        "smooth_density");
 }
 
+recon_status recon_level_scales(recon_handle *H, double *out, int n, int *levels)
+{
+    if (!H || (n > 0 && !out)) return RECON_E_INVALID;
+    const int coarse = H->nlev - 1;
+    if (levels) *levels = coarse;
+    if (n <= 0 || coarse <= 0) return RECON_OK;
+    std::vector<double> scal(recon::S_COUNT);
+    cudaError_t e = cudaStreamSynchronize(H->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(scal.data(), H->scal, sizeof(double) * recon::S_COUNT, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_status(H, e, "recon_level_scales");
+    for (int l = 1; l <= coarse && l <= n; ++l) out[l - 1] = scal[recon::slot_scale(l)];
+    return RECON_OK;
+}
+
 recon_status recon_gaussianise(recon_handle *H, const double *field, double *out)
 {
     if (!H) return RECON_E_INVALID;

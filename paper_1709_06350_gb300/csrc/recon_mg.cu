@@ -1669,6 +1669,8 @@ struct TailFas {
     T *t;                            // top level: theta (in/out) and g (global)
     const T *g;
     const double *cptr;              // c of the top level (coarser levels: 0)
+    double *scal;                    // the handle's device scalars: the per-level
+    int l0;                          // slots of levels l0 + 1 .. are written
     int nu1, nu2, rule, cmax;
     double floor_, crtol;
 };
@@ -1793,7 +1795,10 @@ __global__ void __launch_bounds__(NT) k_fas_tail(TailFas<T> A)
             sr += (double)vr;
         }
         double tot = block_sum<NT>(sr, sh);
-        if (ltid() == 0) sval = tot / nc;
+        if (ltid() == 0) {
+            sval = tot / nc;
+            A.scal[slot_rmean(A.l0 + l + 1)] = sval;
+        }
         __syncthreads();
         const T m = (T)sval;
         const T fl = (T)A.floor_;
@@ -1815,6 +1820,8 @@ __global__ void __launch_bounds__(NT) k_fas_tail(TailFas<T> A)
             if (sc < 1e-3) sc = 0.0;
             sval = sc;
             spscale[l + 1] = sc > 0.0 ? 1.0 / sc : 0.0;
+            A.scal[slot_scale(A.l0 + l + 1)] = sc;
+            A.scal[slot_pscale(A.l0 + l + 1)] = spscale[l + 1];
         }
         __syncthreads();
         const T sc = (T)sval;
@@ -2084,6 +2091,8 @@ cudaError_t fas_tail(recon_handle *H, const Hier<T> &Y, int l, const double *cpt
     A.t = Y.t[l];
     A.g = Y.g[l];
     A.cptr = cptr;
+    A.scal = H->scal;
+    A.l0 = l;
     A.nu1 = cf.nu1;
     A.nu2 = cf.nu2;
     A.rule = cf.rule;

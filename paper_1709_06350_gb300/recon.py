@@ -81,6 +81,7 @@ _SIGS = {
     "recon_displace_fp64": (_I, [_P, _P, _P, _P, _P]),
     "recon_displace_adjoint": (_I, [_P, _P, _P, _P, _P, _P, _P]),
     "recon_gaussianise": (_I, [_P, _P, _P]),
+    "recon_level_scales": (_I, [_P, _P, _I, ctypes.POINTER(_I)]),
     "recon_smooth_density": (_I, [_P, _P, _D, _D, _P]),
     "recon_last_error": (ctypes.c_char_p, [_P]),
     "recon_status_string": (ctypes.c_char_p, [_I]),
@@ -269,6 +270,15 @@ def recon_smooth_density(h, N: int, rho, R: float, floor: float, b) -> None:
                                        _dev_ptr(b, torch.float64, N ** 3)), h)
 
 
+def recon_level_scales(h, n: int = 16) -> list:
+    """The scaled-defect factor of each coarse level in the handle's last FAS
+    V-cycle (level 1 first)."""
+    out = (ctypes.c_double * max(n, 1))()
+    levels = ctypes.c_int(0)
+    _check(load().recon_level_scales(h, out, int(n), ctypes.byref(levels)), h)
+    return [out[i] for i in range(min(n, levels.value))]
+
+
 def recon_gaussianise(h, N: int, field, out) -> None:
     import torch
     _check(load().recon_gaussianise(h, _dev_ptr(field, torch.float64, N ** 3),
@@ -455,6 +465,10 @@ class Solver:
             phi = torch.zeros_like(b)
         _, stats = recon_solve(self.h, self.N, b, phi, tol, max_cycles, raise_on_noconv)
         return phi, stats
+
+    def level_scales(self):
+        """Scaled-defect factor of each coarse level in the last FAS V-cycle."""
+        return recon_level_scales(self.h)
 
     def displace(self, phi, b, psi=None, dl=None):
         """psi, dl: optional outputs (CUDA tensors or pinned CPU tensors)."""

@@ -561,3 +561,27 @@ def test_paper_eps_matches_oracle(R, O, dtype):
     assert st["paper_eps"] == pytest.approx(want, rel=1e-3, abs=1e-14)
     assert 0.0 < st["paper_eps"] < 1e-8
     s.close()
+
+
+def test_level_scales(R, O):
+    """recon_level_scales: one factor per coarse level; a mild field never
+    scales the coarse right side (s = 1), the cubic test's first cycle does
+    (the oracle's V-cycle on the same 64^3 problem gives s ~ 0.5-0.9 on the
+    finest coarse level in its first cycles)."""
+    from paper_1709_06350_gb300 import synth
+    N, L = 32, 64.0
+    b = smooth_density(N, 90, 0.3)
+    s = R.Solver(N, L)
+    s.solve(dev(b), tol=1e-10, max_cycles=30)
+    sc = s.level_scales()
+    assert len(sc) == O.num_levels(N) - 1 and all(x == 1.0 for x in sc)
+    s.close()
+    N, Lb = 64, 64.0
+    s = R.Solver(N, Lb)
+    rho = s.deposit_cic(dev(synth.cube_positions(N, Lb, Lb * 10 / 128)))
+    bc = s.smooth_density(rho, 0.0)
+    s.solve(bc, tol=1e-30, max_cycles=1, raise_on_noconv=False)
+    sc = s.level_scales()
+    assert len(sc) == O.num_levels(N) - 1
+    assert 0.0 <= min(sc) < 1.0 and max(sc) <= 1.0
+    s.close()
