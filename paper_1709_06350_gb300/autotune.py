@@ -124,8 +124,14 @@ def tune(N: int, L: float | None = None, dtype: int = recon.RECON_MIXED, tol: fl
         return t, st["rel_residual"] < tol
 
     m = measure(defaults)
-    default_t = m[0] if m is not None else float("inf")
+    default_t = m[0] if m is not None and m[1] else float("inf")
+    # start from the cached schedule or the defaults, whichever is faster now
+    # (kernels change: a schedule tuned for older ones can fall behind)
     start = cached_config(N, dtype, path) or defaults
+    if start != defaults:
+        mc = measure(start)
+        if mc is None or not mc[1] or mc[0] > default_t:
+            start = defaults
     try:
         best_cfg, best_t, n = descend(measure, start, SPACE, rounds, verbose)
     except ValueError:   # a cached schedule that no longer converges
