@@ -90,9 +90,12 @@ bool reg_sweep_ok(int N, const float *src, const float *dst, const float *g, con
 int reg_sweep_chunk(int N, int want);
 // one sweep src -> dst; lin: J e = f with theta th (else the FAS cubic with
 // right side g + c, c from cptr or cval); chunk: planes per CTA (0 = by size)
+// gshift (FAS, nullable): device scalar subtracted from every value the sweep
+// stores (a gauge shift folded into the sweep: the update depends only on
+// differences of theta)
 cudaError_t reg_sweep_launch(bool lin, int N, const float *src, float *dst, const float *g, const float *th,
                              const double *cptr, double cval, float ih2, float h2_6, int rule, int chunk,
-                             cudaStream_t s);
+                             cudaStream_t s, const double *gshift = nullptr);
 // Planes per CTA of the fused sweeps enqueued next on this host thread (0 = auto).
 void set_fused_chunk(int c);
 
@@ -104,9 +107,11 @@ cudaError_t paper_eps_planes(int N, double h, const double *theta, const double 
                              cudaStream_t s);
 
 // ---- multigrid launchers (recon_mg.cu); all asynchronous on `s`.
+// gshift (nullable): a device scalar subtracted from theta before the first
+// sweep (folded into it where the register-blocked kernel runs)
 template <typename T>
 cudaError_t sweep(int N, double h, int rule, T *t, const T *g, const double *cptr,
-                  double cval, int sweeps, T *work, cudaStream_t s);
+                  double cval, int sweeps, T *work, cudaStream_t s, const double *gshift = nullptr);
 cudaError_t residual_write(int N, double h, const double *t, const double *g,
                            const double *cptr, double cval, double *r, cudaStream_t s);
 cudaError_t det_write(int N, double h, const double *t, double *out, cudaStream_t s);

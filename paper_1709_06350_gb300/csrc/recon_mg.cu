@@ -38,6 +38,16 @@ static inline unsigned red_blocks(size_t work, int threads = kThreads)
 // smoother: one colour pass; a thread handles the cell pair (2m, 2m+1) of
 // its row, of which exactly one has the pass's colour
 // ======================================================================
+// a -= *m (a gauge shift)
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_gauge_by(T *__restrict__ a, size_t n, const double *__restrict__ m)
+{
+    const T v = (T)(*m);
+    for (size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x; id < n; id += (size_t)gridDim.x * blockDim.x)
+        a[id] -= v;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kRowThreads)
 k_rb_pass(const T *__restrict__ src, T *__restrict__ dst, const T *__restrict__ g,
@@ -531,15 +541,15 @@ static cudaError_t fused_sweep_launch(int N, const T *src, T *dst, const T *g, c
 
 template <typename T>
 cudaError_t sweep(int N, double h, int rule, T *t, const T *g, const double *cptr,
-                  double cval, int sweeps, T *work, cudaStream_t s)
+                  double cval, int sweeps, T *work, cudaStream_t s, const double *gshift)
 {
     const T ih2 = (T)(1.0 / (h * h)), h2_6 = (T)(h * h / 6.0);
     if constexpr (std::is_same<T, float>::value) {
-        if (reg_sweep_ok(N, t, work, g, nullptr) && reg_sweep_ok(N, work, t, g, nullptr)) {
+        if (sweeps > 0 && reg_sweep_ok(N, t, work, g, nullptr) && reg_sweep_ok(N, work, t, g, nullptr)) {
             T *a = t, *b = work;
             for (int it = 0; it < sweeps; ++it) {
                 const cudaError_t e = reg_sweep_launch(false, N, a, b, g, nullptr, cptr, cval, ih2, h2_6, rule,
-                                                       g_fused_chunk, s);
+                                                       g_fused_chunk, s, it == 0 ? gshift : nullptr);
                 if (e != cudaSuccess) return e;
                 T *tmp = a;
                 a = b;
@@ -548,6 +558,10 @@ cudaError_t sweep(int N, double h, int rule, T *t, const T *g, const double *cpt
             if (a != t) return cudaMemcpyAsync(t, a, sizeof(T) * (size_t)N * N * N, cudaMemcpyDeviceToDevice, s);
             return cudaSuccess;
         }
+    }
+    if (gshift) {   // no kernel here folds it: subtract first
+        note_launch();
+        k_gauge_by<T><<<stride_blocks((size_t)N * N * N), kThreads, 0, s>>>(t, (size_t)N * N * N, gshift);
     }
     if (N >= kFusedMinN && pair_aligned(t) && pair_aligned(work)) {
         T *a = t, *b = work;
@@ -568,8 +582,8 @@ cudaError_t sweep(int N, double h, int rule, T *t, const T *g, const double *cpt
     }
     return cudaGetLastError();
 }
-template cudaError_t sweep<double>(int, double, int, double *, const double *, const double *, double, int, double *, cudaStream_t);
-template cudaError_t sweep<float>(int, double, int, float *, const float *, const double *, double, int, float *, cudaStream_t);
+template cudaError_t sweep<double>(int, double, int, double *, const double *, const double *, double, int, double *, cudaStream_t, const double *);
+template cudaError_t sweep<float>(int, double, int, float *, const float *, const double *, double, int, float *, cudaStream_t, const double *);
 
 // ======================================================================
 // residuals
@@ -2112,21 +2126,28 @@ cudaError_t fas_tail(recon_handle *H, const Hier<T> &Y, int l, const double *cpt
     return cudaGetLastError();
 }
 
-// FAS V-cycle from level l (Sec. II.A.3).
+// FAS V-cycle from level l (Sec. II.A.3).  gshift (nullable): a device
+// scalar subtracted from level l's theta first (a deferred gauge shift;
+// folded into the first sweep where it can be).
 template <typename T>
-cudaError_t vcycle(recon_handle *H, const Hier<T> &Y, int l, const double *cptr)
+cudaError_t vcycle(recon_handle *H, const Hier<T> &Y, int l, const double *cptr, const double *gshift = nullptr)
 {
     cudaStream_t s = H->stream;
     const recon_config &cf = H->cfg;
     set_fused_chunk(cf.fused_chunk);
     const int N = H->Nl[l];
     const double h = H->hl[l];
+    if (gshift && (l == H->nlev - 1 || ncell(N) <= (size_t)kMaxCoarseCells)) {
+        note_launch();
+        k_gauge_by<T><<<stride_blocks(ncell(N)), kThreads, 0, s>>>(Y.t[l], ncell(N), gshift);
+        gshift = nullptr;
+    }
     if (l < H->nlev - 1 && ncell(N) <= (size_t)kMaxCoarseCells && H->nlev - l <= kTailMaxLevels)
         return fas_tail<T>(H, Y, l, cptr);
     if (l == H->nlev - 1)
         return coarse_solve<T>(N, h, cf.rule, Y.t[l], Y.g[l], cptr, 0.0, cf.coarse_max_sweeps,
                                cf.coarse_rtol, Y.work, nullptr, s);
-    CK(sweep<T>(N, h, cf.rule, Y.t[l], Y.g[l], cptr, 0.0, cf.nu1, Y.work, s));
+    CK(sweep<T>(N, h, cf.rule, Y.t[l], Y.g[l], cptr, 0.0, cf.nu1, Y.work, s, gshift));
 
     const int Nc = H->Nl[l + 1];
     const size_t nc = ncell(Nc);
@@ -2157,9 +2178,11 @@ cudaError_t vcycle(recon_handle *H, const Hier<T> &Y, int l, const double *cptr)
     return sweep<T>(N, h, cf.rule, Y.t[l], Y.g[l], cptr, 0.0, cf.nu2, Y.work, s);
 }
 
-// residual norms of level l, then c -= mean r, rel, and theta -= mean theta.
+// residual norms of level l, then c -= mean r, rel, and theta -= mean theta
+// (apply = false: the mean is left in scal[S_MEAN_T] for the next cycle to
+// subtract)
 template <typename T>
-cudaError_t compat_gauge(recon_handle *H, const Hier<T> &Y, int l)
+cudaError_t compat_gauge(recon_handle *H, const Hier<T> &Y, int l, bool apply = true)
 {
     cudaStream_t s = H->stream;
     const int N = H->Nl[l];
@@ -2169,8 +2192,10 @@ cudaError_t compat_gauge(recon_handle *H, const Hier<T> &Y, int l)
                                                   H->partials, nullptr, nullptr, s);
     note_launch();
     k_finalize_cycle<<<1, kReduceThreads, 0, s>>>(H->partials, nbr, (double)n, H->scal);
-    note_launch();
-    k_gauge<T><<<stride_blocks(n), kThreads, 0, s>>>(Y.t[l], n, H->scal);
+    if (apply) {
+        note_launch();
+        k_gauge<T><<<stride_blocks(n), kThreads, 0, s>>>(Y.t[l], n, H->scal);
+    }
     return cudaGetLastError();
 }
 
@@ -2389,18 +2414,27 @@ cudaError_t mixed_start(recon_handle *H, const double *b, const double *phi)
     const Hier<float> Y = hier32(H);
     note_launch();
     k_to_float<<<blocks_for(n), kThreads, 0, s>>>(b, H->g32[0], n);
-    if (H->cfg.start == RECON_START_FMG) return fmg_start<float>(H, Y);
-    note_launch();
-    k_to_float<<<blocks_for(n), kThreads, 0, s>>>(phi, H->t32[0], n);
-    CK(cudaMemsetAsync(H->scal + S_C, 0, sizeof(double), s));
-    return compat_gauge<float>(H, Y, 0);
+    if (H->cfg.start == RECON_START_FMG) {
+        CK(fmg_start<float>(H, Y));
+    } else {
+        note_launch();
+        k_to_float<<<blocks_for(n), kThreads, 0, s>>>(phi, H->t32[0], n);
+        CK(cudaMemsetAsync(H->scal + S_C, 0, sizeof(double), s));
+        CK(compat_gauge<float>(H, Y, 0));
+    }
+    // no gauge shift pending for the first FP32 cycle
+    return cudaMemsetAsync(H->scal + S_MEAN_T, 0, sizeof(double), s);
 }
 
+// One FP32 FAS cycle on the finest grid.  The gauge (theta -= mean theta)
+// of the previous cycle is applied by this cycle's first sweep (the update
+// depends only on differences of theta), and this cycle's is left pending:
+// one pass over theta per cycle fewer.
 cudaError_t mixed_fas_cycle(recon_handle *H)
 {
     const Hier<float> Y = hier32(H);
-    CK(vcycle<float>(H, Y, 0, H->scal + S_C));
-    return compat_gauge<float>(H, Y, 0);
+    CK(vcycle<float>(H, Y, 0, H->scal + S_C, H->scal + S_MEAN_T));
+    return compat_gauge<float>(H, Y, 0, false);
 }
 
 // from_phi: no FP32 cycle ran after a START_GUESS start, so the caller's FP64
@@ -2409,6 +2443,10 @@ cudaError_t mixed_switch(recon_handle *H, const double *b, double *phi, bool fro
 {
     cudaStream_t s = H->stream;
     const size_t n = ncell(H->N);
+    if (!from_phi) {   // the last FP32 cycle's gauge, still pending
+        note_launch();
+        k_gauge_by<float><<<stride_blocks(n), kThreads, 0, s>>>(H->t32[0], n, H->scal + S_MEAN_T);
+    }
     if (H->cfg.mixed_df_residual) {
         // phi as a double-float pair (theta32 + 0, or the split of phi); b split too
         note_launch(from_phi ? 2 : 1);

@@ -260,6 +260,7 @@ struct RegSweep {
     unsigned NN;
     int j0, k0, i0, i1;
     float ih2, h2_6, c;
+    float gsh;                   // subtracted from the stored values (FAS: a folded gauge shift)
     int rule, w, lane;
     bool hrow, hcol;             // this warp relaxes the ring's rows / columns (warp-uniform)
     int tb, rb;                  // thread bases within an OLD / RED plane
@@ -379,8 +380,12 @@ struct RegSweep {
             out = fas_update2_det(pack19(a0, a1), add2(rhs, f2(c)), ih2, 3.0f * h2_6, h2_6, rule);
         }
         const unsigned base = (unsigned)s * NN + gown;
-        const float2 row0 = B0 ? make_float2(r[Q0][0], out.x) : make_float2(out.x, r[Q0][1]);
-        const float2 row1 = B1 ? make_float2(r[Q0][2], out.y) : make_float2(out.y, r[Q0][3]);
+        float2 row0 = B0 ? make_float2(r[Q0][0], out.x) : make_float2(out.x, r[Q0][1]);
+        float2 row1 = B1 ? make_float2(r[Q0][2], out.y) : make_float2(out.y, r[Q0][3]);
+        if constexpr (!LIN) {
+            row0 = sub2(row0, f2(gsh));
+            row1 = sub2(row1, f2(gsh));
+        }
         *reinterpret_cast<float2 *>(dst + base) = row0;
         *reinterpret_cast<float2 *>(dst + base + (unsigned)N) = row1;
     }
@@ -500,7 +505,7 @@ template <bool LIN>
 __global__ void __launch_bounds__(kBT, LIN ? RECON_REG_CTAS_LIN : RECON_REG_CTAS_FAS)
 k_sweep_reg(const float *__restrict__ src, float *__restrict__ dst, const float *__restrict__ g,
             const float *__restrict__ th, const double *__restrict__ cptr, double cval, int N, int CI,
-            float ih2, float h2_6, int rule)
+            float ih2, float h2_6, int rule, const double *__restrict__ gshift)
 {
     RegSweep<LIN> S;
     S.src = src;
@@ -516,6 +521,7 @@ k_sweep_reg(const float *__restrict__ src, float *__restrict__ dst, const float 
     S.ih2 = ih2;
     S.h2_6 = h2_6;
     S.c = LIN ? 0.0f : (float)(cptr ? *cptr : cval);
+    S.gsh = (!LIN && gshift) ? (float)*gshift : 0.0f;
     S.rule = rule;
     const int tid = threadIdx.x;
     // the warp index through a shuffle from lane 0: the compiler sees it as
@@ -576,7 +582,7 @@ int reg_sweep_chunk(int N, int want)
 
 cudaError_t reg_sweep_launch(bool lin, int N, const float *src, float *dst, const float *g, const float *th,
                              const double *cptr, double cval, float ih2, float h2_6, int rule, int chunk,
-                             cudaStream_t s)
+                             cudaStream_t s, const double *gshift)
 {
     if (!g_reg_ready) {
         const cudaError_t e = prepare_reg_sweeps();
@@ -587,10 +593,10 @@ cudaError_t reg_sweep_launch(bool lin, int N, const float *src, float *dst, cons
     note_launch();
     if (lin)
         k_sweep_reg<true><<<grid, kBT, reg_smem_bytes<true>(), s>>>(src, dst, g, th, cptr, cval, N, CI, ih2,
-                                                                    h2_6, rule);
+                                                                    h2_6, rule, nullptr);
     else
         k_sweep_reg<false><<<grid, kBT, reg_smem_bytes<false>(), s>>>(src, dst, g, th, cptr, cval, N, CI, ih2,
-                                                                      h2_6, rule);
+                                                                      h2_6, rule, gshift);
     return cudaGetLastError();
 }
 
