@@ -719,6 +719,7 @@ def bench_batch(recon, synth, torch, dev, count):
     single = {}
     for n, L in sorted(set(zip(sizes, boxes))):
         single[n] = recon.Solver(n, L, recon.RECON_MIXED)
+        autotune.apply(single[n], n, recon.RECON_MIXED)   # the same schedules as the batch
     for b, n in zip(bs[:5], sizes[:5]):
         single[n].solve(b, tol=1e-8, max_cycles=40)
     torch.cuda.synchronize()
