@@ -13,10 +13,10 @@ struct df {
     float hi, lo;
 };
 
-__device__ __forceinline__ df df_make(float hi, float lo) { return {hi, lo}; }
+__host__ __device__ __forceinline__ df df_make(float hi, float lo) { return {hi, lo}; }
 
 // a + b = s + e exactly (any magnitudes).
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+__host__ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
 {
     s = a + b;
     const float bb = s - a;
@@ -24,13 +24,13 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
 }
 
 // a + b = s + e exactly when |a| >= |b| (or a == 0).
-__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e)
+__host__ __device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e)
 {
     s = a + b;
     e = b - (s - a);
 }
 
-__device__ __forceinline__ df df_add(df a, df b)
+__host__ __device__ __forceinline__ df df_add(df a, df b)
 {
     float s, e;
     two_sum(a.hi, b.hi, s, e);
@@ -40,10 +40,10 @@ __device__ __forceinline__ df df_add(df a, df b)
     return r;
 }
 
-__device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
-__device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
+__host__ __device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
+__host__ __device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
 
-__device__ __forceinline__ df df_mul(df a, df b)
+__host__ __device__ __forceinline__ df df_mul(df a, df b)
 {
     const float p = a.hi * b.hi;
     float e = fmaf(a.hi, b.hi, -p);
@@ -54,8 +54,14 @@ __device__ __forceinline__ df df_mul(df a, df b)
     return r;
 }
 
+// a * b = p + e exactly (the FMA product split)
+__host__ __device__ __forceinline__ void two_prod(float a, float b, float &p, float &e)
+{
+    p = a * b;
+    e = fmaf(a, b, -p);
+}
 // a * 2^k for a power-of-two float factor (exact)
-__device__ __forceinline__ df df_scale2(df a, float f) { return {a.hi * f, a.lo * f}; }
+__host__ __device__ __forceinline__ df df_scale2(df a, float f) { return {a.hi * f, a.lo * f}; }
 
 // double -> double-float (one FP64 subtraction)
 __host__ __device__ __forceinline__ df df_from_double(double x)

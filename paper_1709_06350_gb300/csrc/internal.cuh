@@ -90,9 +90,9 @@ bool reg_sweep_ok(int N, const float *src, const float *dst, const float *g, con
 int reg_sweep_chunk(int N, int want);
 // one sweep src -> dst; lin: J e = f with theta th (else the FAS cubic with
 // right side g + c, c from cptr or cval); chunk: planes per CTA (0 = by size)
-// gshift (FAS, nullable): device scalar subtracted from every value the sweep
-// stores (a gauge shift folded into the sweep: the update depends only on
-// differences of theta)
+// gshift (nullable): a device scalar.  FAS: subtracted from every value the
+// sweep stores (a gauge shift folded into the sweep: the update depends only
+// on differences of theta).  LIN: subtracted from the right side f.
 cudaError_t reg_sweep_launch(bool lin, int N, const float *src, float *dst, const float *g, const float *th,
                              const double *cptr, double cval, float ih2, float h2_6, int rule, int chunk,
                              cudaStream_t s, const double *gshift = nullptr);

@@ -22,6 +22,7 @@
 #include "cellmath.cuh"
 #include "cellmath2.cuh"
 #include "dfloat.cuh"
+#include "dfresid.cuh"
 #include "internal.cuh"
 
 namespace recon {
@@ -1298,8 +1299,10 @@ k_sub_scalar(float *__restrict__ a, size_t n, const double *__restrict__ v)
 
 // ---- double-float fine-grid residual of the mixed path
 // r = b + c - det(I + H phi) with phi = phi_hi + phi_lo and b = b_hi + b_lo
-// evaluated in double-float arithmetic; writes float(r) for the linear solve
-// and the block partials sum r, sum r^2 (float per thread, double per block).
+// evaluated in double-float arithmetic (dfresid.cuh; POW2: 1/h^2 is a power
+// of two); writes float(r) for the linear solve and the block partials
+// sum r, sum r^2 (float per thread, double per block).
+template <bool POW2>
 __global__ void __launch_bounds__(kRowThreads)
 k_residual_df(const float *__restrict__ phi_hi, const float *__restrict__ phi_lo,
               const float *__restrict__ b_hi, const float *__restrict__ b_lo,
@@ -1308,33 +1311,14 @@ k_residual_df(const float *__restrict__ phi_hi, const float *__restrict__ phi_lo
 {
     __shared__ double sh[32];
     const df c = df_from_double(*cptr);
-    const df ih2 = df_make(ih2_hi, ih2_lo), q4 = df_scale2(ih2, 0.25f), one = df_make(1.0f, 0.0f);
+    const df ih2 = df_make(ih2_hi, ih2_lo);
     float sr = 0.0f, sr2 = 0.0f;
     FOR_ROWS(N, i, j)
     for (int k = threadIdx.x; k < N; k += kRowX) {
         const Nb19<float> H = load19<float>(phi_hi, N, i, j, k);
         const Nb19<float> Lo = load19<float>(phi_lo, N, i, j, k);
-        const df C2 = df_make(2.0f * H.c, 2.0f * Lo.c);
-        auto diag = [&](float ph, float pl, float mh, float ml) {
-            return df_add(one, df_mul(df_sub(df_add(df_make(ph, pl), df_make(mh, ml)), C2), ih2));
-        };
-        auto mix = [&](float a, float al, float b, float bl, float cc, float cl, float d, float dl) {
-            return df_mul(df_sub(df_add(df_make(a, al), df_make(b, bl)),
-                                 df_add(df_make(cc, cl), df_make(d, dl))), q4);
-        };
-        const df axx = diag(H.xp, Lo.xp, H.xm, Lo.xm);
-        const df ayy = diag(H.yp, Lo.yp, H.ym, Lo.ym);
-        const df azz = diag(H.zp, Lo.zp, H.zm, Lo.zm);
-        const df hxy = mix(H.xpyp, Lo.xpyp, H.xmym, Lo.xmym, H.xmyp, Lo.xmyp, H.xpym, Lo.xpym);
-        const df hyz = mix(H.ypzp, Lo.ypzp, H.ymzm, Lo.ymzm, H.ymzp, Lo.ymzp, H.ypzm, Lo.ypzm);
-        const df hxz = mix(H.xpzp, Lo.xpzp, H.xmzm, Lo.xmzm, H.xmzp, Lo.xmzp, H.xpzm, Lo.xpzm);
-        const df c1 = df_sub(df_mul(ayy, azz), df_mul(hyz, hyz));
-        const df c2 = df_sub(df_mul(hxy, azz), df_mul(hyz, hxz));
-        const df c3 = df_sub(df_mul(hxy, hyz), df_mul(ayy, hxz));
-        const df det = df_add(df_sub(df_mul(axx, c1), df_mul(hxy, c2)), df_mul(hxz, c3));
         const unsigned id = offs(N, i, j, k);
-        const df r = df_sub(df_add(df_make(b_hi[id], b_lo[id]), c), det);
-        const float rf = r.hi + r.lo;
+        const float rf = dfr_residual<POW2>(H, Lo, b_hi[id], b_lo[id], c, ih2);
         fout[id] = rf;
         sr += rf;
         sr2 = fmaf(rf, rf, sr2);
@@ -1454,15 +1438,18 @@ static inline bool lin_fused(int N, const float *e, const float *work)
 
 // cof: the level's cofactor arrays (read by the two-pass kernels); th: its
 // theta (read by the fused kernel)
+// fshift (nullable): a device scalar subtracted from f on the fly; only the
+// register-blocked kernel takes it (the caller checks lin_fold_ok)
 static cudaError_t lin_sweep(int N, double h, float *e, const float *f, const float *cof,
-                             const float *th, int sweeps, float *work, cudaStream_t s)
+                             const float *th, int sweeps, float *work, cudaStream_t s,
+                             const double *fshift = nullptr)
 {
     const float ih2 = (float)(1.0 / (h * h));
     if (reg_sweep_ok(N, e, work, f, th) && reg_sweep_ok(N, work, e, f, th)) {
         float *a = e, *b = work;
         for (int it = 0; it < sweeps; ++it) {
             const cudaError_t err = reg_sweep_launch(true, N, a, b, f, th, nullptr, 0.0, ih2, (float)(h * h / 6.0),
-                                                     0, g_fused_chunk, s);
+                                                     0, g_fused_chunk, s, fshift);
             if (err != cudaSuccess) return err;
             float *tmp = a;
             a = b;
@@ -1513,11 +1500,13 @@ template <bool FROM_TH>
 __global__ void __launch_bounds__(kRowThreads, RECON_WIN_CTAS)
 k_lin_restrict_residual(const float *__restrict__ e, const float *__restrict__ f,
                         const float *__restrict__ cof, const float *__restrict__ th, int Nf,
-                        float ih2, float *__restrict__ fH, double *__restrict__ partials)
+                        float ih2, float *__restrict__ fH, double *__restrict__ partials,
+                        const double *__restrict__ fshift)
 {
     __shared__ double sh[32];
     const size_t nf = (size_t)Nf * Nf * Nf;
     const int Nc = Nf >> 1;
+    const float fs = fshift ? (float)*fshift : 0.0f;   // subtracted from f (its mean, folded in)
     ThreadSum<float> sacc;
     FOR_ROWS(Nc, I, J)
     for (int K = threadIdx.x; K < Nc; K += kRowX) {
@@ -1549,7 +1538,7 @@ k_lin_restrict_residual(const float *__restrict__ e, const float *__restrict__ f
                     } else {
                         A = cof_at(cof, nf, cof_slot(Nf, 2 * I + a, 2 * J + b - 1, 2 * K + cc - 1));
                     }
-                    acc += f[w.at(1 + a, b, cc)] - jac_apply(A, ne, ih2);
+                    acc += (f[w.at(1 + a, b, cc)] - fs) - jac_apply(A, ne, ih2);
                 }
         }
         const float v = acc * 0.125f;
@@ -2329,7 +2318,9 @@ recon_status solve_f64(recon_handle *H, const double *b, double *phi, double tol
 //     phi += e, until ||r64 - mean|| / ||b - 1|| < tol.
 namespace {
 
-cudaError_t lin_vcycle(recon_handle *H, int l)
+// fshift (nullable, level l only): a device scalar subtracted from f on the
+// fly by the register-blocked sweep and the restriction (lin_fold_ok)
+cudaError_t lin_vcycle(recon_handle *H, int l, const double *fshift = nullptr)
 {
     cudaStream_t s = H->stream;
     const recon_config &cf = H->cfg;
@@ -2382,17 +2373,17 @@ cudaError_t lin_vcycle(recon_handle *H, int l)
                                                                          cf.coarse_rtol);
         return cudaGetLastError();
     }
-    CK(lin_sweep(N, h, H->e32[l], H->f32[l], H->cof32[l], H->t32[l], cf.nu1, H->work32, s));
+    CK(lin_sweep(N, h, H->e32[l], H->f32[l], H->cof32[l], H->t32[l], cf.nu1, H->work32, s, fshift));
     const int Nc = H->Nl[l + 1];
     const size_t nc = ncell(Nc);
     const unsigned nbr = row_grid(Nc, kMaxRedBlocks);
     note_launch();
     if (H->cof32[l])
         k_lin_restrict_residual<false><<<nbr, row_block(), 0, s>>>(H->e32[l], H->f32[l], H->cof32[l], nullptr,
-                                                                    N, ih2, H->f32[l + 1], H->partials);
+                                                                    N, ih2, H->f32[l + 1], H->partials, fshift);
     else
         k_lin_restrict_residual<true><<<nbr, row_block(), 0, s>>>(H->e32[l], H->f32[l], nullptr, H->t32[l],
-                                                                   N, ih2, H->f32[l + 1], H->partials);
+                                                                   N, ih2, H->f32[l + 1], H->partials, fshift);
     note_launch();
     k_finalize_mean<<<1, kReduceThreads, 0, s>>>(H->partials, nbr, (double)nc,
                                                  H->scal + slot_rmean(l + 1));
@@ -2401,7 +2392,18 @@ cudaError_t lin_vcycle(recon_handle *H, int l)
     CK(cudaMemsetAsync(H->e32[l + 1], 0, sizeof(float) * nc, s));
     CK(lin_vcycle(H, l + 1));
     CK(prolong_add<float>(Nc, H->e32[l + 1], (const float *)nullptr, nullptr, 1.0, H->e32[l], s));
-    return lin_sweep(N, h, H->e32[l], H->f32[l], H->cof32[l], H->t32[l], cf.nu2, H->work32, s);
+    return lin_sweep(N, h, H->e32[l], H->f32[l], H->cof32[l], H->t32[l], cf.nu2, H->work32, s, fshift);
+}
+
+// The finest level's f can carry its mean unsubtracted into the linear
+// V-cycles when every kernel that reads it there folds the shift in: the
+// register-blocked sweep (both directions of its ping-pong) and the
+// restriction (a level above the single-block tail).
+static bool lin_fold_ok(recon_handle *H)
+{
+    const int N = H->Nl[0];
+    return H->nlev > 1 && ncell(N) > (size_t)kMaxCoarseCells && reg_sweep_ok(N, H->e32[0], H->work32, H->f32[0], H->t32[0]) &&
+           reg_sweep_ok(N, H->work32, H->e32[0], H->f32[0], H->t32[0]);
 }
 
 }  // namespace
@@ -2472,10 +2474,17 @@ cudaError_t mixed_residual(recon_handle *H, const double *b, const double *phi)
     const double ih2 = 1.0 / (H->h * H->h);
     if (H->cfg.mixed_df_residual) {
         const df ih2df = df_from_double(ih2);
+        int ex;
+        const bool pow2 = ih2df.lo == 0.0f && std::frexp(ih2, &ex) == 0.5;
         note_launch();
-        k_residual_df<<<nbr, row_block(), 0, s>>>(H->t32[0], H->lo32, H->g32[0], H->blo32,
-                                                  H->scal + S_C, H->N, ih2df.hi, ih2df.lo,
-                                                  H->f32[0], H->partials);
+        if (pow2)
+            k_residual_df<true><<<nbr, row_block(), 0, s>>>(H->t32[0], H->lo32, H->g32[0], H->blo32,
+                                                            H->scal + S_C, H->N, ih2df.hi, ih2df.lo,
+                                                            H->f32[0], H->partials);
+        else
+            k_residual_df<false><<<nbr, row_block(), 0, s>>>(H->t32[0], H->lo32, H->g32[0], H->blo32,
+                                                             H->scal + S_C, H->N, ih2df.hi, ih2df.lo,
+                                                             H->f32[0], H->partials);
     } else {
         nbr = launch_residual_norms<double>(phi, b, H->scal + S_C, H->N, ih2, H->partials, H->f32[0],
                                             H->t32[0], s);
@@ -2490,8 +2499,13 @@ cudaError_t mixed_correct(recon_handle *H, double *phi)
 {
     cudaStream_t s = H->stream;
     const size_t n = ncell(H->N);
-    note_launch();
-    k_sub_scalar<<<stride_blocks(n), kThreads, 0, s>>>(H->f32[0], n, H->scal + S_MEAN_R);
+    // r - mean r: subtracted on the fly by the finest level's kernels where
+    // they can, else in a pass of its own
+    const bool fold = lin_fold_ok(H);
+    if (!fold) {
+        note_launch();
+        k_sub_scalar<<<stride_blocks(n), kThreads, 0, s>>>(H->f32[0], n, H->scal + S_MEAN_R);
+    }
     for (int l = 1; l < H->nlev; ++l) CK(restrict_plain<float>(H->Nl[l - 1], H->t32[l - 1], H->t32[l], s));
     for (int l = 0; l < H->nlev; ++l) {
         if (H->Nl[l] >= kFusedMinN) continue;   // formed from theta32 in the kernels
@@ -2500,7 +2514,8 @@ cudaError_t mixed_correct(recon_handle *H, double *phi)
                                                            (float)(1.0 / (H->hl[l] * H->hl[l])), H->cof32[l]);
     }
     CK(cudaMemsetAsync(H->e32[0], 0, sizeof(float) * n, s));
-    for (int v = 0; v < H->cfg.mixed_linear_vcycles; ++v) CK(lin_vcycle(H, 0));
+    for (int v = 0; v < H->cfg.mixed_linear_vcycles; ++v)
+        CK(lin_vcycle(H, 0, fold ? H->scal + S_MEAN_R : nullptr));
     note_launch();
     if (H->cfg.mixed_df_residual)
         k_update_df<<<blocks_for(n), kThreads, 0, s>>>(H->t32[0], H->lo32, H->e32[0], n);

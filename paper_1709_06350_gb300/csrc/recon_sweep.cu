@@ -346,7 +346,7 @@ struct RegSweep {
         if constexpr (LIN) {
             const Nb19<float> t0 = old19<QM, Q0, QP, 0, B0>(t, pm + kHOP, pc + kHOP, pp + kHOP);
             const Nb19<float> t1 = old19<QM, Q0, QP, 1, B1>(t, pm + kHOP, pc + kHOP, pp + kHOP);
-            out = lin_update2(pack19(t0, t1), pack19(n0, n1), rhs, ih2, 6.0f * h2_6);
+            out = lin_update2(pack19(t0, t1), pack19(n0, n1), add2(rhs, f2(c)), ih2, 6.0f * h2_6);
         } else {
             out = fas_update2_det(pack19(n0, n1), add2(rhs, f2(c)), ih2, 3.0f * h2_6, h2_6, rule);
         }
@@ -375,7 +375,7 @@ struct RegSweep {
         if constexpr (LIN) {
             const Nb19<float> t0 = old19<QM, Q0, QP, 0, B0>(t, pm + kHOP, pc + kHOP, pp + kHOP);
             const Nb19<float> t1 = old19<QM, Q0, QP, 1, B1>(t, pm + kHOP, pc + kHOP, pp + kHOP);
-            out = lin_update2(pack19(t0, t1), pack19(a0, a1), rhs, ih2, 6.0f * h2_6);
+            out = lin_update2(pack19(t0, t1), pack19(a0, a1), add2(rhs, f2(c)), ih2, 6.0f * h2_6);
         } else {
             out = fas_update2_det(pack19(a0, a1), add2(rhs, f2(c)), ih2, 3.0f * h2_6, h2_6, rule);
         }
@@ -424,7 +424,7 @@ struct RegSweep {
         if constexpr (LIN) {
             const Nb19<float> ta = gather_at(som + kHOP, soc + kHOP, sop + kHOP, Sa, Oa);
             const Nb19<float> tb_ = gather_at(som + kHOP, soc + kHOP, sop + kHOP, Sb, Ob);
-            out = lin_update2(pack19(ta, tb_), pack19(na, nb), rhs, ih2, 6.0f * h2_6);
+            out = lin_update2(pack19(ta, tb_), pack19(na, nb), add2(rhs, f2(c)), ih2, 6.0f * h2_6);
         } else {
             out = fas_update2_det(pack19(na, nb), add2(rhs, f2(c)), ih2, 3.0f * h2_6, h2_6, rule);
         }
@@ -520,7 +520,9 @@ k_sweep_reg(const float *__restrict__ src, float *__restrict__ dst, const float 
     S.i1 = S.i0 + CI;
     S.ih2 = ih2;
     S.h2_6 = h2_6;
-    S.c = LIN ? 0.0f : (float)(cptr ? *cptr : cval);
+    // FAS: the compatibility scalar c added to the right side; LIN: minus the
+    // shift subtracted from f (its mean, folded in: f + (-m) rounds as f - m)
+    S.c = LIN ? (gshift ? -(float)*gshift : 0.0f) : (float)(cptr ? *cptr : cval);
     S.gsh = (!LIN && gshift) ? (float)*gshift : 0.0f;
     S.rule = rule;
     const int tid = threadIdx.x;
@@ -593,7 +595,7 @@ cudaError_t reg_sweep_launch(bool lin, int N, const float *src, float *dst, cons
     note_launch();
     if (lin)
         k_sweep_reg<true><<<grid, kBT, reg_smem_bytes<true>(), s>>>(src, dst, g, th, cptr, cval, N, CI, ih2,
-                                                                    h2_6, rule, nullptr);
+                                                                    h2_6, rule, gshift);
     else
         k_sweep_reg<false><<<grid, kBT, reg_smem_bytes<false>(), s>>>(src, dst, g, th, cptr, cval, N, CI, ih2,
                                                                       h2_6, rule, gshift);
