@@ -112,6 +112,43 @@ __host__ __device__ __forceinline__ float df_i2f(int d)
     return fmaf(fh, 16384.0f, fl);
 }
 
+__host__ __device__ __forceinline__ double df_dfrombits(unsigned long long u)
+{
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double((long long)u);
+#else
+    double d;
+    __builtin_memcpy(&d, &u, sizeof d);
+    return d;
+#endif
+}
+#ifdef __CUDA_ARCH__
+__device__ __noinline__ double df_f2d_ool(float x) { return (double)x; }
+#else
+inline double df_f2d_ool(float x) { return (double)x; }
+#endif
+// float -> double from the bit pattern (exact) with integer operations only:
+// for a normal float the exponent is rebiased (127 -> 1023) and the 23-bit
+// fraction widened to 52 bits; zeros keep their sign; subnormal, infinite and
+// NaN floats take the conversion instruction, out of line.
+__host__ __device__ __forceinline__ double df_f2d_bits(float x)
+{
+    unsigned u;
+#ifdef __CUDA_ARCH__
+    u = __float_as_uint(x);
+#else
+    __builtin_memcpy(&u, &x, sizeof u);
+#endif
+    const unsigned e = (u >> 23) & 0xFFu;
+    const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+    if (e - 1u >= 254u) {   // e == 0 or e == 255
+        if ((u & 0x7FFFFFFFu) == 0u) return df_dfrombits(sign);
+        return df_f2d_ool(x);
+    }
+    return df_dfrombits(sign | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29));
+}
+// hi + lo in FP64: both parts widened exactly, one FP64 addition
+__host__ __device__ __forceinline__ double df_to_double_bits(df a) { return df_f2d_bits(a.hi) + df_f2d_bits(a.lo); }
 // the FP64 split, out of line on the device so that the rare inputs outside
 // the integer path's range take a real branch (an inlined copy was evaluated
 // for every element and kept the FP64 pipe busy)

@@ -1269,7 +1269,7 @@ __global__ void __launch_bounds__(kThreads)
 k_to_float(const double *__restrict__ a, float *__restrict__ out, size_t n)
 {
     const size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (id < n) out[id] = (float)a[id];
+    if (id < n) out[id] = df_from_double_bits(a[id]).hi;   // RN(a), rounded with integer operations
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -1356,21 +1356,29 @@ k_update_df(float *__restrict__ hi, float *__restrict__ lo, const float *__restr
     }
 }
 
-// phi = phi_hi + phi_lo in FP64, with block partial sums of phi for the gauge
+// block partial sums of phi_hi + phi_lo (double-float sums per thread)
 __global__ void __launch_bounds__(kThreads)
-k_df_to_double(const float *__restrict__ hi, const float *__restrict__ lo, double *__restrict__ phi,
-               size_t n, double *__restrict__ partials)
+k_df_sum(const float *__restrict__ hi, const float *__restrict__ lo, size_t n, double *__restrict__ partials)
 {
     __shared__ double sh[32];
-    double s = 0.0;
+    df s = df_make(0.0f, 0.0f);
     for (size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x; id < n;
-         id += (size_t)gridDim.x * blockDim.x) {
-        const double v = df_to_double(df_make(hi[id], lo[id]));
-        phi[id] = v;
-        s += v;
-    }
-    const double v = block_sum<kThreads>(s, sh);
+         id += (size_t)gridDim.x * blockDim.x)
+        s = df_add(s, df_make(hi[id], lo[id]));
+    const double v = block_sum<kThreads>(df_to_double_bits(s), sh);
     if (ltid() == 0) partials[4 * blockIdx.x + 0] = v;
+}
+
+// phi = (phi_hi + phi_lo) - mean in FP64: the difference in double-float,
+// then both parts widened exactly and added (one FP64 instruction per cell)
+__global__ void __launch_bounds__(kThreads)
+k_df_to_double_gauged(const float *__restrict__ hi, const float *__restrict__ lo, double *__restrict__ phi,
+                      size_t n, const double *__restrict__ mean)
+{
+    const df m = df_from_double(*mean);
+    for (size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x; id < n;
+         id += (size_t)gridDim.x * blockDim.x)
+        phi[id] = df_to_double_bits(df_sub(df_make(hi[id], lo[id]), m));
 }
 
 // ---- linear multigrid for J e = f in FP32.  J = sum adj(I + H theta)_ab D_ab
@@ -2318,6 +2326,18 @@ recon_status solve_f64(recon_handle *H, const double *b, double *phi, double tol
 //     phi += e, until ||r64 - mean|| / ||b - 1|| < tol.
 namespace {
 
+// Level l's f can carry its mean unsubtracted into a linear V-cycle when
+// every kernel that reads it there folds the shift in: the register-blocked
+// sweep (both directions of its ping-pong) and the restriction (a level above
+// the single-block tail and the coarsest solve).
+static bool lin_fold_ok(recon_handle *H, int l)
+{
+    const int N = H->Nl[l];
+    return l < H->nlev - 1 && ncell(N) > (size_t)kMaxCoarseCells &&
+           reg_sweep_ok(N, H->e32[l], H->work32, H->f32[l], H->t32[l]) &&
+           reg_sweep_ok(N, H->work32, H->e32[l], H->f32[l], H->t32[l]);
+}
+
 // fshift (nullable, level l only): a device scalar subtracted from f on the
 // fly by the register-blocked sweep and the restriction (lin_fold_ok)
 cudaError_t lin_vcycle(recon_handle *H, int l, const double *fshift = nullptr)
@@ -2387,24 +2407,18 @@ cudaError_t lin_vcycle(recon_handle *H, int l, const double *fshift = nullptr)
     note_launch();
     k_finalize_mean<<<1, kReduceThreads, 0, s>>>(H->partials, nbr, (double)nc,
                                                  H->scal + slot_rmean(l + 1));
-    note_launch();
-    k_sub_scalar<<<stride_blocks(nc), kThreads, 0, s>>>(H->f32[l + 1], nc, H->scal + slot_rmean(l + 1));
+    // f - mean f on the coarse level: folded into its kernels where they can
+    const bool fold = lin_fold_ok(H, l + 1);
+    if (!fold) {
+        note_launch();
+        k_sub_scalar<<<stride_blocks(nc), kThreads, 0, s>>>(H->f32[l + 1], nc, H->scal + slot_rmean(l + 1));
+    }
     CK(cudaMemsetAsync(H->e32[l + 1], 0, sizeof(float) * nc, s));
-    CK(lin_vcycle(H, l + 1));
+    CK(lin_vcycle(H, l + 1, fold ? H->scal + slot_rmean(l + 1) : nullptr));
     CK(prolong_add<float>(Nc, H->e32[l + 1], (const float *)nullptr, nullptr, 1.0, H->e32[l], s));
     return lin_sweep(N, h, H->e32[l], H->f32[l], H->cof32[l], H->t32[l], cf.nu2, H->work32, s, fshift);
 }
 
-// The finest level's f can carry its mean unsubtracted into the linear
-// V-cycles when every kernel that reads it there folds the shift in: the
-// register-blocked sweep (both directions of its ping-pong) and the
-// restriction (a level above the single-block tail).
-static bool lin_fold_ok(recon_handle *H)
-{
-    const int N = H->Nl[0];
-    return H->nlev > 1 && ncell(N) > (size_t)kMaxCoarseCells && reg_sweep_ok(N, H->e32[0], H->work32, H->f32[0], H->t32[0]) &&
-           reg_sweep_ok(N, H->work32, H->e32[0], H->f32[0], H->t32[0]);
-}
 
 }  // namespace
 
@@ -2501,7 +2515,7 @@ cudaError_t mixed_correct(recon_handle *H, double *phi)
     const size_t n = ncell(H->N);
     // r - mean r: subtracted on the fly by the finest level's kernels where
     // they can, else in a pass of its own
-    const bool fold = lin_fold_ok(H);
+    const bool fold = lin_fold_ok(H, 0);
     if (!fold) {
         note_launch();
         k_sub_scalar<<<stride_blocks(n), kThreads, 0, s>>>(H->f32[0], n, H->scal + S_MEAN_R);
@@ -2532,9 +2546,10 @@ cudaError_t mixed_finish(recon_handle *H, double *phi, bool converged)
     if (H->cfg.mixed_df_residual) {
         const unsigned nb2 = red_blocks(n);
         note_launch(3);
-        k_df_to_double<<<nb2, kThreads, 0, s>>>(H->t32[0], H->lo32, phi, n, H->partials);
+        k_df_sum<<<nb2, kThreads, 0, s>>>(H->t32[0], H->lo32, n, H->partials);
         k_finalize_mean<<<1, kReduceThreads, 0, s>>>(H->partials, nb2, (double)n, H->scal + S_MEAN_T);
-        k_gauge<double><<<stride_blocks(n), kThreads, 0, s>>>(phi, n, H->scal);
+        k_df_to_double_gauged<<<stride_blocks(n), kThreads, 0, s>>>(H->t32[0], H->lo32, phi, n,
+                                                                   H->scal + S_MEAN_T);
     } else if (converged) {
         note_launch();
         k_gauge<double><<<stride_blocks(n), kThreads, 0, s>>>(phi, n, H->scal);

@@ -4,7 +4,8 @@ FP64 definition hi = RN(x), lo = RN(x - hi) (df_from_double): bit for bit,
 on random values over the whole double range and on the cases the integer
 rounding has to get right (ties to even, a carry into the exponent, signs,
 zero remainders, the range edges).  A host program compiled from the
-library's header evaluates both."""
+library's header evaluates both.  Likewise the float -> double widening
+from the bit pattern (df_f2d_bits) against the conversion instruction."""
 import os
 import shutil
 import struct
@@ -72,6 +73,58 @@ def test_integer_split_equals_fp64_split(tmp_path):
                 for sgn in (0, 1):
                     words.append((sgn << 63) | (e << 52) | (keep << 29) | r)
     words += [0, 1 << 63, 0x7FF0000000000000, 0xFFF0000000000000, 0x7FF8000000000000, 1]
+    out = subprocess.run([str(exe)], input="\n".join("%x" % w for w in words),
+                         capture_output=True, text=True, check=True).stdout
+    assert out.strip().endswith("checked %d bad 0" % len(words)), out[-2000:]
+
+
+WIDEN = r"""
+#include <cstdio>
+#include <cstring>
+#include <cmath>
+#include "dfloat.cuh"
+int main()
+{
+    unsigned u;
+    long bad = 0, n = 0;
+    while (scanf("%x", &u) == 1) {
+        float f;
+        std::memcpy(&f, &u, 4);
+        const double a = (double)f, b = recon::df_f2d_bits(f);
+        unsigned long long ua, ub;
+        std::memcpy(&ua, &a, 8); std::memcpy(&ub, &b, 8);
+        ++n;
+        if (ua != ub && !(std::isnan(a) && std::isnan(b))) {
+            if (bad < 5) printf("mismatch %08x: %016llx vs %016llx\n", u, ua, ub);
+            ++bad;
+        }
+    }
+    printf("checked %ld bad %ld\n", n, bad);
+    return 0;
+}
+"""
+
+
+def test_integer_widening_equals_conversion(tmp_path):
+    """df_f2d_bits (the widening the mixed path's final conversion uses)
+    equals the float -> double conversion bit for bit: random patterns over
+    every exponent, signed zeros, subnormals, the normal range's edges,
+    infinities and NaNs."""
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    src = tmp_path / "widen.cu"
+    src.write_text(WIDEN)
+    exe = tmp_path / "widen"
+    subprocess.run([nvcc, "-std=c++17", "-Xcompiler", "-ffp-contract=off",
+                    "-I" + os.path.join(ROOT, "paper_1709_06350_gb300", "csrc"), str(src), "-o", str(exe)],
+                   check=True, capture_output=True)
+    rng = np.random.default_rng(11)
+    words = rng.integers(0, 2 ** 32, 40000, dtype=np.uint64).tolist()
+    for e in (0, 1, 2, 126, 127, 128, 253, 254, 255):
+        for m in (0, 1, 2, 0x400000, 0x7FFFFE, 0x7FFFFF):
+            for sgn in (0, 1):
+                words.append((sgn << 31) | (e << 23) | m)
     out = subprocess.run([str(exe)], input="\n".join("%x" % w for w in words),
                          capture_output=True, text=True, check=True).stdout
     assert out.strip().endswith("checked %d bad 0" % len(words)), out[-2000:]
