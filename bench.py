@@ -33,6 +33,29 @@ METRIC = ("512³ time-to-‖r‖/‖δ‖<1e-8 (mixed vs FP64 GPU); "
 UNIT = "512^3 reconstructions/s"
 
 
+def pin_to_local_cpus(dev_index):
+    """Restrict this process to the CPUs attached to the GPU (its PCI
+    device's local_cpulist), so that page-locked buffers allocated afterwards
+    are placed on that CPU's memory node.  Returns the list, or None when the
+    platform does not report one (nothing is changed then)."""
+    import torch
+    try:
+        p = torch.cuda.get_device_properties(dev_index)
+        bdf = "%04x:%02x:%02x.0" % (p.pci_domain_id, p.pci_bus_id, p.pci_device_id)
+        with open(f"/sys/bus/pci/devices/{bdf}/local_cpulist") as f:
+            spec = f.read().strip()
+        cpus = set()
+        for part in spec.split(","):
+            a, _, b = part.partition("-")
+            cpus.update(range(int(a), int(b or a) + 1))
+        cpus &= os.sched_getaffinity(0)
+        if not cpus:
+            return None
+        os.sched_setaffinity(0, cpus)
+        return spec
+    except (OSError, AttributeError, ValueError):
+        return None
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -266,9 +289,12 @@ def main():
     pos = synth.zeldovich_positions(dh, N, L).contiguous()
     del dh
     torch.cuda.empty_cache()
-    # page-locked host buffers of the end-to-end leg, made before any timed work
+    # page-locked host buffers of the end-to-end leg, made before any timed
+    # work, on the memory node of the CPUs attached to this GPU
     host = None
+    host_cpus = None
     if not args.no_e2e:
+        host_cpus = pin_to_local_cpus(local)
         host = {"pos": pos.cpu().pin_memory(),
                 "dl": [torch.empty((N, N, N), dtype=torch.float64).pin_memory() for _ in range(2)]}
 
@@ -349,7 +375,8 @@ def main():
         posbuf = [torch.empty_like(pos) for _ in range(2)]
         dlbuf = [torch.empty((N, N, N), dtype=torch.float64, device=dev) for _ in range(2)]
         psibuf = torch.empty((3, N, N, N), dtype=torch.float64, device=dev)
-        copy = torch.cuda.Stream(device=dev)
+        copy = torch.cuda.Stream(device=dev)       # positions in
+        copy_out = torch.cuda.Stream(device=dev)   # delta_r out (the other direction)
 
         def run_host(K):
             h2d = [torch.cuda.Event() for _ in range(2)]
@@ -377,12 +404,13 @@ def main():
                 solver.displace(phi, b, psi=psibuf, dl=dlbuf[cur])
                 done = torch.cuda.Event()
                 done.record(stream)
-                with torch.cuda.stream(copy):
-                    copy.wait_event(done)
+                with torch.cuda.stream(copy_out):
+                    copy_out.wait_event(done)
                     dl_host[cur].copy_(dlbuf[cur], non_blocking=True)
                     d2h[cur] = torch.cuda.Event()
-                    d2h[cur].record(copy)
+                    d2h[cur].record(copy_out)
             stream.wait_stream(copy)
+            stream.wait_stream(copy_out)
             return dl_host[(K - 1) % 2]
 
         ke = max(1, args.steps)
@@ -400,7 +428,8 @@ def main():
                "h2d_bytes_per_step": pos.numel() * 8, "d2h_bytes_per_step": N ** 3 * 8,
                "ms_per_step": e2e_ms,
                "transfer": "positions of step k+1 copied in and delta_r of step k copied out by "
-                           "the copy engines on a copy stream, overlapping step k",
+                           "the copy engines, one stream per direction, overlapping step k",
+               "host_buffers_cpus": host_cpus,
                "max_abs_diff_vs_device_step": check}
         del pos_host, dl_host, posbuf, dlbuf, psibuf, host
 
