@@ -70,7 +70,6 @@ __host__ __device__ __forceinline__ df df_from_double(double x)
     return {hi, (float)(x - (double)hi)};
 }
 
-__device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
 
 // The same split as df_from_double, from the bit pattern with integer
 // operations only (FP64 instructions, conversions included, issue at 1/64 of
