@@ -53,7 +53,7 @@ def pin_to_local_cpus(dev_index):
             return None
         os.sched_setaffinity(0, cpus)
         return spec
-    except (OSError, AttributeError, ValueError):
+    except Exception:   # best effort: any failure leaves the affinity as it was
         return None
 
 def parse():
