@@ -693,6 +693,18 @@ MUTATIONS = {
     "smooth-window-exponent": ("oracle.py", "np.exp(-0.5 * k2 * R * R)", "np.exp(-k2 * R * R)"),
     "smooth-no-renorm": ("oracle.py", "    b = np.maximum(r, floor)\n    return b / b.mean()",
                          "    b = np.maximum(r, floor)\n    return b"),
+    "cic-offset": ("double u = x * ((double)N / L) - 0.5;", "double u = x * ((double)N / L);"),
+    "cic-weight-swap": ("double w = (a ? f[0] : 1.0 - f[0]) * (b ? f[1] : 1.0 - f[1])\n"
+                        "                             * (cc ? f[2] : 1.0 - f[2]);\n"
+                        "                    rho[at(N, i0[0] + a, i0[1] + b, i0[2] + cc)] += mass * w;",
+                        "double w = (a ? 1.0 - f[0] : f[0]) * (b ? f[1] : 1.0 - f[1])\n"
+                        "                             * (cc ? f[2] : 1.0 - f[2]);\n"
+                        "                    rho[at(N, i0[0] + a, i0[1] + b, i0[2] + cc)] += mass * w;"),
+    "coarse-rhs-sign": ("Hh->g[l + 1][x] = dH[x] + sc * rr[x];", "Hh->g[l + 1][x] = dH[x] - sc * rr[x];"),
+    "jacobian-row-mixed-once": ("double wxy = 2.0 * cxy / (4.0 * h2);", "double wxy = cxy / (4.0 * h2);"),
+    "jacobian-apply-mixed-once": ("+ 2.0 * (cof[3 * n + id] * D[0][1]", "+ (cof[3 * n + id] * D[0][1]"),
+    "adjoint-no-transpose": ("oracle.py", "AT = A.T.tocsc()", "AT = A.tocsc()"),
+    "gauss-no-mean": ("oracle.py", "g = v.mean() + v.std() * ndtri(", "g = v.std() * ndtri("),
     "eps-no-compat": ("or_cell_cubic(t, N, h, i, j, k, g[at(N, i, j, k)] + c, &s, &p, &q);\n                double L",
                       "or_cell_cubic(t, N, h, i, j, k, g[at(N, i, j, k)], &s, &p, &q);\n                double L"),
 }
@@ -731,6 +743,10 @@ def test_mutations_are_caught(O, name, tmp_path):
         lambda: test_paper_eps_plane_closed_form(M),
         lambda: test_smoothing_window_on_single_modes(M, (1, 2, 3)),
         lambda: test_smoothing_floor_and_mean(M),
+        lambda: test_cic_textbook_definition(M),
+        lambda: test_jacobian_matches_finite_differences(M),
+        lambda: test_adjoint_matches_finite_differences(M),
+        lambda: test_gaussianise_properties(M),
     ]
     failed = 0
     for pin in pins:
