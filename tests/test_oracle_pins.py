@@ -317,6 +317,19 @@ def test_orderings_reach_the_same_solution(O, ordering, rule):
     assert np.max(np.abs(t1 - t0)) < 1e-9 * np.max(np.abs(t0))
 
 
+def test_nested_start_reaches_the_same_solution(O):
+    """The nested-iteration start (coarsest grid first) and the paper's start
+    from theta = 0 on the finest grid converge to the same theta*; the nested
+    start needs no more cycles."""
+    N, L = 16, 32.0
+    b = O.smooth_and_floor(1.0 + synth.smooth_field(N, 37, 1.0, kmax=2), L, 0.0)
+    t0, i0 = O.solve(b, L, fmg=True, **SOLVE)
+    t1, i1 = O.solve(b, L, theta0=np.zeros_like(b), fmg=False, **SOLVE)
+    assert i0["status"] == 0 and i1["status"] == 0
+    assert np.max(np.abs(t1 - t0)) < 1e-9 * np.max(np.abs(t0))
+    assert i0["cycles"] <= i1["cycles"]
+
+
 def test_num_levels(O):
     assert [O.num_levels(n) for n in (4, 6, 8, 32, 96, 192, 512)] == [1, 1, 2, 4, 5, 6, 8]
 
