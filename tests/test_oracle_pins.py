@@ -718,6 +718,8 @@ MUTATIONS = {
     "jacobian-apply-mixed-once": ("+ 2.0 * (cof[3 * n + id] * D[0][1]", "+ (cof[3 * n + id] * D[0][1]"),
     "adjoint-no-transpose": ("oracle.py", "AT = A.T.tocsc()", "AT = A.tocsc()"),
     "gauss-no-mean": ("oracle.py", "g = v.mean() + v.std() * ndtri(", "g = v.std() * ndtri("),
+    "traceless-half": ("Hb[a][b] = H[a][b] - (a == b ? tr / 3.0 : 0.0);",
+                       "Hb[a][b] = H[a][b] - (a == b ? tr / 2.0 : 0.0);"),
     "eps-no-compat": ("or_cell_cubic(t, N, h, i, j, k, g[at(N, i, j, k)] + c, &s, &p, &q);\n                double L",
                       "or_cell_cubic(t, N, h, i, j, k, g[at(N, i, j, k)], &s, &p, &q);\n                double L"),
 }
