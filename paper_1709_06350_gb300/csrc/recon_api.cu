@@ -396,7 +396,8 @@ recon_status recon_smooth_density(recon_handle *H, const double *rho, double R, 
 
 recon_status recon_level_scales(recon_handle *H, double *out, int n, int *levels)
 {
-    if (!H || (n > 0 && !out)) return RECON_E_INVALID;
+    if (!H) return RECON_E_INVALID;
+    if (n > 0 && !out) return set_err(H, RECON_E_INVALID, "NULL pointer");
     const int coarse = H->nlev - 1;
     if (levels) *levels = coarse;
     if (n <= 0 || coarse <= 0) return RECON_OK;
