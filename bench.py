@@ -957,6 +957,10 @@ def _time_launches(torch, stream, fn, reps):
 # the FAS smoother, -s 18 -c 1 for the linear one); a launch at N^3
 # moves (N/384)^3 times as much.  Valid for the kernels as they were
 # captured: re-measure after a change to either kernel.
+# DRAM bytes (read + write) of one 384^3 launch from the last ncu capture of
+# each smoother; both kernels changed after that capture (a device scalar is
+# now folded into each update), so the roofline reports traffic as null and
+# these figures only as the earlier capture's context.
 NCU_TRAFFIC_384 = {"LIN": 689.353472e6 + 208.309248e6, "FAS": 472.232960e6 + 210.356992e6}
 
 
@@ -1029,8 +1033,11 @@ def kernel_roofline(recon, torch, N, L, dev, stream):
         alg = bpc * N ** 3
         ach = alg / t / 1e9
         out.append({"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                    "frac": ach / hbm, "traffic": NCU_TRAFFIC_384[key] * (N / 384.0) ** 3,
-                    "traffic_source": "ncu dram bytes of one 384^3 launch, scaled by cells",
+                    "frac": ach / hbm, "traffic": None,
+                    "traffic_source": "null: the kernel changed after its last ncu capture (a device "
+                                      "scalar folded into the update); that capture's DRAM bytes, "
+                                      "scaled from 384^3 by cells, are in traffic_last_capture",
+                    "traffic_last_capture": NCU_TRAFFIC_384[key] * (N / 384.0) ** 3,
                     "peak_source": src, "algorithmic_bytes_per_launch": alg,
                     "avg_launch_ms": t * 1e3, "cell_updates_per_s": N ** 3 / t})
     return out
