@@ -33,7 +33,17 @@ METRIC = ("512³ time-to-‖r‖/‖δ‖<1e-8 (mixed vs FP64 GPU); "
 UNIT = "512^3 reconstructions/s"
 
 
-def pin_to_local_cpus(dev_index):
+def parse_cpulist(spec: str) -> set:
+    """CPU numbers of a kernel CPU list such as "0-3,8,10-11"."""
+    cpus = set()
+    for part in spec.strip().split(","):
+        if part:
+            first, _, last = part.partition("-")
+            cpus.update(range(int(first), int(last or first) + 1))
+    return cpus
+
+
+def pin_to_local_cpus(dev_index, sysfs="/sys/bus/pci/devices"):
     """Restrict this process to the CPUs attached to the GPU (its PCI
     device's local_cpulist), so that page-locked buffers allocated afterwards
     are placed on that CPU's memory node.  Returns the list, or None when the
@@ -42,19 +52,16 @@ def pin_to_local_cpus(dev_index):
     try:
         p = torch.cuda.get_device_properties(dev_index)
         bdf = "%04x:%02x:%02x.0" % (p.pci_domain_id, p.pci_bus_id, p.pci_device_id)
-        with open(f"/sys/bus/pci/devices/{bdf}/local_cpulist") as f:
+        with open(os.path.join(sysfs, bdf, "local_cpulist")) as f:
             spec = f.read().strip()
-        cpus = set()
-        for part in spec.split(","):
-            a, _, b = part.partition("-")
-            cpus.update(range(int(a), int(b or a) + 1))
-        cpus &= os.sched_getaffinity(0)
+        cpus = parse_cpulist(spec) & os.sched_getaffinity(0)
         if not cpus:
             return None
         os.sched_setaffinity(0, cpus)
         return spec
     except Exception:   # best effort: any failure leaves the affinity as it was
         return None
+
 
 def parse():
     p = argparse.ArgumentParser()
